@@ -1,0 +1,831 @@
+/*
+ * orc.c -- plain FP64 CPU oracle of the ternary free-energy entropic lattice
+ * Boltzmann update of arXiv:1710.07486.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product path.  It shares no code
+ * with the CUDA library.  Every step is written out in the order of the
+ * algorithm, single-threaded, without blocking or fusion.
+ *
+ * The paper states the continuum model (Eqs. 1-8) and names the discrete
+ * schemes (entropic LBM with exact-difference forcing for the density
+ * populations f, BGK for the phase-field populations g) but defers the
+ * discrete formulas to its supplement, which is not available.  Where that
+ * is the case the reading used is stated at the function ("reading: ...").
+ */
+#include "orc.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+struct orc_ctx {
+    int D, Q, nx, ny, nz;
+    long N;
+    int bc[3];
+    orc_params p;
+    double rho_g, rho_l, mu_coex, p_coex;
+    double tau, beta;
+    int c[27][3];
+    double w[27];
+    int opp[27];
+    int rest;
+};
+
+/* ------------------------------------------------------------------------- */
+/* Thermodynamics: Carnahan-Starling free energy, Eq. 4 (without C).         */
+/* ------------------------------------------------------------------------- */
+
+/* Psi~(rho) = rho ( -a rho - 8RT(b rho - 6)/(b rho - 4)^2 + RT ln rho ), Eq. 4
+   with C = 0. */
+double orc_psi_tilde(double a, double b, double R, double T, double rho)
+{
+    double br = b * rho;
+    return rho * (-a * rho - 8.0 * R * T * (br - 6.0) / ((br - 4.0) * (br - 4.0))
+                  + R * T * log(rho));
+}
+
+/* d Psi~ / d rho, differentiated by hand from Eq. 4:
+   -2 a rho - 8RT (24 - 2 b rho)/(b rho - 4)^3 + RT (ln rho + 1). */
+double orc_dpsi_tilde(double a, double b, double R, double T, double rho)
+{
+    double br = b * rho;
+    double d = br - 4.0;
+    return -2.0 * a * rho - 8.0 * R * T * (24.0 - 2.0 * br) / (d * d * d)
+           + R * T * (log(rho) + 1.0);
+}
+
+/* p_eos = rho dPsi/drho - Psi (text before Eq. 4); C cancels. */
+double orc_p_eos(double a, double b, double R, double T, double rho)
+{
+    return rho * orc_dpsi_tilde(a, b, R, T, rho) - orc_psi_tilde(a, b, R, T, rho);
+}
+
+/* Locate the van der Waals loop of p_eos: the local maximum rho_s1 and the
+   following local minimum rho_s2.  Returns 0 if found, -1 otherwise. */
+static int spinodals(double a, double b, double R, double T, double *s1, double *s2)
+{
+    const int M = 20000;
+    double lo = log(1e-7), hi = log(0.98 * 4.0 / b);
+    double prev_p = orc_p_eos(a, b, R, T, exp(lo));
+    int state = 0; /* 0 rising, 1 falling */
+    int i_max = -1, i_min = -1;
+    for (int i = 1; i <= M; i++) {
+        double x = lo + (hi - lo) * i / M;
+        double pv = orc_p_eos(a, b, R, T, exp(x));
+        if (state == 0 && pv < prev_p) { state = 1; i_max = i - 1; }
+        else if (state == 1 && pv > prev_p) { i_min = i - 1; break; }
+        prev_p = pv;
+    }
+    if (i_max < 0 || i_min < 0) return -1;
+    /* golden-section refinement of the extremum in [i-1, i+1] grid cells */
+    for (int which = 0; which < 2; which++) {
+        int ic = which == 0 ? i_max : i_min;
+        double xa = lo + (hi - lo) * (ic - 1) / M, xb = lo + (hi - lo) * (ic + 1) / M;
+        double g = 0.5 * (sqrt(5.0) - 1.0);
+        for (int it = 0; it < 200; it++) {
+            double x1 = xb - g * (xb - xa), x2 = xa + g * (xb - xa);
+            double p1 = orc_p_eos(a, b, R, T, exp(x1)), p2 = orc_p_eos(a, b, R, T, exp(x2));
+            int keep_left = which == 0 ? (p1 > p2) : (p1 < p2);
+            if (keep_left) xb = x2; else xa = x1;
+        }
+        if (which == 0) *s1 = exp(0.5 * (xa + xb)); else *s2 = exp(0.5 * (xa + xb));
+    }
+    return 0;
+}
+
+/* root of p_eos(rho) = target on [lo, hi] where p_eos is increasing */
+static double p_root(double a, double b, double R, double T, double target,
+                     double lo, double hi)
+{
+    for (int it = 0; it < 400; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (orc_p_eos(a, b, R, T, mid) < target) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Common-tangent (Maxwell) construction: the coexisting densities have equal
+   pressure and equal dPsi/drho.  Choosing C = -mu_coex and
+   Psi_0 = Psi_eos(rho_g) = Psi_eos(rho_l) = -p_coex meets the condition stated
+   after Eq. 4.  Solved by bisection on the saturation pressure. */
+int orc_coexistence(double a, double b, double R, double T, double out[4])
+{
+    double s1, s2;
+    if (!(a > 0 && b > 0 && R > 0 && T > 0)) return -1;
+    if (spinodals(a, b, R, T, &s1, &s2)) return -1;
+    double rmax = 0.98 * 4.0 / b;
+    double p_hi = orc_p_eos(a, b, R, T, s1);
+    double p_lo = orc_p_eos(a, b, R, T, s2);
+    if (p_lo < 0.0) p_lo = 0.0;
+    if (orc_p_eos(a, b, R, T, rmax) <= p_hi) return -1;
+    double rg = 0, rl = 0;
+    for (int it = 0; it < 400; it++) {
+        double ps = 0.5 * (p_lo + p_hi);
+        if (ps <= p_lo || ps >= p_hi) break;
+        rg = p_root(a, b, R, T, ps, 1e-300, s1);
+        rl = p_root(a, b, R, T, ps, s2, rmax);
+        double dmu = orc_dpsi_tilde(a, b, R, T, rl) - orc_dpsi_tilde(a, b, R, T, rg);
+        /* dmu > 0: the saturation pressure is too low */
+        if (dmu > 0.0) p_lo = ps; else p_hi = ps;
+    }
+    double ps = 0.5 * (p_lo + p_hi);
+    rg = p_root(a, b, R, T, ps, 1e-300, s1);
+    rl = p_root(a, b, R, T, ps, s2, rmax);
+    out[0] = rg;
+    out[1] = rl;
+    out[2] = 0.5 * (orc_dpsi_tilde(a, b, R, T, rg) + orc_dpsi_tilde(a, b, R, T, rl));
+    out[3] = 0.5 * (orc_p_eos(a, b, R, T, rg) + orc_p_eos(a, b, R, T, rl));
+    return 0;
+}
+
+/* Critical point of the CS isotherms.  Along the spinodal dp/drho = 0; with
+   dp/drho = rho d2Psi~/drho2 and d2Psi~/drho2 = -2a - 32RTb(b rho - 16)/(b rho
+   - 4)^4 + RT/rho this gives T_s(rho) = 2 a rho / (R (1 - 32 b rho (b rho - 16)
+   / (b rho - 4)^4)).  T_c is the maximum of T_s, rho_c its argument. */
+static double t_spinodal(double a, double b, double R, double rho)
+{
+    double br = b * rho, d = br - 4.0;
+    return 2.0 * a * rho / (R * (1.0 - 32.0 * br * (br - 16.0) / (d * d * d * d)));
+}
+
+int orc_critical_point(double a, double b, double R, double out[2])
+{
+    if (!(a > 0 && b > 0 && R > 0)) return -1;
+    double xa = 0.05 / b, xb = 3.5 / b, g = 0.5 * (sqrt(5.0) - 1.0);
+    for (int it = 0; it < 300; it++) {
+        double x1 = xb - g * (xb - xa), x2 = xa + g * (xb - xa);
+        if (t_spinodal(a, b, R, x1) > t_spinodal(a, b, R, x2)) xb = x2; else xa = x1;
+    }
+    out[1] = 0.5 * (xa + xb);
+    out[0] = t_spinodal(a, b, R, out[1]);
+    return 0;
+}
+
+/* The coexistence ratio rho_l/rho_g falls monotonically with T: bisection. */
+int orc_temperature_for_ratio(double a, double b, double R, double ratio, double *T)
+{
+    double cp[2], co[4];
+    if (!(ratio > 1.0) || orc_critical_point(a, b, R, cp)) return -1;
+    double lo = 0.3 * cp[0], hi = 0.999 * cp[0];
+    if (orc_coexistence(a, b, R, lo, co)) return -1;
+    if (co[1] / co[0] < ratio) return -1;
+    if (orc_coexistence(a, b, R, hi, co)) return -1;
+    if (co[1] / co[0] > ratio) return -1;
+    for (int it = 0; it < 200; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (orc_coexistence(a, b, R, mid, co)) return -1;
+        if (co[1] / co[0] > ratio) lo = mid; else hi = mid;
+    }
+    *T = 0.5 * (lo + hi);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Lattice: D2Q9 and D3Q27, c_s^2 = 1/3.                                      */
+/* ------------------------------------------------------------------------- */
+
+/* D2Q9, listed with the x component running fastest. */
+static const int C_D2Q9[9][2] = {
+    {-1, -1}, {0, -1}, {1, -1},
+    {-1, 0},  {0, 0},  {1, 0},
+    {-1, 1},  {0, 1},  {1, 1}};
+static const double W_D2Q9[9] = {
+    1.0 / 36, 1.0 / 9, 1.0 / 36,
+    1.0 / 9,  4.0 / 9, 1.0 / 9,
+    1.0 / 36, 1.0 / 9, 1.0 / 36};
+
+/* D3Q27 weights by the number of non-zero components: rest 8/27, the six face
+   neighbours 2/27, the twelve edge neighbours 1/54, the eight corners 1/216. */
+static double w_d3q27(int cx, int cy, int cz)
+{
+    int k = (cx != 0) + (cy != 0) + (cz != 0);
+    if (k == 0) return 8.0 / 27;
+    if (k == 1) return 2.0 / 27;
+    if (k == 2) return 1.0 / 54;
+    return 1.0 / 216;
+}
+
+orc_ctx *orc_create(int lattice, int nx, int ny, int nz, const orc_params *p,
+                    const int bc[3])
+{
+    if (lattice != 0 && lattice != 1) return NULL;
+    if (nx < 1 || ny < 1 || nz < 1) return NULL;
+    if (lattice == 0 && nz != 1) return NULL;
+    orc_ctx *o = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+    if (!o) return NULL;
+    o->D = lattice == 0 ? 2 : 3;
+    o->Q = lattice == 0 ? 9 : 27;
+    o->nx = nx; o->ny = ny; o->nz = nz;
+    o->N = (long)nx * ny * nz;
+    for (int a = 0; a < 3; a++) o->bc[a] = bc ? bc[a] : 0;
+    if (lattice == 0) o->bc[2] = 0;
+    o->p = *p;
+    if (lattice == 0) {
+        for (int i = 0; i < 9; i++) {
+            o->c[i][0] = C_D2Q9[i][0];
+            o->c[i][1] = C_D2Q9[i][1];
+            o->c[i][2] = 0;
+            o->w[i] = W_D2Q9[i];
+        }
+    } else {
+        int i = 0;
+        for (int cz = -1; cz <= 1; cz++)
+            for (int cy = -1; cy <= 1; cy++)
+                for (int cx = -1; cx <= 1; cx++) {
+                    o->c[i][0] = cx; o->c[i][1] = cy; o->c[i][2] = cz;
+                    o->w[i] = w_d3q27(cx, cy, cz);
+                    i++;
+                }
+    }
+    for (int i = 0; i < o->Q; i++) {
+        if (o->c[i][0] == 0 && o->c[i][1] == 0 && o->c[i][2] == 0) o->rest = i;
+        for (int j = 0; j < o->Q; j++)
+            if (o->c[j][0] == -o->c[i][0] && o->c[j][1] == -o->c[i][1] &&
+                o->c[j][2] == -o->c[i][2])
+                o->opp[i] = j;
+    }
+    double co[4];
+    if (orc_coexistence(p->a, p->b, p->R, p->T, co)) { free(o); return NULL; }
+    o->rho_g = co[0]; o->rho_l = co[1]; o->mu_coex = co[2]; o->p_coex = co[3];
+    /* nu = c_s^2 (tau - 1/2) with c_s^2 = 1/3; KBC uses beta = 1/(2 tau) */
+    o->tau = 3.0 * p->nu + 0.5;
+    o->beta = 1.0 / (2.0 * o->tau);
+    return o;
+}
+
+void orc_destroy(orc_ctx *o) { free(o); }
+int orc_Q(const orc_ctx *o) { return o->Q; }
+long orc_N(const orc_ctx *o) { return o->N; }
+
+void orc_velocities(const orc_ctx *o, int *c, double *w)
+{
+    for (int i = 0; i < o->Q; i++) {
+        for (int a = 0; a < 3; a++) c[3 * i + a] = o->c[i][a];
+        w[i] = o->w[i];
+    }
+}
+
+void orc_derived(const orc_ctx *o, double out[6])
+{
+    out[0] = o->rho_g; out[1] = o->rho_l; out[2] = o->mu_coex; out[3] = o->p_coex;
+    out[4] = o->tau; out[5] = o->beta;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Free energy and chemical potentials (Eqs. 1-5 and the definitions of      */
+/* mu_rho, mu_phi after Eq. 8).                                              */
+/* ------------------------------------------------------------------------- */
+
+/* Psi_eos - Psi_0 with C = -mu_coex and Psi_0 = -p_coex (text after Eq. 4) */
+static double psi_shifted(const orc_ctx *o, double rho)
+{
+    const orc_params *p = &o->p;
+    return orc_psi_tilde(p->a, p->b, p->R, p->T, rho) - o->mu_coex * rho + o->p_coex;
+}
+
+/* C_l1 and C_l2 from (rho, phi), text before Eq. 5 */
+static double conc_l1(const orc_ctx *o, double rho, double phi)
+{
+    return 0.5 * (1.0 + phi / o->p.chi - (rho - o->rho_l) / (o->rho_g - o->rho_l));
+}
+static double conc_l2(const orc_ctx *o, double rho, double phi)
+{
+    return 0.5 * (1.0 - phi / o->p.chi - (rho - o->rho_l) / (o->rho_g - o->rho_l));
+}
+
+/* Eq. 2 */
+double orc_f_bulk(const orc_ctx *o, double rho, double phi)
+{
+    double c1 = conc_l1(o, rho, phi), c2 = conc_l2(o, rho, phi);
+    return 0.5 * o->p.lambda1 * psi_shifted(o, rho)
+           + 0.5 * o->p.lambda2 * c1 * c1 * (1.0 - c1) * (1.0 - c1)
+           + 0.5 * o->p.lambda3 * c2 * c2 * (1.0 - c2) * (1.0 - c2);
+}
+
+/* Neighbour of node (x,y,z) along c for the stencils.  Periodic axes wrap.
+   Reading (wall ghosts; not in the paper): on a bounce-back axis the ghost
+   node beyond the half-way wall mirrors the first fluid node, so -1 -> 0 and
+   n -> n-1 (zero normal gradient, neutral wetting). */
+static long stencil_nb(const orc_ctx *o, int x, int y, int z, const int *c)
+{
+    int q[3] = {x + c[0], y + c[1], z + c[2]};
+    int n[3] = {o->nx, o->ny, o->nz};
+    for (int a = 0; a < 3; a++) {
+        if (q[a] < 0) q[a] = o->bc[a] == 0 ? q[a] + n[a] : 0;
+        else if (q[a] >= n[a]) q[a] = o->bc[a] == 0 ? q[a] - n[a] : n[a] - 1;
+    }
+    return (long)q[0] + (long)o->nx * ((long)q[1] + (long)o->ny * q[2]);
+}
+
+/* Reading (stencils; not in the paper): the lattice-weight isotropic
+   Laplacian  lap psi = (2/c_s^2) sum_i w_i (psi(x+c_i) - psi(x)). */
+void orc_laplacian(const orc_ctx *o, const double *psi, double *lap)
+{
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                long n = x + (long)o->nx * (y + (long)o->ny * z);
+                double s = 0.0;
+                for (int i = 0; i < o->Q; i++)
+                    s += o->w[i] * (psi[stencil_nb(o, x, y, z, o->c[i])] - psi[n]);
+                lap[n] = 6.0 * s;
+            }
+}
+
+/* Reading (stencils): the isotropic gradient
+   grad psi = (1/c_s^2) sum_i w_i c_i psi(x+c_i).  grad is [3][N]. */
+void orc_gradient(const orc_ctx *o, const double *psi, double *grad)
+{
+    long N = o->N;
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                long n = x + (long)o->nx * (y + (long)o->ny * z);
+                double s[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < o->Q; i++) {
+                    double v = psi[stencil_nb(o, x, y, z, o->c[i])];
+                    for (int a = 0; a < 3; a++) s[a] += o->w[i] * o->c[i][a] * v;
+                }
+                for (int a = 0; a < 3; a++) grad[a * N + n] = 3.0 * s[a];
+            }
+}
+
+/* mu_rho = dF/drho and mu_phi = dF/dphi of Eq. 1 written with Eq. 5:
+     mu_rho = (lambda1/2) dPsi_eos/drho
+              - [lambda2 w'(C1) + lambda3 w'(C2)] / (2 Delta)
+              - [kappa1 + (kappa2+kappa3)/(4 Delta^2)] lap rho
+              - (kappa3-kappa2)/(4 chi Delta) lap phi
+     mu_phi = [lambda2 w'(C1) - lambda3 w'(C2)] / (2 chi)
+              - (kappa2+kappa3)/(4 chi^2) lap phi
+              - (kappa3-kappa2)/(4 chi Delta) lap rho
+   with Delta = rho_g - rho_l and w'(C) = C (1-C) (1-2C). */
+void orc_chem_pot(const orc_ctx *o, const double *rho, const double *phi,
+                  double *mu_rho, double *mu_phi)
+{
+    const orc_params *p = &o->p;
+    long N = o->N;
+    double *lr = (double *)malloc(sizeof(double) * N);
+    double *lp = (double *)malloc(sizeof(double) * N);
+    orc_laplacian(o, rho, lr);
+    orc_laplacian(o, phi, lp);
+    double Dl = o->rho_g - o->rho_l, chi = p->chi;
+    for (long n = 0; n < N; n++) {
+        double c1 = conc_l1(o, rho[n], phi[n]), c2 = conc_l2(o, rho[n], phi[n]);
+        double w1 = c1 * (1.0 - c1) * (1.0 - 2.0 * c1);
+        double w2 = c2 * (1.0 - c2) * (1.0 - 2.0 * c2);
+        double dpsi = orc_dpsi_tilde(p->a, p->b, p->R, p->T, rho[n]) - o->mu_coex;
+        mu_rho[n] = 0.5 * p->lambda1 * dpsi
+                    - (p->lambda2 * w1 + p->lambda3 * w2) / (2.0 * Dl)
+                    - (p->kappa1 + (p->kappa2 + p->kappa3) / (4.0 * Dl * Dl)) * lr[n]
+                    - (p->kappa3 - p->kappa2) / (4.0 * chi * Dl) * lp[n];
+        mu_phi[n] = (p->lambda2 * w1 - p->lambda3 * w2) / (2.0 * chi)
+                    - (p->kappa2 + p->kappa3) / (4.0 * chi * chi) * lp[n]
+                    - (p->kappa3 - p->kappa2) / (4.0 * chi * Dl) * lr[n];
+    }
+    free(lr);
+    free(lp);
+}
+
+/* Neighbour for a vector-valued stencil input: like stencil_nb, and sgn[a]
+   is -1 for each axis on which the neighbour was mirrored at a wall (the
+   component of a gradient normal to the wall changes sign under the mirror). */
+static long stencil_nb_vec(const orc_ctx *o, int x, int y, int z, const int *c, int sgn[3])
+{
+    int q[3] = {x + c[0], y + c[1], z + c[2]};
+    int n[3] = {o->nx, o->ny, o->nz};
+    for (int a = 0; a < 3; a++) {
+        sgn[a] = 1;
+        if (q[a] < 0) {
+            if (o->bc[a] == 0) q[a] += n[a]; else { q[a] = 0; sgn[a] = -1; }
+        } else if (q[a] >= n[a]) {
+            if (o->bc[a] == 0) q[a] -= n[a]; else { q[a] = n[a] - 1; sgn[a] = -1; }
+        }
+    }
+    return (long)q[0] + (long)o->nx * ((long)q[1] + (long)o->ny * q[2]);
+}
+
+/* Force on the density populations.  The paper gives div P = rho grad mu_rho
+   + phi grad mu_phi (after Eq. 8) and applies the force of the entropic LBM
+   with exact-difference forcing; the equilibrium of f already carries the
+   ideal pressure rho c_s^2, so (reading) F = -rho grad mu_rho - phi grad
+   mu_phi + F_id with F_id the ideal-pressure term.
+
+   force_form 0 (potential form): F_id = c_s^2 grad rho.
+
+   force_form 1 (lattice-consistent form; reading): at a steady state of the
+   lattice update the streamed populations average the applied force over the
+   neighbours and carry the exact-difference momentum flux F F/(4 rho), so the
+   update balances (I + A)/2 F - div(F F/(4 rho)) = c_s^2 grad rho with
+   A[G]_a(x) = sum_i 3 w_i c_ia (c_i . G(x - c_i)).  Taking, with G = grad rho,
+     F_id = c_s^2 (3/2 G - 1/2 A[G]) + div(c_s^4 G G / (4 rho))
+   makes that balance hold, to the next order, exactly when rho grad mu_rho
+   + phi grad mu_phi = 0, i.e. at the thermodynamic equilibrium of Eq. 1. */
+void orc_force(const orc_ctx *o, const double *rho, const double *phi,
+               const double *mu_rho, const double *mu_phi, double *F)
+{
+    long N = o->N;
+    const double cs2 = 1.0 / 3.0;
+    double *gm = (double *)malloc(sizeof(double) * 3 * N);
+    double *gp = (double *)malloc(sizeof(double) * 3 * N);
+    double *gr = (double *)malloc(sizeof(double) * 3 * N);
+    orc_gradient(o, mu_rho, gm);
+    orc_gradient(o, mu_phi, gp);
+    orc_gradient(o, rho, gr);
+    for (int a = 0; a < 3; a++)
+        for (long n = 0; n < N; n++)
+            F[a * N + n] = -rho[n] * gm[a * N + n] - phi[n] * gp[a * N + n];
+    if (o->p.force_form == 0) {
+        for (long n = 0; n < 3 * N; n++) F[n] += cs2 * gr[n];
+    } else {
+        for (int z = 0; z < o->nz; z++)
+            for (int y = 0; y < o->ny; y++)
+                for (int x = 0; x < o->nx; x++) {
+                    long n = x + (long)o->nx * (y + (long)o->ny * z);
+                    double AG[3] = {0, 0, 0}, divT[3] = {0, 0, 0};
+                    for (int i = 0; i < o->Q; i++) {
+                        int sg[3], mc[3] = {-o->c[i][0], -o->c[i][1], -o->c[i][2]};
+                        /* A[G] reads G at x - c_i */
+                        long m = stencil_nb_vec(o, x, y, z, mc, sg);
+                        double cG = 0.0;
+                        for (int b = 0; b < 3; b++) cG += o->c[i][b] * sg[b] * gr[b * N + m];
+                        for (int a = 0; a < 3; a++) AG[a] += 3.0 * o->w[i] * o->c[i][a] * cG;
+                        /* div T reads T = c_s^4 G G/(4 rho) at x + c_i */
+                        long p = stencil_nb_vec(o, x, y, z, o->c[i], sg);
+                        for (int a = 0; a < 3; a++)
+                            for (int b = 0; b < 3; b++) {
+                                double T = cs2 * cs2 * (sg[a] * gr[a * N + p]) * (sg[b] * gr[b * N + p])
+                                           / (4.0 * rho[p]);
+                                divT[a] += 3.0 * o->w[i] * o->c[i][b] * T;
+                            }
+                    }
+                    for (int a = 0; a < 3; a++)
+                        F[a * N + n] += cs2 * (1.5 * gr[a * N + n] - 0.5 * AG[a]) + divT[a];
+                }
+    }
+    free(gm);
+    free(gp);
+    free(gr);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Collision of f: entropic equilibrium, KBC split, stabiliser, exact-       */
+/* difference forcing.  The paper names the entropic LBM with exact-         */
+/* difference forcing (paragraph after Eq. 8); the formulas below are those  */
+/* of the cited KBC/ELBM method (reading).                                   */
+/* ------------------------------------------------------------------------- */
+
+/* Entropic (product-form) equilibrium:
+   f_i = rho w_i prod_a (2 - S_a) ((2 u_a + S_a)/(1 - u_a))^{c_ia},
+   S_a = sqrt(1 + 3 u_a^2). */
+void orc_feq(const orc_ctx *o, double rho, const double u[3], double *feq)
+{
+    for (int i = 0; i < o->Q; i++) {
+        double prod = 1.0;
+        for (int a = 0; a < o->D; a++) {
+            double S = sqrt(1.0 + 3.0 * u[a] * u[a]);
+            double X = (2.0 * u[a] + S) / (1.0 - u[a]);
+            double pw = o->c[i][a] == 1 ? X : (o->c[i][a] == -1 ? 1.0 / X : 1.0);
+            prod *= (2.0 - S) * pw;
+        }
+        feq[i] = rho * o->w[i] * prod;
+    }
+}
+
+/* Dual basis of the one-dimensional moments {1, c, c^2} on c in {-1,0,1}:
+   sum_c d_k(c) c^m = delta_km. */
+static double dual(int k, int c)
+{
+    if (k == 0) return c == 0 ? 1.0 : 0.0;
+    if (k == 1) return 0.5 * c;
+    return c == 0 ? -1.0 : 0.5;
+}
+
+/* The population vector whose natural moments M_pqr = sum_i X_i cx^p cy^q cz^r
+   are all zero except M(e) = 1: product of the one-dimensional duals. */
+static double dual_vec(const orc_ctx *o, int i, const int e[3])
+{
+    double v = 1.0;
+    for (int a = 0; a < o->D; a++) v *= dual(e[a], o->c[i][a]);
+    return v;
+}
+
+int orc_collide_f(const orc_ctx *o, const double *f, const double F[3],
+                  double *fout, double *ds_out, double *gamma)
+{
+    int Q = o->Q, D = o->D;
+    double rho = 0.0, j[3] = {0, 0, 0};
+    for (int i = 0; i < Q; i++) {
+        rho += f[i];
+        for (int a = 0; a < 3; a++) j[a] += f[i] * o->c[i][a];
+    }
+    if (!(rho > 0.0)) return -3;
+    double u[3], uF[3];
+    for (int a = 0; a < 3; a++) {
+        u[a] = j[a] / rho;
+        uF[a] = u[a] + F[a] / rho;
+    }
+    for (int a = 0; a < D; a++)
+        if (!(fabs(u[a]) < 1.0) || !(fabs(uF[a]) < 1.0)) return -3;
+    double feq[27], feqF[27], dl[27], ds[27], dh[27];
+    orc_feq(o, rho, u, feq);
+    orc_feq(o, rho, uF, feqF);
+    for (int i = 0; i < Q; i++) dl[i] = f[i] - feq[i];
+    /* second-order moments of Delta = f - f^eq */
+    double Pi[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            Pi[a][b] = 0.0;
+            for (int i = 0; i < Q; i++) Pi[a][b] += dl[i] * o->c[i][a] * o->c[i][b];
+        }
+    double tr = 0.0;
+    for (int a = 0; a < D; a++) tr += Pi[a][a];
+    /* Delta s: the deviatoric part of the stress; every other natural moment
+       (density, momentum, the trace of the stress, all higher moments) is 0
+       (reading: trace left in h). */
+    for (int i = 0; i < Q; i++) {
+        double s = 0.0;
+        for (int a = 0; a < D; a++) {
+            int e[3] = {0, 0, 0};
+            e[a] = 2;
+            s += (Pi[a][a] - tr / D) * dual_vec(o, i, e);
+            for (int b = a + 1; b < D; b++) {
+                int e2[3] = {0, 0, 0};
+                e2[a] = 1;
+                e2[b] = 1;
+                s += Pi[a][b] * dual_vec(o, i, e2);
+            }
+        }
+        ds[i] = s;
+        dh[i] = dl[i] - ds[i];
+    }
+    /* entropic scalar products <X|Y> = sum_i X_i Y_i / f^eq_i */
+    double sh = 0.0, hh = 0.0;
+    for (int i = 0; i < Q; i++) {
+        sh += ds[i] * dh[i] / feq[i];
+        hh += dh[i] * dh[i] / feq[i];
+    }
+    double beta = o->beta;
+    double g = 2.0;
+    if (hh > 1e-30 * rho * rho) g = 1.0 / beta - (2.0 - 1.0 / beta) * sh / hh;
+    for (int i = 0; i < Q; i++) {
+        fout[i] = f[i] - beta * (2.0 * ds[i] + g * dh[i]) + (feqF[i] - feq[i]);
+        if (ds_out) ds_out[i] = ds[i];
+    }
+    if (gamma) *gamma = g;
+    for (int i = 0; i < Q; i++)
+        if (!isfinite(fout[i])) return -3;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Phase field: BGK with the standard Cahn-Hilliard equilibrium (paragraph    */
+/* after Eq. 8 cites the textbook scheme; reading):                           */
+/*   g_i = w_i [Gamma mu_phi / c_s^2 + phi c_i.u / c_s^2                      */
+/*              + phi ((c_i.u)^2 / (2 c_s^4) - u.u / (2 c_s^2))],  i != 0      */
+/*   g_0 = phi - sum_{i != 0} g_i.                                             */
+/* ------------------------------------------------------------------------- */
+void orc_geq(const orc_ctx *o, double phi, double mu_phi, const double u[3],
+             double *geq)
+{
+    const double cs2 = 1.0 / 3.0;
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double others = 0.0;
+    for (int i = 0; i < o->Q; i++) {
+        if (i == o->rest) continue;
+        double cu = o->c[i][0] * u[0] + o->c[i][1] * u[1] + o->c[i][2] * u[2];
+        geq[i] = o->w[i] * (o->p.Gamma * mu_phi / cs2 + phi * cu / cs2
+                            + phi * (cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2)));
+        others += geq[i];
+    }
+    geq[o->rest] = phi - others;
+}
+
+void orc_collide_g(const orc_ctx *o, const double *g, double phi, double mu_phi,
+                   const double u[3], double *gout)
+{
+    double geq[27];
+    orc_geq(o, phi, mu_phi, u, geq);
+    for (int i = 0; i < o->Q; i++) gout[i] = g[i] - (g[i] - geq[i]) / o->p.tau_g;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Streaming (pull) with periodic wrap and half-way bounce-back.             */
+/* ------------------------------------------------------------------------- */
+
+/* Source of population i at node (x,y,z): returns the source node index, or
+   -1 when x - c_i lies beyond a bounce-back wall. */
+static long pull_src(const orc_ctx *o, int x, int y, int z, int i)
+{
+    int q[3] = {x - o->c[i][0], y - o->c[i][1], z - o->c[i][2]};
+    int n[3] = {o->nx, o->ny, o->nz};
+    for (int a = 0; a < 3; a++) {
+        if (q[a] < 0 || q[a] >= n[a]) {
+            if (o->bc[a] != 0) return -1;
+            q[a] = (q[a] + n[a]) % n[a];
+        }
+    }
+    return (long)q[0] + (long)o->nx * ((long)q[1] + (long)o->ny * q[2]);
+}
+
+void orc_stream(const orc_ctx *o, const double *post, double *pre)
+{
+    long N = o->N;
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                long n = x + (long)o->nx * (y + (long)o->ny * z);
+                for (int i = 0; i < o->Q; i++) {
+                    long s = pull_src(o, x, y, z, i);
+                    pre[i * N + n] = s >= 0 ? post[i * N + s] : post[o->opp[i] * N + n];
+                }
+            }
+}
+
+void orc_unstream(const orc_ctx *o, const double *pre, double *post)
+{
+    long N = o->N;
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                long n = x + (long)o->nx * (y + (long)o->ny * z);
+                for (int i = 0; i < o->Q; i++) {
+                    long s = pull_src(o, x, y, z, i);
+                    if (s >= 0) post[i * N + s] = pre[i * N + n];
+                    else post[o->opp[i] * N + n] = pre[i * N + n];
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Whole step                                                                */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double *fpre, *gpre, *rho, *phi, *j, *mr, *mp, *F;
+} work_t;
+
+static int work_alloc(const orc_ctx *o, work_t *w)
+{
+    long N = o->N, Q = o->Q;
+    w->fpre = (double *)malloc(sizeof(double) * Q * N);
+    w->gpre = (double *)malloc(sizeof(double) * Q * N);
+    w->rho = (double *)malloc(sizeof(double) * N);
+    w->phi = (double *)malloc(sizeof(double) * N);
+    w->j = (double *)malloc(sizeof(double) * 3 * N);
+    w->mr = (double *)malloc(sizeof(double) * N);
+    w->mp = (double *)malloc(sizeof(double) * N);
+    w->F = (double *)malloc(sizeof(double) * 3 * N);
+    if (!w->fpre || !w->gpre || !w->rho || !w->phi || !w->j || !w->mr || !w->mp || !w->F)
+        return -2;
+    return 0;
+}
+
+static void work_free(work_t *w)
+{
+    free(w->fpre); free(w->gpre); free(w->rho); free(w->phi);
+    free(w->j); free(w->mr); free(w->mp); free(w->F);
+}
+
+/* stream, then the moments rho = sum f, j = sum f c, phi = sum g, then the
+   chemical potentials and the force */
+static void pre_collision(const orc_ctx *o, const double *f, const double *g, work_t *w)
+{
+    long N = o->N;
+    orc_stream(o, f, w->fpre);
+    orc_stream(o, g, w->gpre);
+    for (long n = 0; n < N; n++) {
+        double r = 0.0, p = 0.0, jj[3] = {0, 0, 0};
+        for (int i = 0; i < o->Q; i++) {
+            r += w->fpre[i * N + n];
+            p += w->gpre[i * N + n];
+            for (int a = 0; a < 3; a++) jj[a] += w->fpre[i * N + n] * o->c[i][a];
+        }
+        w->rho[n] = r;
+        w->phi[n] = p;
+        for (int a = 0; a < 3; a++) w->j[a * N + n] = jj[a];
+    }
+    orc_chem_pot(o, w->rho, w->phi, w->mr, w->mp);
+    orc_force(o, w->rho, w->phi, w->mr, w->mp, w->F);
+}
+
+int orc_step(const orc_ctx *o, double *f, double *g, int nsteps)
+{
+    long N = o->N;
+    int Q = o->Q, rc = 0;
+    work_t w;
+    if (nsteps < 0) return -1;
+    if (work_alloc(o, &w)) { work_free(&w); return -2; }
+    for (int s = 0; s < nsteps && rc == 0; s++) {
+        pre_collision(o, f, g, &w);
+        for (long n = 0; n < N; n++) {
+            double fl[27], gl[27], fo[27], go[27], F[3], u[3];
+            for (int i = 0; i < Q; i++) {
+                fl[i] = w.fpre[i * N + n];
+                gl[i] = w.gpre[i * N + n];
+            }
+            for (int a = 0; a < 3; a++) F[a] = w.F[a * N + n];
+            int e = orc_collide_f(o, fl, F, fo, NULL, NULL);
+            if (e) rc = e;
+            /* the phase field is advected with u = (j + F/2)/rho (reading) */
+            for (int a = 0; a < 3; a++) u[a] = (w.j[a * N + n] + 0.5 * F[a]) / w.rho[n];
+            orc_collide_g(o, gl, w.phi[n], w.mp[n], u, go);
+            for (int i = 0; i < Q; i++) {
+                f[i * N + n] = fo[i];
+                g[i * N + n] = go[i];
+            }
+        }
+    }
+    work_free(&w);
+    return rc;
+}
+
+/* Initial state from rho, phi, u (reading): f = f^eq(rho, u - F/(2 rho)),
+   g = g^eq(phi, mu_phi, u), placed so that the first step streams them back
+   onto the nodes they belong to. */
+int orc_init(const orc_ctx *o, const double *rho, const double *phi,
+             const double *u, double *f, double *g)
+{
+    long N = o->N;
+    int Q = o->Q, D = o->D, rc = 0;
+    double *mr = (double *)malloc(sizeof(double) * N);
+    double *mp = (double *)malloc(sizeof(double) * N);
+    double *F = (double *)malloc(sizeof(double) * 3 * N);
+    double *fpre = (double *)malloc(sizeof(double) * Q * N);
+    double *gpre = (double *)malloc(sizeof(double) * Q * N);
+    if (!mr || !mp || !F || !fpre || !gpre) rc = -2;
+    if (rc == 0) {
+        orc_chem_pot(o, rho, phi, mr, mp);
+        orc_force(o, rho, phi, mr, mp, F);
+        for (long n = 0; n < N && rc == 0; n++) {
+            double us[3] = {0, 0, 0}, uu[3] = {0, 0, 0}, fe[27], ge[27];
+            if (!(rho[n] > 0.0)) { rc = -3; break; }
+            for (int a = 0; a < D; a++) {
+                uu[a] = u[a * N + n];
+                us[a] = uu[a] - F[a * N + n] / (2.0 * rho[n]);
+                if (!(fabs(us[a]) < 1.0)) rc = -3;
+            }
+            orc_feq(o, rho[n], us, fe);
+            orc_geq(o, phi[n], mp[n], uu, ge);
+            for (int i = 0; i < Q; i++) {
+                fpre[i * N + n] = fe[i];
+                gpre[i * N + n] = ge[i];
+            }
+        }
+        if (rc == 0) {
+            orc_unstream(o, fpre, f);
+            orc_unstream(o, gpre, g);
+        }
+    }
+    free(mr); free(mp); free(F); free(fpre); free(gpre);
+    return rc;
+}
+
+/* Fields of the state: the moments of the streamed populations, the physical
+   velocity u = (j + F/2)/rho and the isotropic part of the pressure tensor
+   p = rho mu_rho + phi mu_phi - f_B - f_I (f_I of Eq. 5 with the isotropic
+   gradients). */
+int orc_fields(const orc_ctx *o, const double *f, const double *g, double *rho,
+               double *phi, double *u, double *p)
+{
+    long N = o->N;
+    int D = o->D;
+    work_t w;
+    if (work_alloc(o, &w)) { work_free(&w); return -2; }
+    pre_collision(o, f, g, &w);
+    for (long n = 0; n < N; n++) {
+        rho[n] = w.rho[n];
+        phi[n] = w.phi[n];
+        for (int a = 0; a < D; a++) u[a * N + n] = (w.j[a * N + n] + 0.5 * w.F[a * N + n]) / w.rho[n];
+    }
+    if (p) {
+        const orc_params *q = &o->p;
+        double *gr = (double *)malloc(sizeof(double) * 3 * N);
+        double *gp = (double *)malloc(sizeof(double) * 3 * N);
+        orc_gradient(o, w.rho, gr);
+        orc_gradient(o, w.phi, gp);
+        double Dl = o->rho_g - o->rho_l, chi = q->chi;
+        double A = 0.5 * q->kappa1 + (q->kappa2 + q->kappa3) / (8.0 * Dl * Dl);
+        double B = (q->kappa2 + q->kappa3) / (8.0 * chi * chi);
+        double X = (q->kappa3 - q->kappa2) / (4.0 * chi * Dl);
+        for (long n = 0; n < N; n++) {
+            double rr = 0, pp = 0, rp = 0;
+            for (int a = 0; a < 3; a++) {
+                rr += gr[a * N + n] * gr[a * N + n];
+                pp += gp[a * N + n] * gp[a * N + n];
+                rp += gr[a * N + n] * gp[a * N + n];
+            }
+            double fI = A * rr + B * pp + X * rp;
+            p[n] = w.rho[n] * w.mr[n] + w.phi[n] * w.mp[n] - orc_f_bulk(o, w.rho[n], w.phi[n]) - fI;
+        }
+        free(gr);
+        free(gp);
+    }
+    int rc = 0;
+    for (long n = 0; n < N; n++)
+        if (!(w.rho[n] > 0.0) || !isfinite(w.phi[n])) rc = -3;
+    work_free(&w);
+    return rc;
+}
