@@ -1,0 +1,325 @@
+"""Throughput benchmark of the fused ternary entropic LBM step on GB300.
+
+Workload (default): D3Q27, 256^3 periodic nodes, liquid/gas density ratio
+1000, FP32-shifted populations with the FP64 stabiliser/gas-side chemical
+potential, an off-centre binary collision of a liquid-1 and a liquid-2 drop
+(R = 30) with impact parameter B ~ U[0,1], Weber number We ~ U[1,100] and
+surface-tension ratio sigma12/sigma1g in {0.5, 1, 2} drawn from the seed.
+A step is one fused kernel launch over all nodes.  The state (2 x 2 x 27 x
+4 B per node = 3.6 GB) is far larger than L2, so no flush is needed between
+steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the workload instead.  Under torchrun each rank runs an
+independent replica on its own GPU (the update has no exchange step on one
+GPU); value = all ranks' lattice updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline, D3Q27 ternary ELBM; surrogate speedup at ≤1% error"
+A_, B_, R_ = 0.037, 0.2, 1.0
+BYTES_PER_UPDATE = {(1, 1): 432, (1, 0): 864, (0, 1): 144, (0, 0): 288}  # (lattice, fp32?) -> 4 Q s
+
+
+def workload_c3(seed, n=256, ratio=1000.0):
+    """Parameters and initial fields of the off-centre collision."""
+    g = np.random.default_rng(seed)
+    B = float(g.uniform(0.0, 1.0))
+    We = float(g.uniform(1.0, 100.0))
+    srat = float(g.choice([0.5, 1.0, 2.0]))
+    return dict(n=n, ratio=ratio, B=B, We=We, sigma_ratio=srat, seed=seed)
+
+
+def c3_params(w, T, rho_g, rho_l):
+    chi = 5.0
+    kappa1, kappa2, lam2 = 0.01, 1.0, 0.5
+    # sigma12 = sqrt((k2+k3)(l2+l3))/6 for a liquid-liquid interface; the
+    # liquid-gas tension of liquid 1 is estimated from the double well along
+    # C1 with gradient weight kappa1 Delta^2 + kappa2 (equipartition,
+    # sqrt(K lambda)/6).
+    Dl = rho_l - rho_g
+    s1g = math.sqrt((kappa1 * Dl * Dl + kappa2) * lam2) / 6.0
+    # choose kappa3 = kappa2 * r, lambda3 = lambda2 * r so sigma12 = r' s1g
+    target = w["sigma_ratio"] * s1g
+    r = max(0.05, (6.0 * target) ** 2 / ((kappa2 + kappa2) * (lam2 + lam2)))
+    kappa3, lam3 = kappa2 * r, lam2 * r
+    R = 30.0
+    V = math.sqrt(w["We"] * s1g / (rho_l * 2 * R))
+    nu = 0.05
+    p = dict(a=A_, b=B_, R=R_, T=T, lambda1=0.6, lambda2=lam2, lambda3=lam3, kappa1=kappa1,
+             kappa2=kappa2, kappa3=kappa3, chi=chi, nu=nu, Gamma=1.0, tau_g=1.0, force_form=1)
+    return p, V, R
+
+
+def sample_clocks(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return
+    def reader():
+        for line in p.stdout:
+            out.append(line.strip())
+    th = threading.Thread(target=reader, daemon=True)
+    th.start()
+    stop.wait()
+    p.terminate()
+    th.join(timeout=2)
+
+
+def summarize_clocks(lines, gpu_index):
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        parts = [x.strip() for x in ln.split(",")]
+        if len(parts) < 8 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[4:8]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary
+    (profiles/fused_step_d3q27_fp32.json), or None."""
+    fn = os.path.join(ROOT, "profiles", "fused_step_d3q27_fp32.json")
+    try:
+        with open(fn) as fh:
+            d = json.load(fh)
+        return d.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        return None
+
+
+def run_gpu(args):
+    import torch
+    import paper_1710_07486_gb300 as tel
+    from paper_1710_07486_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = workload_c3(args.seed + rank, n=args.n)
+    T = tel.temperature_for_ratio(A_, B_, R_, w["ratio"])
+    rho_g, rho_l = tel.coexistence(A_, B_, R_, T)[:2]
+    p, V, R = c3_params(w, T, rho_g, rho_l)
+    n = w["n"]
+    rho, phi, u = inputs.off_centre_3d(args.seed + rank, n, rho_g, rho_l, p["chi"], V, w["B"], R=R)
+    lat = tel.Lattice(tel.D3Q27, n, n, n, dict(p, precision=tel.FP32_SHIFTED))
+    stream = torch.cuda.Stream()
+    lat.set_stream(stream)
+
+    # ---------------- device-resident timing
+    d_rho = torch.from_numpy(rho).cuda()
+    d_phi = torch.from_numpy(phi).cuda()
+    d_u = torch.from_numpy(np.ascontiguousarray(u.ravel())).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        lat.init_device(d_rho, d_phi, d_u)
+        lat.step(args.warmup)
+    stream.synchronize()
+    stop = threading.Event()
+    clk = []
+    th = threading.Thread(target=sample_clocks, args=(stop, clk), daemon=True)
+    th.start()
+    time.sleep(0.5)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        lat.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stop.set()
+    th.join(timeout=5)
+    status = "stable"
+    try:
+        lat.sync()
+    except tel.TelError as ex:
+        status = f"unstable: {ex}"
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    N = lat.N
+    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / args.steps
+    bpu = BYTES_PER_UPDATE[(1, 1)]
+    achieved = bpu * N / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = profiled_traffic()
+
+    # ---------------- end-to-end through the C ABI with host buffers
+    h_rho = torch.from_numpy(rho).pin_memory()
+    h_phi = torch.from_numpy(phi).pin_memory()
+    h_u = torch.from_numpy(np.ascontiguousarray(u.ravel())).pin_memory()
+    o_rho = torch.empty(N, dtype=torch.float64).pin_memory()
+    o_phi = torch.empty(N, dtype=torch.float64).pin_memory()
+    o_u = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+    import ctypes as C
+    L = tel.lib()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = L.tel_init(lat._h, C.c_void_p(h_rho.data_ptr()), C.c_void_p(h_phi.data_ptr()),
+                    C.c_void_p(h_u.data_ptr()))
+    for _ in range(args.steps):
+        rc |= L.tel_step(lat._h, 1)
+        rc |= (L.tel_sync(lat._h) if rc == 0 else rc)
+    rc |= L.tel_fields(lat._h, C.c_void_p(o_rho.data_ptr()), C.c_void_p(o_phi.data_ptr()),
+                       C.c_void_p(o_u.data_ptr()), None)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_mlups = N * args.steps * world / e2e_s / 1e6
+    h2d = (2 + 3) * N * 8 / args.steps
+    d2h = ((2 + 3) * N * 8 + 4 * args.steps) / args.steps
+
+    if rank == 0:
+        cpu = None if (args.no_cpu or world > 1) else cpu_baseline(args)
+        line = {
+            "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded drop collision; no dataset)",
+            "config": {"workload": f"D3Q27 {n}^3 periodic, density ratio 1000, FP32-shifted populations "
+                                   "with FP64 stabiliser and gas-side chemical potential, off-centre "
+                                   "collision of immiscible drops R=30",
+                       "lattice": "D3Q27", "nodes": N, "precision": "fp32_shifted+fp64_gamma_eos",
+                       "force_form": "lattice", "B": round(w["B"], 4), "We": round(w["We"], 3),
+                       "sigma12_over_sigma1g": w["sigma_ratio"], "seed": args.seed,
+                       "l2": "state 7.2 GB per step (read 3.6 GB + write 3.6 GB) > L2; no flush needed",
+                       "parallelism": f"replicas x{world}", "state_after_timed_steps": status},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                         "algorithmic_bytes_per_update": bpu},
+            "e2e": {"value": round(e2e_mlups, 2), "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "rc": int(rc)},
+            "gpu_launches": args.steps,
+            "clocks": summarize_clocks(clk, local),
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(args, steps=None, n=None):
+    """The FP64 CPU oracle as it stands, single-threaded, on a bounded sample:
+    the same collision scaled into a 64^3 periodic box (R = 7.5), 10 steps."""
+    from oracle import oracle as orc
+    from paper_1710_07486_gb300 import inputs
+    n = n or args.cpu_n
+    steps = steps or args.cpu_steps
+    w = workload_c3(args.seed, n=n)
+    T = orc.temperature_for_ratio(A_, B_, R_, w["ratio"])
+    rg, rl = orc.coexistence(A_, B_, R_, T)[:2]
+    p, V, R = c3_params(w, T, rg, rl)
+    o = orc.Oracle(orc.D3Q27, n, n, n, p)
+    rho, phi, u = inputs.off_centre_3d(args.seed, n, rg, rl, p["chi"], V, w["B"], R=R * n / 256.0)
+    f, g = o.init(rho, phi, u)
+    t0 = time.perf_counter()
+    o.step(f, g, steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(n ** 3 * steps / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"D3Q27 {n}^3 periodic box, same collision scaled (R={R * n / 256.0:g}), {steps} steps, "
+                      f"FP64, single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args, steps=1, n=args.ref_n)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args, steps=1, n=args.ref_n)["value"])
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded drop collision; no dataset)",
+            "config": {"workload": "D3Q27 ternary ELBM, density ratio 1000, off-centre drop collision "
+                                   f"(bounded sample: {args.ref_n}^3 box, 1 step per timed step)",
+                       "parallelism": "cpu, 1 thread"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"D3Q27 {args.ref_n}^3 periodic box, one step per timed step"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=1710)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--cpu-n", type=int, default=64)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--ref-n", type=int, default=48)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

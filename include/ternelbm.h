@@ -1,0 +1,161 @@
+/*
+ * ternelbm.h -- C ABI of libternelbm, a CUDA (sm_103a) implementation of the
+ * per-timestep lattice update of the ternary free-energy entropic lattice
+ * Boltzmann method of Woehrwag, Semprebon, Mazloomi M., Karlin and
+ * Kusumaatmaja, "Ternary free-energy entropic lattice Boltzmann model with
+ * high density ratio" (arXiv:1710.07486).
+ *
+ * The model (paper, Eqs. 1-8): one gas and two liquids described by the
+ * density rho and the phase field phi; bulk free energy of Eq. 2 with the
+ * Carnahan-Starling free energy of Eq. 4; square-gradient energy of Eqs. 3
+ * and 5; chemical potentials mu_rho = dF/drho, mu_phi = dF/dphi and pressure
+ * tensor with div P = rho grad mu_rho + phi grad mu_phi (text after Eq. 8).
+ * The density/momentum populations f use the entropic (KBC) collision with
+ * exact-difference forcing, the phase-field populations g a BGK collision
+ * (text after Eq. 8).  Lattices D2Q9 and D3Q27 (c_s^2 = 1/3), periodic or
+ * half-way bounce-back boundaries per axis.
+ *
+ * Conventions
+ *   - Node index n = x + nx*(y + ny*z), x fastest.  nz = 1 for D2Q9.
+ *   - Velocity i has c_i = (i%3 - 1, (i/3)%3 - 1, i/9 - 1) (the z component
+ *     only for D3Q27); the opposite of i is Q-1-i.
+ *   - Field arrays are FP64: rho[N], phi[N], u[D*N] component-major
+ *     (u[a*N + n]), p[N].  Population arrays are FP64 [Q][N].
+ *   - Host pointers are caller-owned and only read/written during the call;
+ *     nothing is retained.  "_device" entry points take caller-owned device
+ *     pointers on the context's device.
+ *   - The context owns all device memory it allocates (populations, double
+ *     buffered; scratch for fields and state conversion; an error word).
+ *   - All work is enqueued on the context's stream (default: a stream the
+ *     library creates; see tel_set_stream).  tel_step is asynchronous; host
+ *     entry points that return data synchronise the stream.
+ *
+ * Errors: every int-returning call returns TEL_OK (0) or a negative code;
+ * tel_last_error() gives a message for the last failing call on a context.
+ * A numerically unstable node (rho <= 0, a velocity component with
+ * |u| >= 1 or |u + F/rho| >= 1 where the entropic equilibrium is undefined,
+ * or a non-finite value) sets a device flag; it is reported as TEL_EUNSTABLE
+ * by the next synchronising call (tel_sync, tel_fields, tel_get_state).
+ */
+#ifndef TERNELBM_H
+#define TERNELBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TEL_OK 0
+#define TEL_EINVAL (-1)    /* bad lattice, size, pointer or parameter */
+#define TEL_ENOMEM (-2)    /* device allocation failed */
+#define TEL_ECUDA (-3)     /* CUDA runtime error (launch, copy, device) */
+#define TEL_EUNSTABLE (-4) /* the device flagged an unstable node */
+#define TEL_ESTATE (-5)    /* call out of order (e.g. step before init) */
+
+typedef enum { TEL_D2Q9 = 0, TEL_D3Q27 = 1 } tel_lattice;
+
+/* TEL_FP64: populations stored and updated in FP64.
+ * TEL_FP32_SHIFTED: populations stored in FP32 as f_i - w_i rho_ref (and
+ * g_i - w_i * 0); arithmetic in FP32 except the entropic stabiliser's
+ * scalar products and the gas-side (rho < sqrt(rho_g rho_l)) local chemical
+ * potentials, which are evaluated in FP64. */
+typedef enum { TEL_FP64 = 0, TEL_FP32_SHIFTED = 1 } tel_precision;
+
+typedef enum { TEL_PERIODIC = 0, TEL_BOUNCEBACK = 1 } tel_bc;
+
+/* Discretisation of the ideal-pressure part of the force
+ * F = -rho grad mu_rho - phi grad mu_phi + F_id:
+ *   TEL_FORCE_POTENTIAL: F_id = c_s^2 grad rho (isotropic gradient);
+ *   TEL_FORCE_LATTICE:   F_id = c_s^2 (3/2 G - 1/2 A[G]) + div(c_s^4 G G/(4 rho)),
+ *     G = grad rho, A[G]_a(x) = sum_i 3 w_i c_ia c_i.G(x - c_i): the form for
+ *     which a steady state of the update is the thermodynamic equilibrium to
+ *     the next order (see the oracle and design notes). */
+typedef enum { TEL_FORCE_POTENTIAL = 0, TEL_FORCE_LATTICE = 1 } tel_force_form;
+
+typedef struct {
+    double a, b, R, T;                /* Carnahan-Starling EOS, Eq. 4 (absolute T) */
+    double lambda1, lambda2, lambda3; /* Eq. 2 */
+    double kappa1, kappa2, kappa3;    /* Eq. 3 */
+    double chi;                       /* phase-field scale: minima at (rho_l, +-chi) */
+    double nu;                        /* kinematic viscosity; tau = 3 nu + 1/2, beta = 1/(2 tau) */
+    double Gamma, tau_g;              /* mobility M = Gamma (tau_g - 1/2) */
+    double rho_ref;                   /* FP32 shift density; <= 0 selects rho_g */
+    int precision;                    /* tel_precision */
+    int force_form;                   /* tel_force_form */
+    int bc[3];                        /* tel_bc per axis (bc[2] ignored for D2Q9) */
+} tel_params;
+
+typedef struct tel_ctx tel_ctx;
+
+/* Create a lattice of nx*ny*nz nodes on the current CUDA device.
+ * Validates the parameters (tau > 1/2, tau_g > 1/2, chi > 0, kappa >= 0,
+ * lambda >= 0, T below the critical temperature, every extent >= 4, nz == 1
+ * for D2Q9), solves the common-tangent construction for rho_g, rho_l
+ * (text after Eq. 4), allocates the double-buffered populations and returns
+ * the context in *out.  Errors: TEL_EINVAL, TEL_ENOMEM, TEL_ECUDA. */
+int tel_create(int lattice, int nx, int ny, int nz, const tel_params *params,
+               tel_ctx **out);
+
+/* Release all device memory and the library-created stream. NULL is a no-op. */
+void tel_destroy(tel_ctx *ctx);
+
+/* Message for the last failing call on ctx (or the last tel_create failure
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char *tel_last_error(const tel_ctx *ctx);
+
+/* Run subsequent work on a caller stream (a cudaStream_t, e.g. PyTorch's
+ * current stream); NULL returns to the library's own stream.  The caller
+ * keeps ownership of its stream. */
+int tel_set_stream(tel_ctx *ctx, void *cuda_stream);
+
+/* Initial state from host fields rho[N], phi[N], u[D*N] (u is the physical
+ * velocity): f = f^eq(rho, u - F/(2 rho)), g = g^eq(phi, mu_phi, u), placed
+ * so that the first step streams them onto their nodes (reading of the
+ * initialisation; the paper defers it to its supplement).  Synchronises. */
+int tel_init(tel_ctx *ctx, const double *rho, const double *phi, const double *u);
+
+/* As tel_init with device pointers (FP64, same layouts); asynchronous. */
+int tel_init_device(tel_ctx *ctx, const double *rho, const double *phi, const double *u);
+
+/* Advance nsteps time steps: per node pull-stream f and g, moments,
+ * chemical potentials (Eqs. 1-5) on the isotropic stencils, force,
+ * KBC collision with per-node stabiliser and exact-difference forcing for f,
+ * BGK for g.  One fused kernel launch per step.  Asynchronous.
+ * TEL_ESTATE before initialisation. */
+int tel_step(tel_ctx *ctx, int nsteps);
+
+/* Wait for the context's stream and report the device's instability flag
+ * (TEL_EUNSTABLE), then clear it. */
+int tel_sync(tel_ctx *ctx);
+
+/* Macroscopic fields of the current state, on the host: rho, phi, physical
+ * velocity u = (j + F/2)/rho [D*N], and (if p != NULL) the isotropic part of
+ * the pressure tensor p = rho mu_rho + phi mu_phi - f_B - f_I.  Any of rho,
+ * phi, u may be NULL to skip it.  Synchronises; reports TEL_EUNSTABLE. */
+int tel_fields(tel_ctx *ctx, double *rho, double *phi, double *u, double *p);
+
+/* As tel_fields into caller device buffers (any may be NULL); asynchronous. */
+int tel_fields_device(tel_ctx *ctx, double *rho, double *phi, double *u, double *p);
+
+/* Copy the state (post-collision populations, the arrays the next step
+ * streams from) to / from host FP64 arrays f[Q*N], g[Q*N].  In the FP32
+ * mode the shift is removed / applied.  tel_get_state synchronises. */
+int tel_get_state(tel_ctx *ctx, double *f, double *g);
+int tel_set_state(tel_ctx *ctx, const double *f, const double *g);
+
+/* Sizes and derived constants: out[0..9] = {D, Q, nx, ny, nz, N, rho_g,
+ * rho_l, mu_coex, p_coex}. */
+int tel_info(const tel_ctx *ctx, double out[10]);
+
+/* Context-free thermodynamics of the CS free energy (Eq. 4): coexistence
+ * out[4] = {rho_g, rho_l, mu_coex, p_coex} at temperature T, and the
+ * temperature at which rho_l/rho_g equals ratio.  TEL_EINVAL when there is
+ * no liquid-gas coexistence. */
+int tel_coexistence(double a, double b, double R, double T, double out[4]);
+int tel_temperature_for_ratio(double a, double b, double R, double ratio, double *T);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TERNELBM_H */

@@ -1,0 +1,225 @@
+"""Python binding of libternelbm: the ternary free-energy entropic lattice
+Boltzmann update of arXiv:1710.07486 on GB300 (sm_103a).
+
+Argument marshalling only: every step of the update runs in the CUDA kernels
+of ``libternelbm.so`` (C ABI in ``include/ternelbm.h``).  There is no CPU
+fallback: if the library cannot be built or loaded, ``lib()`` raises.
+
+PyTorch is optional and only used to hand device buffers and streams to the
+library (``init_device``, ``fields_device``, ``set_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = ["Lattice", "lib", "coexistence", "temperature_for_ratio", "TelError",
+           "D2Q9", "D3Q27", "FP64", "FP32_SHIFTED", "PERIODIC", "BOUNCEBACK",
+           "FORCE_POTENTIAL", "FORCE_LATTICE"]
+
+D2Q9, D3Q27 = 0, 1
+FP64, FP32_SHIFTED = 0, 1
+PERIODIC, BOUNCEBACK = 0, 1
+FORCE_POTENTIAL, FORCE_LATTICE = 0, 1
+
+TEL_OK, TEL_EINVAL, TEL_ENOMEM, TEL_ECUDA, TEL_EUNSTABLE, TEL_ESTATE = 0, -1, -2, -3, -4, -5
+_NAMES = {-1: "TEL_EINVAL", -2: "TEL_ENOMEM", -3: "TEL_ECUDA", -4: "TEL_EUNSTABLE", -5: "TEL_ESTATE"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libternelbm.so")
+
+
+class TelError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    """Mirror of ``tel_params``."""
+
+    _fields_ = [(n, C.c_double) for n in (
+        "a", "b", "R", "T", "lambda1", "lambda2", "lambda3", "kappa1", "kappa2",
+        "kappa3", "chi", "nu", "Gamma", "tau_g", "rho_ref")] + [
+        ("precision", C.c_int), ("force_form", C.c_int), ("bc", C.c_int * 3)]
+
+
+_lib = None
+SYMBOLS = ("tel_create", "tel_destroy", "tel_last_error", "tel_set_stream", "tel_init",
+           "tel_init_device", "tel_step", "tel_sync", "tel_fields", "tel_fields_device",
+           "tel_get_state", "tel_set_state", "tel_info", "tel_coexistence",
+           "tel_temperature_for_ratio")
+
+
+def lib(build: bool = True):
+    """Load libternelbm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libternelbm.so not found at {LIB_PATH}; run paper_1710_07486_gb300/build.py")
+    L = C.CDLL(LIB_PATH)
+    vp, d, i = C.c_void_p, C.c_double, C.c_int
+    dp = C.POINTER(C.c_double)
+    L.tel_create.argtypes = [i, i, i, i, C.POINTER(Params), C.POINTER(vp)]
+    L.tel_destroy.argtypes = [vp]
+    L.tel_destroy.restype = None
+    L.tel_last_error.argtypes = [vp]
+    L.tel_last_error.restype = C.c_char_p
+    L.tel_set_stream.argtypes = [vp, vp]
+    for name in ("tel_init", "tel_init_device"):
+        getattr(L, name).argtypes = [vp, vp, vp, vp]
+    L.tel_step.argtypes = [vp, i]
+    L.tel_sync.argtypes = [vp]
+    for name in ("tel_fields", "tel_fields_device"):
+        getattr(L, name).argtypes = [vp, vp, vp, vp, vp]
+    L.tel_get_state.argtypes = [vp, vp, vp]
+    L.tel_set_state.argtypes = [vp, vp, vp]
+    L.tel_info.argtypes = [vp, dp]
+    L.tel_coexistence.argtypes = [d, d, d, d, dp]
+    L.tel_temperature_for_ratio.argtypes = [d, d, d, d, dp]
+    for name in SYMBOLS:
+        if name not in ("tel_destroy", "tel_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def coexistence(a, b, R, T):
+    out = (C.c_double * 4)()
+    rc = lib().tel_coexistence(a, b, R, T, out)
+    if rc:
+        raise TelError(rc, f"no liquid-gas coexistence at T={T}")
+    return tuple(out)
+
+
+def temperature_for_ratio(a, b, R, ratio):
+    T = C.c_double()
+    rc = lib().tel_temperature_for_ratio(a, b, R, ratio, C.byref(T))
+    if rc:
+        raise TelError(rc, f"no temperature with density ratio {ratio}")
+    return T.value
+
+
+class Lattice:
+    """One lattice state on the current CUDA device.
+
+    ``params``: dict with a, b, R, T, lambda1..3, kappa1..3, chi, nu, Gamma,
+    tau_g and optionally rho_ref, precision, force_form, bc.
+    """
+
+    def __init__(self, lattice, nx, ny, nz=1, params=None, bc=None, precision=None,
+                 force_form=None):
+        p = dict(params or {})
+        if bc is not None:
+            p["bc"] = bc
+        if precision is not None:
+            p["precision"] = precision
+        if force_form is not None:
+            p["force_form"] = force_form
+        s = Params()
+        for k in ("a", "b", "R", "T", "lambda1", "lambda2", "lambda3", "kappa1", "kappa2",
+                  "kappa3", "chi", "nu", "Gamma", "tau_g"):
+            setattr(s, k, float(p[k]))
+        s.rho_ref = float(p.get("rho_ref", 0.0))
+        s.precision = int(p.get("precision", FP64))
+        s.force_form = int(p.get("force_form", FORCE_LATTICE))
+        bcs = tuple(p.get("bc", (0, 0, 0)))
+        for k in range(3):
+            s.bc[k] = int(bcs[k])
+        self._L = lib()
+        h = C.c_void_p()
+        rc = self._L.tel_create(int(lattice), int(nx), int(ny), int(nz), C.byref(s), C.byref(h))
+        if rc:
+            raise TelError(rc, self._L.tel_last_error(None).decode())
+        self._h = h
+        info = (C.c_double * 10)()
+        self._L.tel_info(self._h, info)
+        self.D, self.Q = int(info[0]), int(info[1])
+        self.nx, self.ny, self.nz = int(info[2]), int(info[3]), int(info[4])
+        self.N = int(info[5])
+        self.rho_g, self.rho_l, self.mu_coex, self.p_coex = info[6], info[7], info[8], info[9]
+        self.precision = s.precision
+        self.lattice = int(lattice)
+
+    # ------------------------------------------------------------------ utils
+    def _check(self, rc):
+        if rc:
+            raise TelError(rc, self._L.tel_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.tel_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f64(self, a, n):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.size != n:
+            raise ValueError(f"expected {n} values, got {a.size}")
+        return a
+
+    # --------------------------------------------------------------- host API
+    def init(self, rho, phi, u):
+        rho = self._f64(rho, self.N)
+        phi = self._f64(phi, self.N)
+        u = self._f64(u, self.D * self.N)
+        self._check(self._L.tel_init(self._h, _ptr(rho), _ptr(phi), _ptr(u)))
+
+    def step(self, n=1):
+        self._check(self._L.tel_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._L.tel_sync(self._h))
+
+    def fields(self, with_p=True):
+        rho = np.empty(self.N)
+        phi = np.empty(self.N)
+        u = np.empty((self.D, self.N))
+        p = np.empty(self.N) if with_p else None
+        self._check(self._L.tel_fields(self._h, _ptr(rho), _ptr(phi), _ptr(u), _ptr(p)))
+        return {"rho": rho, "phi": phi, "u": u, "p": p}
+
+    def get_state(self):
+        f = np.empty((self.Q, self.N))
+        g = np.empty((self.Q, self.N))
+        self._check(self._L.tel_get_state(self._h, _ptr(f), _ptr(g)))
+        return f, g
+
+    def set_state(self, f, g):
+        f = self._f64(f, self.Q * self.N)
+        g = self._f64(g, self.Q * self.N)
+        self._check(self._L.tel_set_state(self._h, _ptr(f), _ptr(g)))
+
+    # ------------------------------------------------------------- device API
+    def set_stream(self, stream=None):
+        """``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        raw = None
+        if stream is not None:
+            raw = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.tel_set_stream(self._h, C.c_void_p(raw) if raw else None))
+
+    def init_device(self, rho, phi, u):
+        """Device float64 tensors (torch) of N, N and D*N elements."""
+        for t, n in ((rho, self.N), (phi, self.N), (u, self.D * self.N)):
+            if t.numel() != n or not t.is_contiguous() or str(t.dtype) != "torch.float64" or not t.is_cuda:
+                raise ValueError("init_device wants contiguous CUDA float64 tensors")
+        self._check(self._L.tel_init_device(self._h, C.c_void_p(rho.data_ptr()),
+                                            C.c_void_p(phi.data_ptr()), C.c_void_p(u.data_ptr())))
+
+    def fields_device(self, rho=None, phi=None, u=None, p=None):
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(self._L.tel_fields_device(self._h, ptr(rho), ptr(phi), ptr(u), ptr(p)))

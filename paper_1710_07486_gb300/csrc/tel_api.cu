@@ -1,0 +1,480 @@
+// tel_api.cu -- host side of libternelbm: the C ABI declared in
+// include/ternelbm.h.  Validates parameters, solves the common-tangent
+// construction of the Carnahan-Starling free energy (text after Eq. 4 of
+// arXiv:1710.07486), owns the device state and launches the fused kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/ternelbm.h"
+#include "tel_kernels.cuh"
+
+struct tel_ctx {
+    int lattice, D, Q, nx, ny, nz;
+    long long N;
+    tel_params p;
+    tel::DevParams dp;
+    void *f[2], *g[2];
+    int cur;
+    unsigned *d_err;
+    unsigned *h_err;  // pinned
+    double *scratch;  // FP64 fields / state staging, lazily allocated
+    size_t scratch_elems;
+    cudaStream_t own_stream, stream;
+    int initialized;
+    char msg[512];
+};
+
+static char g_create_msg[512] = "";
+
+static int fail(tel_ctx *c, int code, const char *fmt, ...)
+{
+    char *dst = c ? c->msg : g_create_msg;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_OR_FAIL(ctx, expr)                                                              \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), TEL_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Carnahan-Starling thermodynamics (Eq. 4).  With eta = b rho / 4 the
+// pressure p = rho dPsi/drho - Psi is rho R T (1 + eta + eta^2 - eta^3)/(1 -
+// eta)^3 - a rho^2; the chemical potential m = dPsi~/drho is the derivative
+// of Eq. 4 with C = 0.  Coexistence: equal p and equal m.  Solved here by
+// bisection on the chemical potential (gas and liquid branches bracketed by
+// the spinodals, where dp/drho = 0), then Newton polishing of the 2x2 system.
+// ---------------------------------------------------------------------------
+namespace {
+struct CS {
+    double a, b, R, T;
+    double p(double r) const
+    {
+        const double e = 0.25 * b * r;
+        return r * R * T * (1 + e + e * e - e * e * e) / ((1 - e) * (1 - e) * (1 - e)) - a * r * r;
+    }
+    double m(double r) const  // dPsi~/drho
+    {
+        const double d = b * r - 4.0;
+        return -2.0 * a * r - 8.0 * R * T * (24.0 - 2.0 * b * r) / (d * d * d) + R * T * (std::log(r) + 1.0);
+    }
+    double dm(double r) const  // d2Psi~/drho2 (dp/drho = rho dm)
+    {
+        const double d = b * r - 4.0;
+        return -2.0 * a - 32.0 * R * T * b * (b * r - 16.0) / (d * d * d * d) + R * T / r;
+    }
+};
+
+// spinodals: the two roots of dm = 0 on (0, 4/b); returns false above T_c
+bool spinodals(const CS &s, double &s1, double &s2)
+{
+    const double hi = 0.999 * 4.0 / s.b;
+    const int M = 4000;
+    double prev = s.dm(1e-6 / s.b), x_prev = 1e-6 / s.b;
+    int found = 0;
+    double roots[2];
+    for (int k = 1; k <= M && found < 2; ++k) {
+        const double x = 1e-6 / s.b * std::pow(hi / (1e-6 / s.b), (double)k / M);
+        const double v = s.dm(x);
+        if ((prev > 0) != (v > 0)) {
+            double lo_ = x_prev, hi_ = x;
+            for (int it = 0; it < 200; ++it) {
+                const double mid = 0.5 * (lo_ + hi_);
+                if ((s.dm(mid) > 0) == (s.dm(lo_) > 0)) lo_ = mid; else hi_ = mid;
+            }
+            roots[found++] = 0.5 * (lo_ + hi_);
+        }
+        prev = v;
+        x_prev = x;
+    }
+    if (found < 2) return false;
+    s1 = roots[0];
+    s2 = roots[1];
+    return true;
+}
+
+// root of m(r) = target on a branch where m is increasing
+double m_root(const CS &s, double target, double lo, double hi)
+{
+    for (int it = 0; it < 300; ++it) {
+        const double mid = lo + 0.5 * (hi - lo);
+        if (mid <= lo || mid >= hi) break;
+        if (s.m(mid) < target) lo = mid; else hi = mid;
+    }
+    return lo + 0.5 * (hi - lo);
+}
+
+bool coexist(const CS &s, double out[4])
+{
+    double s1, s2;
+    if (!(s.a > 0 && s.b > 0 && s.R > 0 && s.T > 0)) return false;
+    if (!spinodals(s, s1, s2)) return false;
+    const double rmax = 0.999 * 4.0 / s.b;
+    // chemical potentials spanned by both branches
+    double mlo = s.m(s2), mhi = s.m(s1);
+    if (!(mhi > mlo)) return false;
+    double rg = 0, rl = 0;
+    for (int it = 0; it < 300; ++it) {
+        const double mu = 0.5 * (mlo + mhi);
+        if (mu <= mlo || mu >= mhi) break;
+        rg = m_root(s, mu, 1e-300, s1);
+        rl = m_root(s, mu, s2, rmax);
+        // too high a chemical potential leaves the liquid at the higher pressure
+        if (s.p(rl) > s.p(rg)) mhi = mu; else mlo = mu;
+    }
+    const double mu = 0.5 * (mlo + mhi);
+    rg = m_root(s, mu, 1e-300, s1);
+    rl = m_root(s, mu, s2, rmax);
+    // Newton polish on (m(rl) - m(rg), p(rl) - p(rg)) = 0
+    for (int it = 0; it < 4; ++it) {
+        const double F1 = s.m(rl) - s.m(rg), F2 = s.p(rl) - s.p(rg);
+        const double a11 = -s.dm(rg), a12 = s.dm(rl), a21 = -rg * s.dm(rg), a22 = rl * s.dm(rl);
+        const double det = a11 * a22 - a12 * a21;
+        if (!(std::fabs(det) > 0)) break;
+        const double drg = (F1 * a22 - F2 * a12) / det, drl = (a11 * F2 - a21 * F1) / det;
+        const double nrg = rg - drg, nrl = rl - drl;
+        if (!(nrg > 0 && nrg < s1 && nrl > s2 && nrl < rmax)) break;
+        rg = nrg;
+        rl = nrl;
+    }
+    out[0] = rg;
+    out[1] = rl;
+    out[2] = 0.5 * (s.m(rg) + s.m(rl));
+    out[3] = 0.5 * (s.p(rg) + s.p(rl));
+    return std::isfinite(out[0]) && std::isfinite(out[1]);
+}
+}  // namespace
+
+extern "C" int tel_coexistence(double a, double b, double R, double T, double out[4])
+{
+    if (!out) return TEL_EINVAL;
+    CS s{a, b, R, T};
+    return coexist(s, out) ? TEL_OK : TEL_EINVAL;
+}
+
+extern "C" int tel_temperature_for_ratio(double a, double b, double R, double ratio, double *T)
+{
+    if (!T || !(ratio > 1.0) || !(a > 0 && b > 0 && R > 0)) return TEL_EINVAL;
+    // bracket: a low temperature with a larger ratio, and one near T_c
+    double lo = 0.02 * a / (b * R), hi = lo, out[4];
+    {
+        CS s{a, b, R, lo};
+        if (!coexist(s, out) || out[1] / out[0] < ratio) return TEL_EINVAL;
+    }
+    // walk up until coexistence disappears or the ratio falls below target
+    for (double t = lo; t < 1.0 * a / (b * R); t *= 1.01) {
+        CS s{a, b, R, t};
+        if (!coexist(s, out) || out[1] / out[0] < ratio) { hi = t; break; }
+        lo = t;
+    }
+    if (!(hi > lo)) return TEL_EINVAL;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        CS s{a, b, R, mid};
+        if (coexist(s, out) && out[1] / out[0] > ratio) lo = mid; else hi = mid;
+    }
+    *T = 0.5 * (lo + hi);
+    return TEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
+{
+    if (lattice != TEL_D2Q9 && lattice != TEL_D3Q27) return fail(nullptr, TEL_EINVAL, "lattice must be 0 (D2Q9) or 1 (D3Q27)");
+    if (nx < 4 || ny < 4 || (lattice == TEL_D3Q27 && nz < 4))
+        return fail(nullptr, TEL_EINVAL, "every lattice extent must be >= 4 (got %d x %d x %d)", nx, ny, nz);
+    if (lattice == TEL_D2Q9 && nz != 1) return fail(nullptr, TEL_EINVAL, "nz must be 1 for D2Q9");
+    if (!p) return fail(nullptr, TEL_EINVAL, "params is NULL");
+    if (!(p->nu > 0) || !std::isfinite(p->nu)) return fail(nullptr, TEL_EINVAL, "nu must be > 0 (tau > 1/2)");
+    if (!(p->tau_g > 0.5) || !std::isfinite(p->tau_g)) return fail(nullptr, TEL_EINVAL, "tau_g must be > 1/2");
+    if (!(p->chi > 0)) return fail(nullptr, TEL_EINVAL, "chi must be > 0");
+    if (!(p->Gamma >= 0)) return fail(nullptr, TEL_EINVAL, "Gamma must be >= 0");
+    if (!(p->kappa1 >= 0 && p->kappa2 >= 0 && p->kappa3 >= 0)) return fail(nullptr, TEL_EINVAL, "kappa must be >= 0");
+    if (!(p->lambda1 >= 0 && p->lambda2 >= 0 && p->lambda3 >= 0)) return fail(nullptr, TEL_EINVAL, "lambda must be >= 0");
+    if (p->precision != TEL_FP64 && p->precision != TEL_FP32_SHIFTED) return fail(nullptr, TEL_EINVAL, "bad precision");
+    if (p->force_form != TEL_FORCE_POTENTIAL && p->force_form != TEL_FORCE_LATTICE) return fail(nullptr, TEL_EINVAL, "bad force_form");
+    for (int a = 0; a < 3; ++a)
+        if (p->bc[a] != TEL_PERIODIC && p->bc[a] != TEL_BOUNCEBACK) return fail(nullptr, TEL_EINVAL, "bad bc[%d]", a);
+    if (((long long)nx * ny * nz) > (1LL << 40)) return fail(nullptr, TEL_EINVAL, "lattice too large");
+    return TEL_OK;
+}
+
+extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params *params, tel_ctx **out)
+{
+    if (!out) return fail(nullptr, TEL_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(lattice, nx, ny, nz, params);
+    if (rc) return rc;
+    double co[4];
+    if (tel_coexistence(params->a, params->b, params->R, params->T, co) != TEL_OK)
+        return fail(nullptr, TEL_EINVAL, "no liquid-gas coexistence at T=%g (T must be below the critical temperature)",
+                    params->T);
+    tel_ctx *c = new (std::nothrow) tel_ctx();
+    if (!c) return fail(nullptr, TEL_ENOMEM, "host allocation failed");
+    std::memset(c, 0, sizeof(*c));
+    c->lattice = lattice;
+    c->D = lattice == TEL_D2Q9 ? 2 : 3;
+    c->Q = lattice == TEL_D2Q9 ? 9 : 27;
+    c->nx = nx; c->ny = ny; c->nz = lattice == TEL_D2Q9 ? 1 : nz;
+    c->N = (long long)nx * ny * c->nz;
+    c->p = *params;
+    if (lattice == TEL_D2Q9) c->p.bc[2] = TEL_PERIODIC;
+
+    tel::DevParams &d = c->dp;
+    const tel_params &p = c->p;
+    d.nx = nx; d.ny = ny; d.nz = c->nz;
+    for (int a = 0; a < 3; ++a) d.bc[a] = p.bc[a];
+    d.N = c->N;
+    d.chunk = lattice == TEL_D2Q9 ? 16 : 64;
+    d.force_form = p.force_form;
+    d.a = p.a; d.b = p.b; d.RT = p.R * p.T;
+    d.rho_g = co[0]; d.rho_l = co[1]; d.mu_coex = co[2]; d.p_coex = co[3];
+    const double Dl = co[0] - co[1];
+    d.lam1h = 0.5 * p.lambda1; d.lam2 = p.lambda2; d.lam3 = p.lambda3;
+    d.inv_Dl = 1.0 / Dl;
+    d.inv_chi = 1.0 / p.chi;
+    d.inv_2Dl = 1.0 / (2.0 * Dl);
+    d.inv_2chi = 1.0 / (2.0 * p.chi);
+    d.Kr = p.kappa1 + (p.kappa2 + p.kappa3) / (4.0 * Dl * Dl);
+    d.Kp = (p.kappa2 + p.kappa3) / (4.0 * p.chi * p.chi);
+    d.Kx = (p.kappa3 - p.kappa2) / (4.0 * p.chi * Dl);
+    d.AI = 0.5 * p.kappa1 + (p.kappa2 + p.kappa3) / (8.0 * Dl * Dl);
+    d.BI = (p.kappa2 + p.kappa3) / (8.0 * p.chi * p.chi);
+    d.XI = (p.kappa3 - p.kappa2) / (4.0 * p.chi * Dl);
+    d.rho_switch = std::sqrt(co[0] * co[1]);
+    const double tau = 3.0 * p.nu + 0.5;
+    d.beta = 1.0 / (2.0 * tau);
+    d.inv_beta = 2.0 * tau;
+    d.Gamma = p.Gamma;
+    d.inv_tau_g = 1.0 / p.tau_g;
+    d.rho_ref = p.precision == TEL_FP32_SHIFTED ? (p.rho_ref > 0 ? p.rho_ref : co[0]) : 0.0;
+    c->p.rho_ref = d.rho_ref;
+
+    const size_t es = p.precision == TEL_FP64 ? sizeof(double) : sizeof(float);
+    const size_t bytes = es * (size_t)c->Q * (size_t)c->N;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&c->f[k], bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&c->g[k], bytes);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->own_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->own_stream);
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        tel_destroy(c);
+        return fail(nullptr, oom ? TEL_ENOMEM : TEL_ECUDA, "device setup failed: %s", cudaGetErrorString(e));
+    }
+    c->stream = c->own_stream;
+    d.err = c->d_err;
+    *out = c;
+    return TEL_OK;
+}
+
+extern "C" void tel_destroy(tel_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < 2; ++k) {
+        if (c->f[k]) cudaFree(c->f[k]);
+        if (c->g[k]) cudaFree(c->g[k]);
+    }
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+extern "C" const char *tel_last_error(const tel_ctx *c) { return c ? c->msg : g_create_msg; }
+
+extern "C" int tel_set_stream(tel_ctx *c, void *s)
+{
+    if (!c) return TEL_EINVAL;
+    c->stream = s ? (cudaStream_t)s : c->own_stream;
+    return TEL_OK;
+}
+
+extern "C" int tel_info(const tel_ctx *c, double out[10])
+{
+    if (!c || !out) return TEL_EINVAL;
+    out[0] = c->D; out[1] = c->Q; out[2] = c->nx; out[3] = c->ny; out[4] = c->nz;
+    out[5] = (double)c->N; out[6] = c->dp.rho_g; out[7] = c->dp.rho_l; out[8] = c->dp.mu_coex; out[9] = c->dp.p_coex;
+    return TEL_OK;
+}
+
+static cudaError_t launch(tel_ctx *c, int mode, const tel::LaunchArgs &A)
+{
+    if (c->lattice == TEL_D2Q9) return tel::launch_d2q9(c->p.precision, mode, c->dp, A, c->stream);
+    return tel::launch_d3q27(c->p.precision, mode, c->dp, A, c->stream);
+}
+
+static int ensure_scratch(tel_ctx *c, size_t elems)
+{
+    if (c->scratch_elems >= elems) return TEL_OK;
+    if (c->scratch) {
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_elems = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->scratch, elems * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, TEL_ENOMEM, "scratch allocation of %zu doubles failed: %s", elems, cudaGetErrorString(e));
+    }
+    c->scratch_elems = elems;
+    return TEL_OK;
+}
+
+static int check_flag(tel_ctx *c)
+{
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    const unsigned f = *c->h_err;
+    if (f) {
+        CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+        return fail(c, TEL_EUNSTABLE, "unstable node(s) flagged on the device:%s%s%s",
+                    (f & tel::ERR_RHO) ? " non-positive density;" : "",
+                    (f & tel::ERR_VEL) ? " |u| or |u+F/rho| >= 1;" : "",
+                    (f & tel::ERR_NAN) ? " non-finite value;" : "");
+    }
+    return TEL_OK;
+}
+
+extern "C" int tel_init_device(tel_ctx *c, const double *rho, const double *phi, const double *u)
+{
+    if (!c) return TEL_EINVAL;
+    if (!rho || !phi || !u) return fail(c, TEL_EINVAL, "tel_init: rho, phi and u are required");
+    tel::LaunchArgs A{};
+    A.in_rho = rho; A.in_phi = phi; A.in_u = u;
+    A.fdst = c->f[c->cur]; A.gdst = c->g[c->cur];
+    CUDA_OR_FAIL(c, launch(c, tel::MODE_INIT, A));
+    c->initialized = 1;
+    return TEL_OK;
+}
+
+extern "C" int tel_init(tel_ctx *c, const double *rho, const double *phi, const double *u)
+{
+    if (!c) return TEL_EINVAL;
+    if (!rho || !phi || !u) return fail(c, TEL_EINVAL, "tel_init: rho, phi and u are required");
+    const size_t N = (size_t)c->N;
+    int rc = ensure_scratch(c, (size_t)(2 + c->D) * N);
+    if (rc) return rc;
+    double *d = c->scratch;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d + N, phi, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d + 2 * N, u, (size_t)c->D * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    rc = tel_init_device(c, d, d + N, d + 2 * N);
+    if (rc) return rc;
+    return check_flag(c);
+}
+
+extern "C" int tel_step(tel_ctx *c, int nsteps)
+{
+    if (!c) return TEL_EINVAL;
+    if (nsteps < 0) return fail(c, TEL_EINVAL, "nsteps must be >= 0");
+    if (!c->initialized) return fail(c, TEL_ESTATE, "tel_step before tel_init/tel_set_state");
+    for (int s = 0; s < nsteps; ++s) {
+        tel::LaunchArgs A{};
+        A.fsrc = c->f[c->cur]; A.gsrc = c->g[c->cur];
+        A.fdst = c->f[1 - c->cur]; A.gdst = c->g[1 - c->cur];
+        CUDA_OR_FAIL(c, launch(c, tel::MODE_STEP, A));
+        c->cur = 1 - c->cur;
+    }
+    return TEL_OK;
+}
+
+extern "C" int tel_sync(tel_ctx *c)
+{
+    if (!c) return TEL_EINVAL;
+    return check_flag(c);
+}
+
+extern "C" int tel_fields_device(tel_ctx *c, double *rho, double *phi, double *u, double *p)
+{
+    if (!c) return TEL_EINVAL;
+    if (!c->initialized) return fail(c, TEL_ESTATE, "tel_fields before tel_init/tel_set_state");
+    tel::LaunchArgs A{};
+    A.fsrc = c->f[c->cur]; A.gsrc = c->g[c->cur];
+    A.out_rho = rho; A.out_phi = phi; A.out_u = u; A.out_p = p;
+    CUDA_OR_FAIL(c, launch(c, tel::MODE_FIELDS, A));
+    return TEL_OK;
+}
+
+extern "C" int tel_fields(tel_ctx *c, double *rho, double *phi, double *u, double *p)
+{
+    if (!c) return TEL_EINVAL;
+    if (!c->initialized) return fail(c, TEL_ESTATE, "tel_fields before tel_init/tel_set_state");
+    const size_t N = (size_t)c->N;
+    int rc = ensure_scratch(c, (size_t)(3 + c->D) * N);
+    if (rc) return rc;
+    double *d = c->scratch;
+    rc = tel_fields_device(c, rho ? d : nullptr, phi ? d + N : nullptr, u ? d + 2 * N : nullptr,
+                           p ? d + (2 + c->D) * N : nullptr);
+    if (rc) return rc;
+    if (rho) CUDA_OR_FAIL(c, cudaMemcpyAsync(rho, d, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (phi) CUDA_OR_FAIL(c, cudaMemcpyAsync(phi, d + N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (u) CUDA_OR_FAIL(c, cudaMemcpyAsync(u, d + 2 * N, (size_t)c->D * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (p) CUDA_OR_FAIL(c, cudaMemcpyAsync(p, d + (2 + c->D) * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return check_flag(c);
+}
+
+extern "C" int tel_get_state(tel_ctx *c, double *f, double *g)
+{
+    if (!c || !f || !g) return c ? fail(c, TEL_EINVAL, "tel_get_state: NULL array") : TEL_EINVAL;
+    if (!c->initialized) return fail(c, TEL_ESTATE, "tel_get_state before tel_init/tel_set_state");
+    const size_t QN = (size_t)c->Q * (size_t)c->N;
+    if (c->p.precision == TEL_FP64) {
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(f, c->f[c->cur], QN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(g, c->g[c->cur], QN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        int rc = ensure_scratch(c, QN);
+        if (rc) return rc;
+        CUDA_OR_FAIL(c, tel::launch_state_to_f64(c->lattice, (const float *)c->f[c->cur], c->scratch, c->N, c->dp.rho_ref, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(f, c->scratch, QN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+        CUDA_OR_FAIL(c, tel::launch_state_to_f64(c->lattice, (const float *)c->g[c->cur], c->scratch, c->N, 0.0, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(g, c->scratch, QN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    return check_flag(c);
+}
+
+extern "C" int tel_set_state(tel_ctx *c, const double *f, const double *g)
+{
+    if (!c || !f || !g) return c ? fail(c, TEL_EINVAL, "tel_set_state: NULL array") : TEL_EINVAL;
+    const size_t QN = (size_t)c->Q * (size_t)c->N;
+    if (c->p.precision == TEL_FP64) {
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->f[c->cur], f, QN * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->g[c->cur], g, QN * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    } else {
+        int rc = ensure_scratch(c, QN);
+        if (rc) return rc;
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->scratch, f, QN * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CUDA_OR_FAIL(c, tel::launch_state_from_f64(c->lattice, c->scratch, (float *)c->f[c->cur], c->N, c->dp.rho_ref, c->stream));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->scratch, g, QN * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CUDA_OR_FAIL(c, tel::launch_state_from_f64(c->lattice, c->scratch, (float *)c->g[c->cur], c->N, 0.0, c->stream));
+    }
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    c->initialized = 1;
+    return TEL_OK;
+}

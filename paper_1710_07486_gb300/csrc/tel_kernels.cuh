@@ -1,0 +1,652 @@
+// tel_kernels.cuh -- the fused per-timestep kernel of the ternary free-energy
+// entropic lattice Boltzmann update (arXiv:1710.07486), D2Q9 and D3Q27,
+// FP64 or FP32-shifted storage.
+//
+// One launch advances every node by one time step.  A CTA owns a tile of
+// TX x TY nodes in the plane normal to the last axis (the "marching" axis: y
+// for D2Q9, z for D3Q27) and marches along that axis through a chunk of
+// planes.  Per plane it runs three phases, each in shared memory:
+//   A  moments rho, phi of plane m+2 on the tile plus a ring of 2 nodes,
+//      from populations pulled out of the source buffers;
+//   B  chemical potentials mu_rho, mu_phi (Eqs. 1-5) of plane m+1 on the tile
+//      plus a ring of 1 (isotropic Laplacians of the plane-m..m+2 moments),
+//      and, for the lattice-consistent force, grad rho there;
+//   C  for each node of plane m: the force, the KBC collision with per-node
+//      stabiliser and exact-difference forcing of f, the BGK collision of g,
+//      and the store of the post-collision populations to the destination
+//      buffers (pull streaming: the next step reads them at x + c_i).
+// So every population is read from HBM once (the ring pulls of phase A and
+// the second pull of phase C are served by L1/L2) and written once.
+//
+// The same template also initialises the state from fields (MODE_INIT) and
+// extracts the fields of the state (MODE_FIELDS).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tel {
+
+enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_FIELDS = 2 };
+
+// Error bits raised by the device (see TEL_EUNSTABLE).
+enum : unsigned { ERR_RHO = 1u, ERR_VEL = 2u, ERR_NAN = 4u };
+
+struct DevParams {
+    int nx, ny, nz;          // lattice extents (nz = 1 for D2Q9)
+    int bc[3];               // 0 periodic, 1 bounce-back walls at both ends
+    long long N;             // nodes
+    int chunk;               // planes per CTA along the marching axis
+    int force_form;          // 0 potential, 1 lattice-consistent
+    // Carnahan-Starling free energy, Eq. 4, shifted by the common tangent
+    double a, b, RT, mu_coex, p_coex;
+    double lam1h, lam2, lam3;         // lambda1/2, lambda2, lambda3
+    double rho_g, rho_l;
+    double inv_Dl;                    // 1/(rho_g - rho_l)
+    double inv_chi;                   // 1/chi
+    double inv_2Dl, inv_2chi;         // 1/(2 Delta), 1/(2 chi)
+    double Kr, Kp, Kx;                // Laplacian weights of mu (Eq. 5)
+    double AI, BI, XI;                // f_I = AI |grad rho|^2 + BI |grad phi|^2 + XI grad rho.grad phi
+    double rho_switch;                // FP32 mode: gas side is rho < rho_switch
+    // collision
+    double beta, inv_beta;            // beta = 1/(2 tau)
+    double Gamma, inv_tau_g;
+    double rho_ref;                   // FP32 shift (0 in FP64)
+    unsigned *err;                    // device error word
+};
+
+struct LaunchArgs {
+    const void *fsrc, *gsrc;                  // populations (step, fields)
+    void *fdst, *gdst;                        // populations (step, init)
+    const double *in_rho, *in_phi, *in_u;     // init
+    double *out_rho, *out_phi, *out_u, *out_p;// fields (nullable)
+};
+
+// ---------------------------------------------------------------------------
+// Lattice: c_i = (i%3 - 1, (i/3)%3 - 1, i/9 - 1); D2Q9 uses the first two.
+// The in-plane components are (X, Y) and the marching component is M:
+//   D2Q9: X = c_x, Y = 0, M = c_y;  D3Q27: X = c_x, Y = c_y, M = c_z.
+// ---------------------------------------------------------------------------
+template <int D> struct Lat {
+    static constexpr int Q = D == 2 ? 9 : 27;
+    static constexpr int REST = D == 2 ? 4 : 13;
+    __host__ __device__ static constexpr int cx(int i) { return i % 3 - 1; }
+    __host__ __device__ static constexpr int cy(int i) { return (i / 3) % 3 - 1; }
+    __host__ __device__ static constexpr int cz(int i) { return D == 2 ? 0 : i / 9 - 1; }
+    __host__ __device__ static constexpr int c(int i, int a) { return a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i)); }
+    __host__ __device__ static constexpr int pX(int i) { return cx(i); }
+    __host__ __device__ static constexpr int pY(int i) { return D == 2 ? 0 : cy(i); }
+    __host__ __device__ static constexpr int pM(int i) { return D == 2 ? cy(i) : cz(i); }
+    __host__ __device__ static constexpr int nnz(int i) { return (cx(i) != 0) + (cy(i) != 0) + (cz(i) != 0); }
+    // weights: D2Q9 {4/9, 1/9, 1/36}, D3Q27 {8/27, 2/27, 1/54, 1/216}
+    __host__ __device__ static constexpr double w(int i)
+    {
+        return D == 2 ? (nnz(i) == 0 ? 4.0 / 9 : (nnz(i) == 1 ? 1.0 / 9 : 1.0 / 36))
+                      : (nnz(i) == 0 ? 8.0 / 27 : (nnz(i) == 1 ? 2.0 / 27 : (nnz(i) == 2 ? 1.0 / 54 : 1.0 / 216)));
+    }
+};
+
+// Ghost/ring coordinate map: periodic axes wrap; on a bounce-back axis the
+// ghost beyond the half-way wall mirrors the fluid node (-1 -> 0, n -> n-1).
+__device__ __forceinline__ int map_coord(int q, int n, int wall)
+{
+    if (q >= 0 && q < n) return q;
+    if (!wall) {
+        q %= n;
+        return q < 0 ? q + n : q;
+    }
+    int p = 2 * n;
+    q %= p;
+    if (q < 0) q += p;
+    return q < n ? q : p - 1 - q;
+}
+
+template <typename T> __device__ __forceinline__ T sqrt_(T x);
+template <> __device__ __forceinline__ double sqrt_<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float sqrt_<float>(float x) { return sqrtf(x); }
+template <typename T> __device__ __forceinline__ T log_(T x);
+template <> __device__ __forceinline__ double log_<double>(double x) { return log(x); }
+template <> __device__ __forceinline__ float log_<float>(float x) { return logf(x); }
+
+// Local (gradient-free) parts of the chemical potentials at (rho, phi):
+//   mu_rho = lambda1/2 (dPsi~/drho - mu_coex) - (lambda2 w'(C1) + lambda3 w'(C2))/(2 Delta)
+//   mu_phi = (lambda2 w'(C1) - lambda3 w'(C2))/(2 chi),  w'(C) = C (1-C)(1-2C)
+// with dPsi~/drho = -2 a rho - 8RT (24 - 2 b rho)/(b rho - 4)^3 + RT (ln rho + 1).
+template <typename T>
+__device__ __forceinline__ void mu_local(const DevParams &P, T rho, T phi, T &mr, T &mp)
+{
+    const T br = (T)P.b * rho;
+    const T d = br - (T)4;
+    const T dpsi = (T)(-2.0 * P.a) * rho - (T)(8.0 * P.RT) * ((T)24 - (T)2 * br) / (d * d * d)
+                   + (T)P.RT * (log_<T>(rho) + (T)1) - (T)P.mu_coex;
+    const T s = (rho - (T)P.rho_l) * (T)P.inv_Dl;
+    const T pc = phi * (T)P.inv_chi;
+    const T c1 = (T)0.5 * ((T)1 + pc - s);
+    const T c2 = (T)0.5 * ((T)1 - pc - s);
+    const T w1 = c1 * ((T)1 - c1) * ((T)1 - (T)2 * c1);
+    const T w2 = c2 * ((T)1 - c2) * ((T)1 - (T)2 * c2);
+    mr = (T)P.lam1h * dpsi - ((T)P.lam2 * w1 + (T)P.lam3 * w2) * (T)P.inv_2Dl;
+    mp = ((T)P.lam2 * w1 - (T)P.lam3 * w2) * (T)P.inv_2chi;
+}
+
+// Bulk free energy f_B of Eq. 2 (Psi_eos - Psi_0 with the common tangent).
+__device__ __forceinline__ double f_bulk(const DevParams &P, double rho, double phi)
+{
+    const double br = P.b * rho, d = br - 4.0;
+    const double psi = rho * (-P.a * rho - 8.0 * P.RT * (br - 6.0) / (d * d) + P.RT * log(rho))
+                       - P.mu_coex * rho + P.p_coex;
+    const double s = (rho - P.rho_l) * P.inv_Dl, pc = phi * P.inv_chi;
+    const double c1 = 0.5 * (1.0 + pc - s), c2 = 0.5 * (1.0 - pc - s);
+    return P.lam1h * psi + 0.5 * P.lam2 * c1 * c1 * (1 - c1) * (1 - c1)
+           + 0.5 * P.lam3 * c2 * c2 * (1 - c2) * (1 - c2);
+}
+
+// One-dimensional factors of the entropic equilibrium, including the
+// one-dimensional weight: e[c+1] for c = -1, 0, 1 with
+//   e[1] = 2/3 (2 - S),  e[2] = 1/6 (2 - S)(S + 2u)/(1 - u),
+//   e[0] = 1/6 (2 - S)(S - 2u)/(1 + u),  S = sqrt(1 + 3u^2),
+// so that f^eq_i = rho prod_a e_a[c_ia + 1].
+template <typename T>
+__device__ __forceinline__ void eq_factors(T u, T e[3])
+{
+    const T S = sqrt_<T>((T)1 + (T)3 * u * u);
+    const T t = (T)2 - S;
+    e[1] = (T)(2.0 / 3.0) * t;
+    e[2] = (T)(1.0 / 6.0) * t * (S + (T)2 * u) / ((T)1 - u);
+    e[0] = (T)(1.0 / 6.0) * t * (S - (T)2 * u) / ((T)1 + u);
+}
+
+template <typename ST> struct StoreTraits;
+template <> struct StoreTraits<double> { typedef double CT; static constexpr bool shifted = false; };
+template <> struct StoreTraits<float> { typedef float CT; static constexpr bool shifted = true; };
+
+// ---------------------------------------------------------------------------
+// The fused kernel.
+// ---------------------------------------------------------------------------
+template <int D, int TX, int TY, typename ST, int MODE>
+struct Fused {
+    typedef Lat<D> L;
+    typedef typename StoreTraits<ST>::CT CT;
+    static constexpr int Q = L::Q;
+    static constexpr int NT = TX * TY;
+    static constexpr int R2X = TX + 4, R2Y = (D == 3 ? TY + 4 : 1), NA = R2X * R2Y;
+    static constexpr int R1X = TX + 2, R1Y = (D == 3 ? TY + 2 : 1), NB = R1X * R1Y;
+    static constexpr int OY2 = (D == 3 ? 2 : 0), OY1 = (D == 3 ? 1 : 0);
+
+    // shared memory layout (in CT units)
+    static constexpr int OFF_RHO = 0;
+    static constexpr int OFF_PHI = OFF_RHO + 5 * NA;
+    static constexpr int OFF_MR = OFF_PHI + 5 * NA;
+    static constexpr int OFF_MP = OFF_MR + 3 * NB;
+    static constexpr int OFF_G = OFF_MP + 3 * NB;
+    static constexpr int SMEM_ELEMS = OFF_G + 3 * D * NB;
+    static constexpr size_t SMEM_BYTES = sizeof(CT) * SMEM_ELEMS;
+
+    __device__ static __forceinline__ int idx2(int ox, int oy) { return (ox + 2) + R2X * (oy + OY2); }
+    __device__ static __forceinline__ int idx1(int ox, int oy) { return (ox + 1) + R1X * (oy + OY1); }
+    __device__ static __forceinline__ int slot5(int m) { int s = m % 5; return s < 0 ? s + 5 : s; }
+    __device__ static __forceinline__ int slot3(int m) { int s = m % 3; return s < 0 ? s + 3 : s; }
+
+    // global index of the population i pulled into node (x,y,m): the value
+    // post-collision at (x,y,m) - c_i, or the reversed population of the node
+    // itself when that source lies beyond a bounce-back wall.
+    __device__ static __forceinline__ long long pull_index(const DevParams &P, int PX, int PY, int PM,
+                                                           int x, int y, int m, long long n, int i)
+    {
+        int sx = x - L::pX(i), sy = y - L::pY(i), sm = m - L::pM(i);
+        const int bx = P.bc[0], by = (D == 3 ? P.bc[1] : 0), bm = (D == 3 ? P.bc[2] : P.bc[1]);
+        bool bb = false;
+        if (sx < 0) { if (bx) bb = true; else sx += PX; }
+        else if (sx >= PX) { if (bx) bb = true; else sx -= PX; }
+        if (D == 3) {
+            if (sy < 0) { if (by) bb = true; else sy += PY; }
+            else if (sy >= PY) { if (by) bb = true; else sy -= PY; }
+        }
+        if (sm < 0) { if (bm) bb = true; else sm += PM; }
+        else if (sm >= PM) { if (bm) bb = true; else sm -= PM; }
+        if (bb) return (long long)(Q - 1 - i) * P.N + n;
+        return (long long)i * P.N + (long long)sx + (long long)PX * ((long long)sy + (long long)PY * sm);
+    }
+
+    __device__ static void run(const DevParams P, const LaunchArgs A)
+    {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        CT *sm = reinterpret_cast<CT *>(smem_raw);
+        CT *rho_s = sm + OFF_RHO, *phi_s = sm + OFF_PHI, *mr_s = sm + OFF_MR, *mp_s = sm + OFF_MP;
+        CT *g_s = sm + OFF_G;
+
+        const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
+        const int bX = P.bc[0], bY = (D == 3 ? P.bc[1] : 0), bM = (D == 3 ? P.bc[2] : P.bc[1]);
+        const int tid = threadIdx.x;
+        const int x0 = blockIdx.x * TX;
+        const int y0 = (D == 3 ? blockIdx.y * TY : 0);
+        const int m0 = (D == 3 ? blockIdx.z : blockIdx.y) * P.chunk;
+        const int m1 = min(m0 + P.chunk, PM);
+        const CT shift = (CT)P.rho_ref;
+        const ST *fs = reinterpret_cast<const ST *>(A.fsrc);
+        const ST *gs = reinterpret_cast<const ST *>(A.gsrc);
+
+        const int iters = (m1 - m0) + 4;
+        for (int it = 0; it < iters; ++it) {
+            // ---------------- phase A: moments of plane mA on tile + ring 2
+            const int mA = m0 - 2 + it;
+            if (mA <= m1 + 1) {
+                const int mm = map_coord(mA, PM, bM);
+                CT *rs = rho_s + slot5(mA) * NA, *ps = phi_s + slot5(mA) * NA;
+                for (int r = tid; r < NA; r += NT) {
+                    const int ox = r % R2X - 2, oy = (D == 3 ? r / R2X - 2 : 0);
+                    const int xx = map_coord(x0 + ox, PX, bX);
+                    const int yy = (D == 3 ? map_coord(y0 + oy, PY, bY) : 0);
+                    const long long n = (long long)xx + (long long)PX * ((long long)yy + (long long)PY * mm);
+                    CT rho, phi;
+                    if (MODE == MODE_INIT) {
+                        rho = (CT)A.in_rho[n];
+                        phi = (CT)A.in_phi[n];
+                    } else {
+                        CT sr = 0, sp = 0;
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            const long long k = pull_index(P, PX, PY, PM, xx, yy, mm, n, i);
+                            sr += (CT)__ldg(fs + k);
+                        }
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            const long long k = pull_index(P, PX, PY, PM, xx, yy, mm, n, i);
+                            sp += (CT)__ldg(gs + k);
+                        }
+                        rho = StoreTraits<ST>::shifted ? shift + sr : sr;
+                        phi = sp;
+                    }
+                    rs[r] = rho;
+                    ps[r] = phi;
+                }
+            }
+            __syncthreads();
+            // ---------------- phase B: chemical potentials of plane mB on tile + ring 1
+            const int mB = mA - 1;
+            if (mB >= m0 - 1 && mB <= m1) {
+                const int sB = slot3(mB);
+                for (int s = tid; s < NB; s += NT) {
+                    const int ox = s % R1X - 1, oy = (D == 3 ? s / R1X - 1 : 0);
+                    const int c0 = idx2(ox, oy);
+                    const CT r0 = rho_s[slot5(mB) * NA + c0], p0 = phi_s[slot5(mB) * NA + c0];
+                    CT lr = 0, lp = 0, gx = 0, gy = 0, gz = 0;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const int k = slot5(mB + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i));
+                        const CT wi = (CT)L::w(i);
+                        const CT rv = rho_s[k];
+                        lr += wi * (rv - r0);
+                        lp += wi * (phi_s[k] - p0);
+                        if (L::cx(i)) gx += wi * (CT)L::cx(i) * rv;
+                        if (L::cy(i)) gy += wi * (CT)L::cy(i) * rv;
+                        if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * rv;
+                    }
+                    lr *= (CT)6;
+                    lp *= (CT)6;
+                    CT mr, mp;
+                    if (StoreTraits<ST>::shifted && r0 < (CT)P.rho_switch) {
+                        double mrd, mpd;
+                        mu_local<double>(P, (double)r0, (double)p0, mrd, mpd);
+                        mr = (CT)mrd;
+                        mp = (CT)mpd;
+                    } else {
+                        mu_local<CT>(P, r0, p0, mr, mp);
+                    }
+                    mr_s[sB * NB + s] = mr - (CT)P.Kr * lr - (CT)P.Kx * lp;
+                    mp_s[sB * NB + s] = mp - (CT)P.Kp * lp - (CT)P.Kx * lr;
+                    if (P.force_form == 1) {
+                        g_s[(sB * D + 0) * NB + s] = (CT)3 * gx;
+                        g_s[(sB * D + 1) * NB + s] = (CT)3 * gy;
+                        if (D == 3) g_s[(sB * D + 2) * NB + s] = (CT)3 * gz;
+                    }
+                }
+            }
+            __syncthreads();
+            // ---------------- phase C: collide plane mC
+            const int mC = mA - 2;
+            if (mC >= m0 && mC < m1) {
+                const int tx = tid % TX, ty = tid / TX;
+                const int x = x0 + tx, y = y0 + ty;
+                if (x < PX && (D == 2 || y < PY)) node(P, A, fs, gs, rho_s, phi_s, mr_s, mp_s, g_s, x, y, mC, tx, ty);
+            }
+        }
+    }
+
+    __device__ static void node(const DevParams &P, const LaunchArgs &A, const ST *fs, const ST *gs,
+                                const CT *rho_s, const CT *phi_s, const CT *mr_s, const CT *mp_s,
+                                const CT *g_s, int x, int y, int m, int tx, int ty)
+    {
+        const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
+        const long long n = (long long)x + (long long)PX * ((long long)y + (long long)PY * m);
+        const int ox = tx, oy = (D == 3 ? ty : 0);
+        const CT rho = rho_s[slot5(m) * NA + idx2(ox, oy)];
+        const CT phi = phi_s[slot5(m) * NA + idx2(ox, oy)];
+        const CT shift = (CT)P.rho_ref;
+
+        // gradients at the node: grad mu_rho, grad mu_phi (ring-1 tiles),
+        // grad rho and grad phi (ring-2 tiles)
+        CT gm[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, gr[3] = {0, 0, 0}, gf[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (L::nnz(i) == 0) continue;
+            const int k1 = slot3(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i));
+            const int k2 = slot5(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i));
+            const CT wi = (CT)L::w(i);
+            const CT vm = mr_s[k1], vp = mp_s[k1], vr = rho_s[k2], vf = phi_s[k2];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int ca = L::c(i, a);
+                if (ca) {
+                    gm[a] += wi * (CT)ca * vm;
+                    gp[a] += wi * (CT)ca * vp;
+                    gr[a] += wi * (CT)ca * vr;
+                    gf[a] += wi * (CT)ca * vf;
+                }
+            }
+        }
+        CT F[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            gm[a] *= (CT)3; gp[a] *= (CT)3; gr[a] *= (CT)3; gf[a] *= (CT)3;
+            F[a] = -rho * gm[a] - phi * gp[a];
+        }
+        const CT cs2 = (CT)(1.0 / 3.0);
+        if (P.force_form == 0) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) F[a] += cs2 * gr[a];
+        } else {
+            // A[G]_a = sum_i 3 w_i c_ia c_i.G(x - c_i);  div T with T = c_s^4 G G/(4 rho) at x + c_i
+            CT AG[3] = {0, 0, 0}, dT[3] = {0, 0, 0};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (L::nnz(i) == 0) continue;
+                const CT wi3 = (CT)(3.0 * L::w(i));
+                const int sm_ = slot3(m - L::pM(i));
+                const int km = idx1(ox - L::pX(i), oy - L::pY(i));
+                CT cG = 0;
+#pragma unroll
+                for (int b = 0; b < D; ++b)
+                    if (L::c(i, b)) cG += (CT)L::c(i, b) * g_s[(sm_ * D + b) * NB + km];
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    if (L::c(i, a)) AG[a] += wi3 * (CT)L::c(i, a) * cG;
+                const int sp_ = slot3(m + L::pM(i));
+                const int kp = idx1(ox + L::pX(i), oy + L::pY(i));
+                const CT rp = rho_s[slot5(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
+                CT Gp[3];
+#pragma unroll
+                for (int b = 0; b < D; ++b) Gp[b] = g_s[(sp_ * D + b) * NB + kp];
+                CT cGp = 0;
+#pragma unroll
+                for (int b = 0; b < D; ++b)
+                    if (L::c(i, b)) cGp += (CT)L::c(i, b) * Gp[b];
+                // sum_b c_ib T_ab = c_s^4 G_a (c.G) / (4 rho)
+                const CT q = wi3 * cs2 * cs2 * cGp / ((CT)4 * rp);
+#pragma unroll
+                for (int a = 0; a < D; ++a) dT[a] += q * Gp[a];
+            }
+            const CT *G0 = g_s;  // G at the node itself
+            const int s0 = slot3(m), k0 = idx1(ox, oy);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                F[a] += cs2 * ((CT)1.5 * G0[(s0 * D + a) * NB + k0] - (CT)0.5 * AG[a]) + dT[a];
+        }
+        const CT mu_phi = mp_s[slot3(m) * NB + idx1(ox, oy)];
+
+        if (MODE == MODE_INIT) {
+            init_node(P, A, n, x, y, m, rho, phi, mu_phi, F);
+            return;
+        }
+
+        // ---- pull f: momentum and second moments
+        CT f[Q];
+        CT fsum = 0;  // same summation order as phase A: equals rho - rho_ref
+        CT j[3] = {0, 0, 0};
+        CT Pi[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
+        const int PXl = PX, PYl = PY, PMl = PM;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const long long k = pull_index(P, PXl, PYl, PMl, x, y, m, n, i);
+            f[i] = (CT)__ldg(fs + k);
+            fsum += f[i];
+            if (L::cx(i)) { j[0] += (CT)L::cx(i) * f[i]; Pi[0] += f[i]; }
+            if (L::cy(i)) { j[1] += (CT)L::cy(i) * f[i]; Pi[1] += f[i]; }
+            if (D == 3 && L::cz(i)) { j[2] += (CT)L::cz(i) * f[i]; Pi[2] += f[i]; }
+            if (L::cx(i) * L::cy(i)) Pi[3] += (CT)(L::cx(i) * L::cy(i)) * f[i];
+            if (D == 3 && L::cx(i) * L::cz(i)) Pi[4] += (CT)(L::cx(i) * L::cz(i)) * f[i];
+            if (D == 3 && L::cy(i) * L::cz(i)) Pi[5] += (CT)(L::cy(i) * L::cz(i)) * f[i];
+        }
+        if (StoreTraits<ST>::shifted) {
+            // the shift w_i rho_ref adds rho_ref c_s^2 to each diagonal second moment
+            Pi[0] += shift * cs2; Pi[1] += shift * cs2; if (D == 3) Pi[2] += shift * cs2;
+        }
+        CT u[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) u[a] = j[a] / rho;
+
+        unsigned bad = 0;
+        if (!(rho > (CT)0)) bad |= ERR_RHO;
+
+        if (MODE == MODE_FIELDS) {
+            fields_node(P, A, n, rho, phi, j, F, gr, gf, mr_s[slot3(m) * NB + idx1(ox, oy)], mu_phi);
+            if (bad) atomicOr(P.err, bad);
+            return;
+        }
+
+        CT uF[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            uF[a] = u[a] + F[a] / rho;
+            if (!(fabs(u[a]) < (CT)1) || !(fabs(uF[a]) < (CT)1)) bad |= ERR_VEL;
+        }
+        // equilibrium factors at u and at u + F/rho
+        CT e[3][3], eF[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a < D) { eq_factors<CT>(u[a], e[a]); eq_factors<CT>(uF[a], eF[a]); }
+            else { e[a][0] = 0; e[a][1] = 1; e[a][2] = 0; eF[a][0] = 0; eF[a][1] = 1; eF[a][2] = 0; }
+        }
+        // second moments of f^eq from the factor moments M0 = sum e, M1 = sum c e, M2 = sum c^2 e
+        CT M0[3], M1[3], M2[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            M0[a] = e[a][0] + e[a][1] + e[a][2];
+            M1[a] = e[a][2] - e[a][0];
+            M2[a] = e[a][2] + e[a][0];
+        }
+        CT dPi[6];
+        dPi[0] = Pi[0] - rho * M2[0] * M0[1] * M0[2];
+        dPi[1] = Pi[1] - rho * M0[0] * M2[1] * M0[2];
+        dPi[2] = (D == 3) ? Pi[2] - rho * M0[0] * M0[1] * M2[2] : (CT)0;
+        dPi[3] = Pi[3] - rho * M1[0] * M1[1] * M0[2];
+        dPi[4] = (D == 3) ? Pi[4] - rho * M1[0] * M0[1] * M1[2] : (CT)0;
+        dPi[5] = (D == 3) ? Pi[5] - rho * M0[0] * M1[1] * M1[2] : (CT)0;
+        const CT tr = dPi[0] + dPi[1] + dPi[2];
+        const CT dev[3] = {dPi[0] - tr / (CT)D, dPi[1] - tr / (CT)D, dPi[2] - tr / (CT)D};
+
+        // entropic scalar products <ds|dh>, <dh|dh> (FP64 accumulation)
+        double sh = 0.0, hh = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
+            const CT dl = StoreTraits<ST>::shifted ? f[i] - (feq - (CT)L::w(i) * shift) : f[i] - feq;
+            const CT ds = ds_of(i, dev, dPi);
+            const CT dh = dl - ds;
+            const CT r = (CT)1 / feq;
+            sh += (double)(ds * dh * r);
+            hh += (double)(dh * dh * r);
+        }
+        const double rhod = (double)rho;
+        double gamma = 2.0;
+        if (hh > 1e-30 * rhod * rhod) gamma = P.inv_beta - (2.0 - P.inv_beta) * sh / hh;
+        if (!isfinite(gamma)) bad |= ERR_NAN;
+        const CT bet = (CT)P.beta, gb = (CT)(gamma * P.beta);
+        ST *fd = reinterpret_cast<ST *>(A.fdst);
+        // FP32 storage: the rest population closes the node's mass so that the
+        // stored set sums to the pulled mass; rounding of the other outputs
+        // is then unbiased and the total mass does not drift.
+        double others_out = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
+            const CT feqF = rho * eF[0][L::cx(i) + 1] * eF[1][L::cy(i) + 1] * eF[2][L::cz(i) + 1];
+            const CT dl = StoreTraits<ST>::shifted ? f[i] - (feq - (CT)L::w(i) * shift) : f[i] - feq;
+            const CT ds = ds_of(i, dev, dPi);
+            const CT dh = dl - ds;
+            const CT out = f[i] - ((CT)2 * bet * ds + gb * dh) + (feqF - feq);
+            if (StoreTraits<ST>::shifted && i == L::REST) continue;
+            if (StoreTraits<ST>::shifted) others_out += (double)(ST)out;
+            fd[(long long)i * P.N + n] = (ST)out;
+        }
+        if (StoreTraits<ST>::shifted) fd[(long long)L::REST * P.N + n] = (ST)((double)fsum - others_out);
+
+        // ---- phase field: BGK towards g^eq(phi, mu_phi, u_phys)
+        CT up[3] = {0, 0, 0};
+        CT uu = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) { up[a] = (j[a] + (CT)0.5 * F[a]) / rho; uu += up[a] * up[a]; }
+        const CT Gm3 = (CT)(3.0 * P.Gamma) * mu_phi;
+        CT others = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (i == L::REST) continue;
+            others += geq_of(i, Gm3, phi, up, uu);
+        }
+        const CT itg = (CT)P.inv_tau_g;
+        ST *gd = reinterpret_cast<ST *>(A.gdst);
+        double gothers = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (StoreTraits<ST>::shifted && i == L::REST) continue;
+            const CT ge = (i == L::REST) ? phi - others : geq_of(i, Gm3, phi, up, uu);
+            const long long k = pull_index(P, PXl, PYl, PMl, x, y, m, n, i);
+            const CT gi = (CT)__ldg(gs + k);
+            const ST go = (ST)(gi - (gi - ge) * itg);
+            if (StoreTraits<ST>::shifted) gothers += (double)go;
+            gd[(long long)i * P.N + n] = go;
+        }
+        // FP32 storage: the rest population closes the node's phase-field sum
+        if (StoreTraits<ST>::shifted) gd[(long long)L::REST * P.N + n] = (ST)((double)phi - gothers);
+        if (bad) atomicOr(P.err, bad);
+    }
+
+    // Delta s_i: the population vector whose natural moments vanish except
+    // the deviatoric second moments of Delta (dual basis of {1, c, c^2} per
+    // axis; trace left in the higher-order part).
+    __device__ static __forceinline__ CT ds_of(int i, const CT dev[3], const CT dPi[6])
+    {
+        const int k = L::nnz(i);
+        if (k == 1) {
+            if (L::cx(i)) return (CT)0.5 * dev[0];
+            if (L::cy(i)) return (CT)0.5 * dev[1];
+            return (CT)0.5 * dev[2];
+        }
+        if (k == 2) {
+            if (L::cz(i) == 0) return (CT)(0.25 * L::cx(i) * L::cy(i)) * dPi[3];
+            if (L::cy(i) == 0) return (CT)(0.25 * L::cx(i) * L::cz(i)) * dPi[4];
+            return (CT)(0.25 * L::cy(i) * L::cz(i)) * dPi[5];
+        }
+        return (CT)0;
+    }
+
+    // g^eq_i, i != rest: w_i [3 Gamma mu_phi + 3 phi c.u + phi (9/2 (c.u)^2 - 3/2 u.u)]
+    __device__ static __forceinline__ CT geq_of(int i, CT Gm3, CT phi, const CT up[3], CT uu)
+    {
+        CT cu = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (L::c(i, a)) cu += (CT)L::c(i, a) * up[a];
+        return (CT)L::w(i) * (Gm3 + (CT)3 * phi * cu + phi * ((CT)4.5 * cu * cu - (CT)1.5 * uu));
+    }
+
+    __device__ static void init_node(const DevParams &P, const LaunchArgs &A, long long n, int x, int y, int m,
+                                     CT rho, CT phi, CT mu_phi, const CT F[3])
+    {
+        const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
+        const CT shift = (CT)P.rho_ref;
+        CT u[3] = {0, 0, 0}, us[3] = {0, 0, 0}, uu = 0;
+        unsigned bad = 0;
+        if (!(rho > (CT)0)) bad |= ERR_RHO;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            u[a] = (CT)A.in_u[(long long)a * P.N + n];
+            us[a] = u[a] - F[a] / ((CT)2 * rho);
+            uu += u[a] * u[a];
+            if (!(fabs(us[a]) < (CT)1)) bad |= ERR_VEL;
+        }
+        CT e[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a < D) eq_factors<CT>(us[a], e[a]);
+            else { e[a][0] = 0; e[a][1] = 1; e[a][2] = 0; }
+        }
+        const CT Gm3 = (CT)(3.0 * P.Gamma) * mu_phi;
+        CT others = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (i != L::REST) others += geq_of(i, Gm3, phi, u, uu);
+        ST *fd = reinterpret_cast<ST *>(A.fdst);
+        ST *gd = reinterpret_cast<ST *>(A.gdst);
+        const int bx = P.bc[0], by = (D == 3 ? P.bc[1] : 0), bm = (D == 3 ? P.bc[2] : P.bc[1]);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
+            if (StoreTraits<ST>::shifted) feq -= (CT)L::w(i) * shift;
+            const CT ge = (i == L::REST) ? phi - others : geq_of(i, Gm3, phi, u, uu);
+            // place the value where the first pull of node n in direction i reads it
+            int sx = x - L::pX(i), sy = y - L::pY(i), sm = m - L::pM(i);
+            bool bb = false;
+            if (sx < 0) { if (bx) bb = true; else sx += PX; } else if (sx >= PX) { if (bx) bb = true; else sx -= PX; }
+            if (D == 3) { if (sy < 0) { if (by) bb = true; else sy += PY; } else if (sy >= PY) { if (by) bb = true; else sy -= PY; } }
+            if (sm < 0) { if (bm) bb = true; else sm += PM; } else if (sm >= PM) { if (bm) bb = true; else sm -= PM; }
+            const long long k = bb ? (long long)(Q - 1 - i) * P.N + n
+                                   : (long long)i * P.N + (long long)sx + (long long)PX * ((long long)sy + (long long)PY * sm);
+            fd[k] = (ST)feq;
+            gd[k] = (ST)ge;
+        }
+        if (bad) atomicOr(P.err, bad);
+    }
+
+    __device__ static void fields_node(const DevParams &P, const LaunchArgs &A, long long n, CT rho, CT phi,
+                                       const CT j[3], const CT F[3], const CT gr[3], const CT gf[3], CT mu_rho,
+                                       CT mu_phi)
+    {
+        if (A.out_rho) A.out_rho[n] = (double)rho;
+        if (A.out_phi) A.out_phi[n] = (double)phi;
+        if (A.out_u) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) A.out_u[(long long)a * P.N + n] = (double)((j[a] + (CT)0.5 * F[a]) / rho);
+        }
+        if (A.out_p) {
+            double rr = 0, pp = 0, rp = 0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                rr += (double)gr[a] * (double)gr[a];
+                pp += (double)gf[a] * (double)gf[a];
+                rp += (double)gr[a] * (double)gf[a];
+            }
+            const double fI = P.AI * rr + P.BI * pp + P.XI * rp;
+            A.out_p[n] = (double)rho * (double)mu_rho + (double)phi * (double)mu_phi
+                         - f_bulk(P, (double)rho, (double)phi) - fI;
+        }
+    }
+};
+
+template <int D, int TX, int TY, typename ST, int MODE>
+__global__ void __launch_bounds__(TX * TY) fused_kernel(const DevParams P, const LaunchArgs A)
+{
+    Fused<D, TX, TY, ST, MODE>::run(P, A);
+}
+
+// Tile shapes and launcher (defined per lattice in tel_d2q9.cu / tel_d3q27.cu).
+cudaError_t launch_d2q9(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s);
+cudaError_t launch_d3q27(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s);
+
+// Shift conversion of whole population arrays (FP32 mode state get/set).
+cudaError_t launch_state_to_f64(int lattice, const float *src, double *dst, long long N, double shift,
+                                cudaStream_t s);
+cudaError_t launch_state_from_f64(int lattice, const double *src, float *dst, long long N, double shift,
+                                  cudaStream_t s);
+
+}  // namespace tel
