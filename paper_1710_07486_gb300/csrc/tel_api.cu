@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -209,7 +210,7 @@ static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
     if (p->force_form != TEL_FORCE_POTENTIAL && p->force_form != TEL_FORCE_LATTICE) return fail(nullptr, TEL_EINVAL, "bad force_form");
     for (int a = 0; a < 3; ++a)
         if (p->bc[a] != TEL_PERIODIC && p->bc[a] != TEL_BOUNCEBACK) return fail(nullptr, TEL_EINVAL, "bad bc[%d]", a);
-    if (((long long)nx * ny * nz) > (1LL << 40)) return fail(nullptr, TEL_EINVAL, "lattice too large");
+    if (((long long)nx * ny * nz) >= (1LL << 31)) return fail(nullptr, TEL_EINVAL, "lattice too large (N must be < 2^31)");
     return TEL_OK;
 }
 
@@ -240,6 +241,10 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     for (int a = 0; a < 3; ++a) d.bc[a] = p.bc[a];
     d.N = c->N;
     d.chunk = lattice == TEL_D2Q9 ? 16 : 64;
+    if (const char *ev = std::getenv("TEL_CHUNK")) {  // tuning override: planes per CTA
+        const int v = std::atoi(ev);
+        if (v >= 1) d.chunk = v;
+    }
     d.force_form = p.force_form;
     d.a = p.a; d.b = p.b; d.RT = p.R * p.T;
     d.rho_g = co[0]; d.rho_l = co[1]; d.mu_coex = co[2]; d.p_coex = co[3];
@@ -256,6 +261,11 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     d.BI = (p.kappa2 + p.kappa3) / (8.0 * p.chi * p.chi);
     d.XI = (p.kappa3 - p.kappa2) / (4.0 * p.chi * Dl);
     d.rho_switch = std::sqrt(co[0] * co[1]);
+    d.inv_rho_g = 1.0 / co[0];
+    {
+        const double dg = p.b * co[0] - 4.0;
+        d.h_g = (24.0 - 2.0 * p.b * co[0]) / (dg * dg * dg);
+    }
     const double tau = 3.0 * p.nu + 0.5;
     d.beta = 1.0 / (2.0 * tau);
     d.inv_beta = 2.0 * tau;

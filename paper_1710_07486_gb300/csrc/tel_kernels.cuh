@@ -48,6 +48,8 @@ struct DevParams {
     double Kr, Kp, Kx;                // Laplacian weights of mu (Eq. 5)
     double AI, BI, XI;                // f_I = AI |grad rho|^2 + BI |grad phi|^2 + XI grad rho.grad phi
     double rho_switch;                // FP32 mode: gas side is rho < rho_switch
+    double inv_rho_g;                 // 1/rho_g
+    double h_g;                       // (24 - 2 b rho_g)/(b rho_g - 4)^3
     // collision
     double beta, inv_beta;            // beta = 1/(2 tau)
     double Gamma, inv_tau_g;
@@ -104,6 +106,16 @@ __device__ __forceinline__ int map_coord(int q, int n, int wall)
 template <typename T> __device__ __forceinline__ T sqrt_(T x);
 template <> __device__ __forceinline__ double sqrt_<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float sqrt_<float>(float x) { return sqrtf(x); }
+// s + c += v with Knuth's error-free two-sum (no reassociation, no FMA).
+template <typename T>
+__device__ __forceinline__ void two_sum_acc(T &s, T &c, T v)
+{
+    const T t = s + v;
+    const T bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+
 template <typename T> __device__ __forceinline__ T log_(T x);
 template <> __device__ __forceinline__ double log_<double>(double x) { return log(x); }
 template <> __device__ __forceinline__ float log_<float>(float x) { return logf(x); }
@@ -112,21 +124,52 @@ template <> __device__ __forceinline__ float log_<float>(float x) { return logf(
 //   mu_rho = lambda1/2 (dPsi~/drho - mu_coex) - (lambda2 w'(C1) + lambda3 w'(C2))/(2 Delta)
 //   mu_phi = (lambda2 w'(C1) - lambda3 w'(C2))/(2 chi),  w'(C) = C (1-C)(1-2C)
 // with dPsi~/drho = -2 a rho - 8RT (24 - 2 b rho)/(b rho - 4)^3 + RT (ln rho + 1).
+// mu_eos is the first (equation-of-state) term, mu_wells the rest.
 template <typename T>
-__device__ __forceinline__ void mu_local(const DevParams &P, T rho, T phi, T &mr, T &mp)
+__device__ __forceinline__ T mu_eos(const DevParams &P, T rho)
 {
     const T br = (T)P.b * rho;
     const T d = br - (T)4;
     const T dpsi = (T)(-2.0 * P.a) * rho - (T)(8.0 * P.RT) * ((T)24 - (T)2 * br) / (d * d * d)
                    + (T)P.RT * (log_<T>(rho) + (T)1) - (T)P.mu_coex;
+    return (T)P.lam1h * dpsi;
+}
+
+template <typename T>
+__device__ __forceinline__ void mu_wells(const DevParams &P, T rho, T phi, T &mr, T &mp)
+{
     const T s = (rho - (T)P.rho_l) * (T)P.inv_Dl;
     const T pc = phi * (T)P.inv_chi;
     const T c1 = (T)0.5 * ((T)1 + pc - s);
     const T c2 = (T)0.5 * ((T)1 - pc - s);
     const T w1 = c1 * ((T)1 - c1) * ((T)1 - (T)2 * c1);
     const T w2 = c2 * ((T)1 - c2) * ((T)1 - (T)2 * c2);
-    mr = (T)P.lam1h * dpsi - ((T)P.lam2 * w1 + (T)P.lam3 * w2) * (T)P.inv_2Dl;
+    mr = -((T)P.lam2 * w1 + (T)P.lam3 * w2) * (T)P.inv_2Dl;
     mp = ((T)P.lam2 * w1 - (T)P.lam3 * w2) * (T)P.inv_2chi;
+}
+
+// FP32-storage mode, gas side (rho < rho_switch): the equation-of-state part
+// of mu_rho in FP64 from its difference to the gas coexistence point, where
+// mu_coex = dPsi~/drho(rho_g):
+//   dPsi~(rho) - dPsi~(rho_g) = RT ln(rho/rho_g) - 8RT (h(rho) - h(rho_g)) - 2a (rho - rho_g),
+//   h(rho) = (24 - 2 b rho)/(b rho - 4)^3.
+// ln(rho/rho_g) = log1p((rho - rho_g)/rho_g) is well conditioned in FP32; the
+// rational difference and the combination are FP64, with 1/(b rho - 4)^3 from
+// an FP32 reciprocal refined by two Newton-Raphson steps in FP64
+// (r <- r (2 - d r), relative error ~1e-16).
+__device__ __forceinline__ float mu_eos_gas(const DevParams &P, float rho)
+{
+    const double t = (double)rho;
+    const double dg = t - P.rho_g;
+    const float L = log1pf((float)(dg * P.inv_rho_g));
+    const double d = P.b * t - 4.0;
+    const double d3 = d * d * d;
+    double r = (double)__frcp_rn((float)d3);
+    r = r * (2.0 - d3 * r);
+    r = r * (2.0 - d3 * r);
+    const double h = (24.0 - 2.0 * P.b * t) * r;
+    const double eos = P.RT * (double)L - 8.0 * P.RT * (h - P.h_g) - 2.0 * P.a * dg;
+    return (float)(P.lam1h * eos);
 }
 
 // Bulk free energy f_B of Eq. 2 (Psi_eos - Psi_0 with the common tangent).
@@ -187,25 +230,46 @@ struct Fused {
     __device__ static __forceinline__ int slot5(int m) { int s = m % 5; return s < 0 ? s + 5 : s; }
     __device__ static __forceinline__ int slot3(int m) { int s = m % 3; return s < 0 ? s + 3 : s; }
 
-    // global index of the population i pulled into node (x,y,m): the value
-    // post-collision at (x,y,m) - c_i, or the reversed population of the node
-    // itself when that source lies beyond a bounce-back wall.
-    __device__ static __forceinline__ long long pull_index(const DevParams &P, int PX, int PY, int PM,
-                                                           int x, int y, int m, long long n, int i)
+    // Sources of the populations pulled into node (x, y, m): per axis the
+    // source coordinate x - c for c = -1, 0, 1 (periodic wrap) as an offset,
+    // and a bit per (axis, c) when that source lies beyond a bounce-back wall
+    // (the node then takes its own reversed population, half-way bounce-back).
+    struct Nbr {
+        int n;                // node index (N < 2^31 is enforced at creation)
+        int off[3][3];        // [axis X, Y, M][c + 1]
+        unsigned out;         // bit 3*axis + (c + 1)
+    };
+
+    __device__ static __forceinline__ void make_nbr(const DevParams &P, int PX, int PY, int PM, int x, int y,
+                                                    int m, Nbr &b)
     {
-        int sx = x - L::pX(i), sy = y - L::pY(i), sm = m - L::pM(i);
         const int bx = P.bc[0], by = (D == 3 ? P.bc[1] : 0), bm = (D == 3 ? P.bc[2] : P.bc[1]);
-        bool bb = false;
-        if (sx < 0) { if (bx) bb = true; else sx += PX; }
-        else if (sx >= PX) { if (bx) bb = true; else sx -= PX; }
-        if (D == 3) {
-            if (sy < 0) { if (by) bb = true; else sy += PY; }
-            else if (sy >= PY) { if (by) bb = true; else sy -= PY; }
+        b.n = x + PX * (y + PY * m);
+        b.out = 0u;
+        const int q[3] = {x, y, m}, ext[3] = {PX, PY, PM}, wall[3] = {bx, by, bm};
+        const int stride[3] = {1, PX, PX * PY};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int c = -1; c <= 1; ++c) {
+                int sc = q[a] - c;
+                if (a == 1 && D == 2) sc = 0;
+                bool o = false;
+                if (sc < 0) { if (wall[a]) o = true; else sc += ext[a]; }
+                else if (sc >= ext[a]) { if (wall[a]) o = true; else sc -= ext[a]; }
+                b.off[a][c + 1] = sc * stride[a];
+                if (o) b.out |= 1u << (3 * a + c + 1);
+            }
         }
-        if (sm < 0) { if (bm) bb = true; else sm += PM; }
-        else if (sm >= PM) { if (bm) bb = true; else sm -= PM; }
-        if (bb) return (long long)(Q - 1 - i) * P.N + n;
-        return (long long)i * P.N + (long long)sx + (long long)PX * ((long long)sy + (long long)PY * sm);
+    }
+
+    // global index of population i pulled into the node described by b
+    __device__ static __forceinline__ long long src_index(const Nbr &b, long long N, int i)
+    {
+        const int cX = L::pX(i) + 1, cY = L::pY(i) + 1, cM = L::pM(i) + 1;
+        const unsigned mask = (1u << cX) | (D == 3 ? (1u << (3 + cY)) : 0u) | (1u << (6 + cM));
+        if (b.out & mask) return (long long)(Q - 1 - i) * N + b.n;
+        return (long long)i * N + (b.off[0][cX] + b.off[1][cY] + b.off[2][cM]);
     }
 
     __device__ static void run(const DevParams P, const LaunchArgs A)
@@ -237,23 +301,19 @@ struct Fused {
                     const int ox = r % R2X - 2, oy = (D == 3 ? r / R2X - 2 : 0);
                     const int xx = map_coord(x0 + ox, PX, bX);
                     const int yy = (D == 3 ? map_coord(y0 + oy, PY, bY) : 0);
-                    const long long n = (long long)xx + (long long)PX * ((long long)yy + (long long)PY * mm);
                     CT rho, phi;
                     if (MODE == MODE_INIT) {
+                        const long long n = (long long)xx + (long long)PX * ((long long)yy + (long long)PY * mm);
                         rho = (CT)A.in_rho[n];
                         phi = (CT)A.in_phi[n];
                     } else {
+                        Nbr nb;
+                        make_nbr(P, PX, PY, PM, xx, yy, mm, nb);
                         CT sr = 0, sp = 0;
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) {
-                            const long long k = pull_index(P, PX, PY, PM, xx, yy, mm, n, i);
-                            sr += (CT)__ldg(fs + k);
-                        }
+                        for (int i = 0; i < Q; ++i) sr += (CT)__ldg(fs + src_index(nb, P.N, i));
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) {
-                            const long long k = pull_index(P, PX, PY, PM, xx, yy, mm, n, i);
-                            sp += (CT)__ldg(gs + k);
-                        }
+                        for (int i = 0; i < Q; ++i) sp += (CT)__ldg(gs + src_index(nb, P.N, i));
                         rho = StoreTraits<ST>::shifted ? shift + sr : sr;
                         phi = sp;
                     }
@@ -285,14 +345,11 @@ struct Fused {
                     lr *= (CT)6;
                     lp *= (CT)6;
                     CT mr, mp;
-                    if (StoreTraits<ST>::shifted && r0 < (CT)P.rho_switch) {
-                        double mrd, mpd;
-                        mu_local<double>(P, (double)r0, (double)p0, mrd, mpd);
-                        mr = (CT)mrd;
-                        mp = (CT)mpd;
-                    } else {
-                        mu_local<CT>(P, r0, p0, mr, mp);
-                    }
+                    mu_wells<CT>(P, r0, p0, mr, mp);
+                    if (StoreTraits<ST>::shifted && r0 < (CT)P.rho_switch)
+                        mr = (CT)mu_eos_gas(P, (float)r0) + mr;  // FP64 gas side
+                    else
+                        mr = mu_eos<CT>(P, r0) + mr;
                     mr_s[sB * NB + s] = mr - (CT)P.Kr * lr - (CT)P.Kx * lp;
                     mp_s[sB * NB + s] = mp - (CT)P.Kp * lp - (CT)P.Kx * lr;
                     if (P.force_form == 1) {
@@ -400,15 +457,15 @@ struct Fused {
         }
 
         // ---- pull f: momentum and second moments
+        Nbr nb;
+        make_nbr(P, PX, PY, PM, x, y, m, nb);
         CT f[Q];
         CT fsum = 0;  // same summation order as phase A: equals rho - rho_ref
         CT j[3] = {0, 0, 0};
         CT Pi[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
-        const int PXl = PX, PYl = PY, PMl = PM;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const long long k = pull_index(P, PXl, PYl, PMl, x, y, m, n, i);
-            f[i] = (CT)__ldg(fs + k);
+            f[i] = (CT)__ldg(fs + src_index(nb, P.N, i));
             fsum += f[i];
             if (L::cx(i)) { j[0] += (CT)L::cx(i) * f[i]; Pi[0] += f[i]; }
             if (L::cy(i)) { j[1] += (CT)L::cy(i) * f[i]; Pi[1] += f[i]; }
@@ -464,9 +521,14 @@ struct Fused {
         dPi[5] = (D == 3) ? Pi[5] - rho * M0[0] * M1[1] * M1[2] : (CT)0;
         const CT tr = dPi[0] + dPi[1] + dPi[2];
         const CT dev[3] = {dPi[0] - tr / (CT)D, dPi[1] - tr / (CT)D, dPi[2] - tr / (CT)D};
+        CT sh_f = 0, hh_f = 0;
 
-        // entropic scalar products <ds|dh>, <dh|dh> (FP64 accumulation)
+        // entropic scalar products <ds|dh>, <dh|dh>: FP64 sums in FP64 storage;
+        // in FP32 storage the FP32 terms are summed with error-free
+        // transformations (Knuth's two-sum; the sum of the terms is exact to
+        // ~2^-48) and combined in FP64 below.
         double sh = 0.0, hh = 0.0;
+        CT shc = 0, hhc = 0;  // compensation terms (FP32 storage)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
@@ -474,8 +536,17 @@ struct Fused {
             const CT ds = ds_of(i, dev, dPi);
             const CT dh = dl - ds;
             const CT r = (CT)1 / feq;
-            sh += (double)(ds * dh * r);
-            hh += (double)(dh * dh * r);
+            if (StoreTraits<ST>::shifted) {
+                two_sum_acc<CT>(sh_f, shc, ds * dh * r);
+                two_sum_acc<CT>(hh_f, hhc, dh * dh * r);
+            } else {
+                sh += (double)(ds * dh * r);
+                hh += (double)(dh * dh * r);
+            }
+        }
+        if (StoreTraits<ST>::shifted) {
+            sh = (double)sh_f + (double)shc;
+            hh = (double)hh_f + (double)hhc;
         }
         const double rhod = (double)rho;
         double gamma = 2.0;
@@ -520,8 +591,7 @@ struct Fused {
         for (int i = 0; i < Q; ++i) {
             if (StoreTraits<ST>::shifted && i == L::REST) continue;
             const CT ge = (i == L::REST) ? phi - others : geq_of(i, Gm3, phi, up, uu);
-            const long long k = pull_index(P, PXl, PYl, PMl, x, y, m, n, i);
-            const CT gi = (CT)__ldg(gs + k);
+            const CT gi = (CT)__ldg(gs + src_index(nb, P.N, i));
             const ST go = (ST)(gi - (gi - ge) * itg);
             if (StoreTraits<ST>::shifted) gothers += (double)go;
             gd[(long long)i * P.N + n] = go;
@@ -633,8 +703,15 @@ struct Fused {
     }
 };
 
+// Minimum resident CTAs per SM requested from the register allocator.
+#ifndef TEL_MIN_BLOCKS_FP32
+#define TEL_MIN_BLOCKS_FP32 2
+#endif
+template <typename ST> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<float> { static constexpr int value = TEL_MIN_BLOCKS_FP32; };
+
 template <int D, int TX, int TY, typename ST, int MODE>
-__global__ void __launch_bounds__(TX * TY) fused_kernel(const DevParams P, const LaunchArgs A)
+__global__ void __launch_bounds__(TX * TY, MinBlocks<ST>::value) fused_kernel(const DevParams P, const LaunchArgs A)
 {
     Fused<D, TX, TY, ST, MODE>::run(P, A);
 }
