@@ -11,7 +11,7 @@
 #include <cstring>
 #include <new>
 
-#include "../../include/ternelbm.h"
+#include "ternelbm.h"
 #include "tel_kernels.cuh"
 
 struct tel_ctx {
@@ -193,6 +193,18 @@ extern "C" int tel_temperature_for_ratio(double a, double b, double R, double ra
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------
+template <typename T>
+static void fill_coef(const tel::DevParams &d, tel::Coef<T> &k)
+{
+    k.b = (T)d.b; k.a2 = (T)(-2.0 * d.a); k.RT8 = (T)(8.0 * d.RT); k.RT = (T)d.RT;
+    k.mu_coex = (T)d.mu_coex; k.lam1h = (T)d.lam1h;
+    k.rho_l = (T)d.rho_l; k.inv_Dl = (T)d.inv_Dl; k.inv_chi = (T)d.inv_chi;
+    k.lam2 = (T)d.lam2; k.lam3 = (T)d.lam3; k.inv_2Dl = (T)d.inv_2Dl; k.inv_2chi = (T)d.inv_2chi;
+    k.Kr = (T)d.Kr; k.Kp = (T)d.Kp; k.Kx = (T)d.Kx;
+    k.rho_switch = (T)d.rho_switch; k.rho_ref = (T)d.rho_ref;
+    k.beta = (T)d.beta; k.Gamma3 = (T)(3.0 * d.Gamma); k.inv_tau_g = (T)d.inv_tau_g;
+}
+
 static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
 {
     if (lattice != TEL_D2Q9 && lattice != TEL_D3Q27) return fail(nullptr, TEL_EINVAL, "lattice must be 0 (D2Q9) or 1 (D3Q27)");
@@ -240,7 +252,7 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     d.nx = nx; d.ny = ny; d.nz = c->nz;
     for (int a = 0; a < 3; ++a) d.bc[a] = p.bc[a];
     d.N = c->N;
-    d.chunk = lattice == TEL_D2Q9 ? 16 : 64;
+    d.chunk = 32;
     if (const char *ev = std::getenv("TEL_CHUNK")) {  // tuning override: planes per CTA
         const int v = std::atoi(ev);
         if (v >= 1) d.chunk = v;
@@ -273,6 +285,8 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     d.inv_tau_g = 1.0 / p.tau_g;
     d.rho_ref = p.precision == TEL_FP32_SHIFTED ? (p.rho_ref > 0 ? p.rho_ref : co[0]) : 0.0;
     c->p.rho_ref = d.rho_ref;
+    fill_coef(d, d.cf);
+    fill_coef(d, d.cd);
 
     const size_t es = p.precision == TEL_FP64 ? sizeof(double) : sizeof(float);
     const size_t bytes = es * (size_t)c->Q * (size_t)c->N;

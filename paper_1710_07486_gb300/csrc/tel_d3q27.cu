@@ -2,10 +2,17 @@
 // marching along z; also the FP32-shift conversions of whole state arrays.
 #include "tel_launch.cuh"
 
+#ifndef TEL_D3_TX
+#define TEL_D3_TX 32
+#endif
+#ifndef TEL_D3_TY
+#define TEL_D3_TY 8
+#endif
+
 namespace tel {
 cudaError_t launch_d3q27(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s)
 {
-    return launch_lattice<3, 32, 8>(precision, mode, P, A, s);
+    return launch_lattice<3, TEL_D3_TX, TEL_D3_TY>(precision, mode, P, A, s);
 }
 
 // f_i = fbar_i + w_i shift (shift = 0 for g)

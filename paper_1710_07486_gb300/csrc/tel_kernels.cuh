@@ -32,6 +32,17 @@ enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_FIELDS = 2 };
 // Error bits raised by the device (see TEL_EUNSTABLE).
 enum : unsigned { ERR_RHO = 1u, ERR_VEL = 2u, ERR_NAN = 4u };
 
+// Model coefficients in the compute precision (float copies for the FP32
+// path so that no double-to-float conversion runs on the slow FP64 pipe).
+template <typename T>
+struct Coef {
+    T b, a2, RT8, RT, mu_coex, lam1h;  // a2 = -2a, RT8 = 8RT
+    T rho_l, inv_Dl, inv_chi, lam2, lam3, inv_2Dl, inv_2chi;
+    T Kr, Kp, Kx;
+    T rho_switch, rho_ref;
+    T beta, Gamma3, inv_tau_g;         // Gamma3 = 3 Gamma
+};
+
 struct DevParams {
     int nx, ny, nz;          // lattice extents (nz = 1 for D2Q9)
     int bc[3];               // 0 periodic, 1 bounce-back walls at both ends
@@ -55,7 +66,13 @@ struct DevParams {
     double Gamma, inv_tau_g;
     double rho_ref;                   // FP32 shift (0 in FP64)
     unsigned *err;                    // device error word
+    Coef<float> cf;
+    Coef<double> cd;
 };
+
+template <typename T> __device__ __forceinline__ const Coef<T> &coef(const DevParams &P);
+template <> __device__ __forceinline__ const Coef<float> &coef<float>(const DevParams &P) { return P.cf; }
+template <> __device__ __forceinline__ const Coef<double> &coef<double>(const DevParams &P) { return P.cd; }
 
 struct LaunchArgs {
     const void *fsrc, *gsrc;                  // populations (step, fields)
@@ -128,24 +145,26 @@ template <> __device__ __forceinline__ float log_<float>(float x) { return logf(
 template <typename T>
 __device__ __forceinline__ T mu_eos(const DevParams &P, T rho)
 {
-    const T br = (T)P.b * rho;
+    const Coef<T> &K = coef<T>(P);
+    const T br = K.b * rho;
     const T d = br - (T)4;
-    const T dpsi = (T)(-2.0 * P.a) * rho - (T)(8.0 * P.RT) * ((T)24 - (T)2 * br) / (d * d * d)
-                   + (T)P.RT * (log_<T>(rho) + (T)1) - (T)P.mu_coex;
-    return (T)P.lam1h * dpsi;
+    const T dpsi = K.a2 * rho - K.RT8 * ((T)24 - (T)2 * br) / (d * d * d) + K.RT * (log_<T>(rho) + (T)1)
+                   - K.mu_coex;
+    return K.lam1h * dpsi;
 }
 
 template <typename T>
 __device__ __forceinline__ void mu_wells(const DevParams &P, T rho, T phi, T &mr, T &mp)
 {
-    const T s = (rho - (T)P.rho_l) * (T)P.inv_Dl;
-    const T pc = phi * (T)P.inv_chi;
+    const Coef<T> &K = coef<T>(P);
+    const T s = (rho - K.rho_l) * K.inv_Dl;
+    const T pc = phi * K.inv_chi;
     const T c1 = (T)0.5 * ((T)1 + pc - s);
     const T c2 = (T)0.5 * ((T)1 - pc - s);
     const T w1 = c1 * ((T)1 - c1) * ((T)1 - (T)2 * c1);
     const T w2 = c2 * ((T)1 - c2) * ((T)1 - (T)2 * c2);
-    mr = -((T)P.lam2 * w1 + (T)P.lam3 * w2) * (T)P.inv_2Dl;
-    mp = ((T)P.lam2 * w1 - (T)P.lam3 * w2) * (T)P.inv_2chi;
+    mr = -(K.lam2 * w1 + K.lam3 * w2) * K.inv_2Dl;
+    mp = (K.lam2 * w1 - K.lam3 * w2) * K.inv_2chi;
 }
 
 // FP32-storage mode, gas side (rho < rho_switch): the equation-of-state part
@@ -222,7 +241,8 @@ struct Fused {
     static constexpr int OFF_MR = OFF_PHI + 5 * NA;
     static constexpr int OFF_MP = OFF_MR + 3 * NB;
     static constexpr int OFF_G = OFF_MP + 3 * NB;
-    static constexpr int SMEM_ELEMS = OFF_G + 3 * D * NB;
+    static constexpr int OFF_F = OFF_G + 3 * D * NB;   // per-thread population stash [Q][NT]
+    static constexpr int SMEM_ELEMS = OFF_F + (MODE == MODE_STEP ? Q * NT : 0);
     static constexpr size_t SMEM_BYTES = sizeof(CT) * SMEM_ELEMS;
 
     __device__ static __forceinline__ int idx2(int ox, int oy) { return (ox + 2) + R2X * (oy + OY2); }
@@ -286,7 +306,7 @@ struct Fused {
         const int y0 = (D == 3 ? blockIdx.y * TY : 0);
         const int m0 = (D == 3 ? blockIdx.z : blockIdx.y) * P.chunk;
         const int m1 = min(m0 + P.chunk, PM);
-        const CT shift = (CT)P.rho_ref;
+        const CT shift = coef<CT>(P).rho_ref;
         const ST *fs = reinterpret_cast<const ST *>(A.fsrc);
         const ST *gs = reinterpret_cast<const ST *>(A.gsrc);
 
@@ -346,12 +366,12 @@ struct Fused {
                     lp *= (CT)6;
                     CT mr, mp;
                     mu_wells<CT>(P, r0, p0, mr, mp);
-                    if (StoreTraits<ST>::shifted && r0 < (CT)P.rho_switch)
+                    if (StoreTraits<ST>::shifted && r0 < coef<CT>(P).rho_switch)
                         mr = (CT)mu_eos_gas(P, (float)r0) + mr;  // FP64 gas side
                     else
                         mr = mu_eos<CT>(P, r0) + mr;
-                    mr_s[sB * NB + s] = mr - (CT)P.Kr * lr - (CT)P.Kx * lp;
-                    mp_s[sB * NB + s] = mp - (CT)P.Kp * lp - (CT)P.Kx * lr;
+                    mr_s[sB * NB + s] = mr - coef<CT>(P).Kr * lr - coef<CT>(P).Kx * lp;
+                    mp_s[sB * NB + s] = mp - coef<CT>(P).Kp * lp - coef<CT>(P).Kx * lr;
                     if (P.force_form == 1) {
                         g_s[(sB * D + 0) * NB + s] = (CT)3 * gx;
                         g_s[(sB * D + 1) * NB + s] = (CT)3 * gy;
@@ -365,21 +385,23 @@ struct Fused {
             if (mC >= m0 && mC < m1) {
                 const int tx = tid % TX, ty = tid / TX;
                 const int x = x0 + tx, y = y0 + ty;
-                if (x < PX && (D == 2 || y < PY)) node(P, A, fs, gs, rho_s, phi_s, mr_s, mp_s, g_s, x, y, mC, tx, ty);
+                if (x < PX && (D == 2 || y < PY))
+                    node(P, A, fs, gs, rho_s, phi_s, mr_s, mp_s, g_s, sm + OFF_F + tid, x, y, mC, tx, ty);
             }
         }
     }
 
     __device__ static void node(const DevParams &P, const LaunchArgs &A, const ST *fs, const ST *gs,
                                 const CT *rho_s, const CT *phi_s, const CT *mr_s, const CT *mp_s,
-                                const CT *g_s, int x, int y, int m, int tx, int ty)
+                                const CT *g_s, CT *fq, int x, int y, int m, int tx, int ty)
     {
         const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
         const long long n = (long long)x + (long long)PX * ((long long)y + (long long)PY * m);
         const int ox = tx, oy = (D == 3 ? ty : 0);
         const CT rho = rho_s[slot5(m) * NA + idx2(ox, oy)];
         const CT phi = phi_s[slot5(m) * NA + idx2(ox, oy)];
-        const CT shift = (CT)P.rho_ref;
+        const Coef<CT> &K = coef<CT>(P);
+        const CT shift = K.rho_ref;
 
         // gradients at the node: grad mu_rho, grad mu_phi (ring-1 tiles),
         // grad rho and grad phi (ring-2 tiles)
@@ -456,23 +478,25 @@ struct Fused {
             return;
         }
 
-        // ---- pull f: momentum and second moments
+        // ---- pull f: momentum and second moments.  The pulled populations
+        // are kept in this thread's column of shared memory (fq[i * NT]) for
+        // the two later passes instead of 27 registers.
         Nbr nb;
         make_nbr(P, PX, PY, PM, x, y, m, nb);
-        CT f[Q];
         CT fsum = 0;  // same summation order as phase A: equals rho - rho_ref
         CT j[3] = {0, 0, 0};
         CT Pi[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f[i] = (CT)__ldg(fs + src_index(nb, P.N, i));
-            fsum += f[i];
-            if (L::cx(i)) { j[0] += (CT)L::cx(i) * f[i]; Pi[0] += f[i]; }
-            if (L::cy(i)) { j[1] += (CT)L::cy(i) * f[i]; Pi[1] += f[i]; }
-            if (D == 3 && L::cz(i)) { j[2] += (CT)L::cz(i) * f[i]; Pi[2] += f[i]; }
-            if (L::cx(i) * L::cy(i)) Pi[3] += (CT)(L::cx(i) * L::cy(i)) * f[i];
-            if (D == 3 && L::cx(i) * L::cz(i)) Pi[4] += (CT)(L::cx(i) * L::cz(i)) * f[i];
-            if (D == 3 && L::cy(i) * L::cz(i)) Pi[5] += (CT)(L::cy(i) * L::cz(i)) * f[i];
+            const CT fi = (CT)__ldg(fs + src_index(nb, P.N, i));
+            if (MODE == MODE_STEP) fq[i * NT] = fi;
+            fsum += fi;
+            if (L::cx(i)) { j[0] += (CT)L::cx(i) * fi; Pi[0] += fi; }
+            if (L::cy(i)) { j[1] += (CT)L::cy(i) * fi; Pi[1] += fi; }
+            if (D == 3 && L::cz(i)) { j[2] += (CT)L::cz(i) * fi; Pi[2] += fi; }
+            if (L::cx(i) * L::cy(i)) Pi[3] += (CT)(L::cx(i) * L::cy(i)) * fi;
+            if (D == 3 && L::cx(i) * L::cz(i)) Pi[4] += (CT)(L::cx(i) * L::cz(i)) * fi;
+            if (D == 3 && L::cy(i) * L::cz(i)) Pi[5] += (CT)(L::cy(i) * L::cz(i)) * fi;
         }
         if (StoreTraits<ST>::shifted) {
             // the shift w_i rho_ref adds rho_ref c_s^2 to each diagonal second moment
@@ -490,6 +514,34 @@ struct Fused {
             if (bad) atomicOr(P.err, bad);
             return;
         }
+
+        // ---- phase field first (its pulls reuse the offsets just computed):
+        // BGK towards g^eq(phi, mu_phi, u_phys)
+        CT up[3] = {0, 0, 0};
+        CT uu = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) { up[a] = (j[a] + (CT)0.5 * F[a]) / rho; uu += up[a] * up[a]; }
+        const CT Gm3 = K.Gamma3 * mu_phi;
+        CT others = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (i == L::REST) continue;
+            others += geq_of(i, Gm3, phi, up, uu);
+        }
+        const CT itg = K.inv_tau_g;
+        ST *gd = reinterpret_cast<ST *>(A.gdst);
+        CT goth = 0, gothc = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (StoreTraits<ST>::shifted && i == L::REST) continue;
+            const CT ge = (i == L::REST) ? phi - others : geq_of(i, Gm3, phi, up, uu);
+            const CT gi = (CT)__ldg(gs + src_index(nb, P.N, i));
+            const CT go = gi - (gi - ge) * itg;
+            if (StoreTraits<ST>::shifted) two_sum_acc<CT>(goth, gothc, (CT)(ST)go);
+            gd[(long long)i * P.N + n] = (ST)go;
+        }
+        // FP32 storage: the rest population closes the node's phase-field sum
+        if (StoreTraits<ST>::shifted) gd[(long long)L::REST * P.N + n] = (ST)((phi - goth) - gothc);
 
         CT uF[3] = {0, 0, 0};
 #pragma unroll
@@ -521,83 +573,67 @@ struct Fused {
         dPi[5] = (D == 3) ? Pi[5] - rho * M0[0] * M1[1] * M1[2] : (CT)0;
         const CT tr = dPi[0] + dPi[1] + dPi[2];
         const CT dev[3] = {dPi[0] - tr / (CT)D, dPi[1] - tr / (CT)D, dPi[2] - tr / (CT)D};
-        CT sh_f = 0, hh_f = 0;
 
-        // entropic scalar products <ds|dh>, <dh|dh>: FP64 sums in FP64 storage;
-        // in FP32 storage the FP32 terms are summed with error-free
-        // transformations (Knuth's two-sum; the sum of the terms is exact to
-        // ~2^-48) and combined in FP64 below.
-        double sh = 0.0, hh = 0.0;
-        CT shc = 0, hhc = 0;  // compensation terms (FP32 storage)
+        // entropic scalar products <ds|dh>, <dh|dh>.  FP64 storage: FP64
+        // sums.  FP32 storage: the FP32 terms are summed with Knuth's
+        // error-free two-sum (the sum of the terms exact to ~2^-48).
+        double shd = 0.0, hhd = 0.0;
+        CT sh = 0, hh = 0, shc = 0, hhc = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
+            const CT fi = fq[i * NT];
             const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
-            const CT dl = StoreTraits<ST>::shifted ? f[i] - (feq - (CT)L::w(i) * shift) : f[i] - feq;
+            const CT dl = StoreTraits<ST>::shifted ? fi - (feq - (CT)L::w(i) * shift) : fi - feq;
             const CT ds = ds_of(i, dev, dPi);
             const CT dh = dl - ds;
-            const CT r = (CT)1 / feq;
             if (StoreTraits<ST>::shifted) {
-                two_sum_acc<CT>(sh_f, shc, ds * dh * r);
-                two_sum_acc<CT>(hh_f, hhc, dh * dh * r);
+                const CT r = __frcp_rn((float)feq);
+                two_sum_acc<CT>(sh, shc, ds * dh * r);
+                two_sum_acc<CT>(hh, hhc, dh * dh * r);
             } else {
-                sh += (double)(ds * dh * r);
-                hh += (double)(dh * dh * r);
+                const CT r = (CT)1 / feq;
+                shd += (double)(ds * dh * r);
+                hhd += (double)(dh * dh * r);
             }
         }
-        if (StoreTraits<ST>::shifted) {
-            sh = (double)sh_f + (double)shc;
-            hh = (double)hh_f + (double)hhc;
-        }
-        const double rhod = (double)rho;
+        // stabiliser gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh> in FP64
+        // (FP32 storage: from the two compensated FP32 sums, with 1/<dh|dh> an
+        // FP32 reciprocal refined by one Newton-Raphson step in FP64)
         double gamma = 2.0;
-        if (hh > 1e-30 * rhod * rhod) gamma = P.inv_beta - (2.0 - P.inv_beta) * sh / hh;
+        if (StoreTraits<ST>::shifted) {
+            const CT shs = sh + shc, hhs = hh + hhc;
+            if (hhs > (CT)1e-30 * rho * rho) {
+                const double H = (double)hhs;
+                double rH = (double)__frcp_rn((float)hhs);
+                rH = rH * (2.0 - H * rH);
+                gamma = P.inv_beta - (2.0 - P.inv_beta) * ((double)shs * rH);
+            }
+        } else {
+            const double rhod = (double)rho;
+            if (hhd > 1e-30 * rhod * rhod) gamma = P.inv_beta - (2.0 - P.inv_beta) * shd / hhd;
+        }
         if (!isfinite(gamma)) bad |= ERR_NAN;
-        const CT bet = (CT)P.beta, gb = (CT)(gamma * P.beta);
+        const CT bet = K.beta, gb = (CT)(gamma * P.beta);
         ST *fd = reinterpret_cast<ST *>(A.fdst);
         // FP32 storage: the rest population closes the node's mass so that the
         // stored set sums to the pulled mass; rounding of the other outputs
         // is then unbiased and the total mass does not drift.
-        double others_out = 0.0;
+        CT oth = 0, othc = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
+            const CT fi = fq[i * NT];
             const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
             const CT feqF = rho * eF[0][L::cx(i) + 1] * eF[1][L::cy(i) + 1] * eF[2][L::cz(i) + 1];
-            const CT dl = StoreTraits<ST>::shifted ? f[i] - (feq - (CT)L::w(i) * shift) : f[i] - feq;
+            const CT dl = StoreTraits<ST>::shifted ? fi - (feq - (CT)L::w(i) * shift) : fi - feq;
             const CT ds = ds_of(i, dev, dPi);
             const CT dh = dl - ds;
-            const CT out = f[i] - ((CT)2 * bet * ds + gb * dh) + (feqF - feq);
+            const CT out = fi - ((CT)2 * bet * ds + gb * dh) + (feqF - feq);
             if (StoreTraits<ST>::shifted && i == L::REST) continue;
-            if (StoreTraits<ST>::shifted) others_out += (double)(ST)out;
+            if (StoreTraits<ST>::shifted) two_sum_acc<CT>(oth, othc, out);
             fd[(long long)i * P.N + n] = (ST)out;
         }
-        if (StoreTraits<ST>::shifted) fd[(long long)L::REST * P.N + n] = (ST)((double)fsum - others_out);
+        if (StoreTraits<ST>::shifted) fd[(long long)L::REST * P.N + n] = (ST)((fsum - oth) - othc);
 
-        // ---- phase field: BGK towards g^eq(phi, mu_phi, u_phys)
-        CT up[3] = {0, 0, 0};
-        CT uu = 0;
-#pragma unroll
-        for (int a = 0; a < D; ++a) { up[a] = (j[a] + (CT)0.5 * F[a]) / rho; uu += up[a] * up[a]; }
-        const CT Gm3 = (CT)(3.0 * P.Gamma) * mu_phi;
-        CT others = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (i == L::REST) continue;
-            others += geq_of(i, Gm3, phi, up, uu);
-        }
-        const CT itg = (CT)P.inv_tau_g;
-        ST *gd = reinterpret_cast<ST *>(A.gdst);
-        double gothers = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (StoreTraits<ST>::shifted && i == L::REST) continue;
-            const CT ge = (i == L::REST) ? phi - others : geq_of(i, Gm3, phi, up, uu);
-            const CT gi = (CT)__ldg(gs + src_index(nb, P.N, i));
-            const ST go = (ST)(gi - (gi - ge) * itg);
-            if (StoreTraits<ST>::shifted) gothers += (double)go;
-            gd[(long long)i * P.N + n] = go;
-        }
-        // FP32 storage: the rest population closes the node's phase-field sum
-        if (StoreTraits<ST>::shifted) gd[(long long)L::REST * P.N + n] = (ST)((double)phi - gothers);
         if (bad) atomicOr(P.err, bad);
     }
 
@@ -634,7 +670,7 @@ struct Fused {
                                      CT rho, CT phi, CT mu_phi, const CT F[3])
     {
         const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
-        const CT shift = (CT)P.rho_ref;
+        const CT shift = coef<CT>(P).rho_ref;
         CT u[3] = {0, 0, 0}, us[3] = {0, 0, 0}, uu = 0;
         unsigned bad = 0;
         if (!(rho > (CT)0)) bad |= ERR_RHO;
@@ -651,7 +687,7 @@ struct Fused {
             if (a < D) eq_factors<CT>(us[a], e[a]);
             else { e[a][0] = 0; e[a][1] = 1; e[a][2] = 0; }
         }
-        const CT Gm3 = (CT)(3.0 * P.Gamma) * mu_phi;
+        const CT Gm3 = coef<CT>(P).Gamma3 * mu_phi;
         CT others = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i)

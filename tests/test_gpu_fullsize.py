@@ -1,0 +1,101 @@
+"""Parity at full size, in the launch configuration the benchmark times.
+
+The update of one node depends only on the state within 3 lattice units
+(pull at radius 1 of moments at radius 2).  So for a sampled node x the
+oracle advances a periodic 7-wide window of the GPU's state centred on x by
+one step, and the window's centre must equal the GPU's post-step populations
+at x.  Workloads: D3Q27 256^3 FP32-shifted (the benchmark's drop collision at
+density ratio 1000) and D2Q9 512^2 FP64 (head-on collision, ratio 1000).
+Tolerances: FP64 storage 1e-12, FP32 storage 2e-5 (one FP32 step against
+FP64), relative to the largest population of the node.
+"""
+import numpy as np
+import pytest
+
+import paper_1710_07486_gb300 as tel
+from paper_1710_07486_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+A_, B_, R_ = 0.037, 0.2, 1.0
+
+
+def window(state, shape, center, r=3):
+    """Periodic window [Q, (2r+1)^D] of a [Q, N] state around center."""
+    Q = state.shape[0]
+    D = len(shape)
+    arr = state.reshape((Q,) + tuple(reversed(shape)))  # [Q, (z,) y, x]
+    idx = [np.arange(c - r, c + r + 1) % n for c, n in zip(reversed(center), reversed(shape))]
+    sub = arr[np.ix_(range(Q), *idx)]
+    return np.ascontiguousarray(sub.reshape(Q, -1))
+
+
+def check_samples(orc, lattice, shape, params, f0, g0, f1, g1, rng, nsamp, tol):
+    D = len(shape)
+    w = 7
+    wshape = (w,) * D
+    o = orc.Oracle(lattice, w, w, 1 if D == 2 else w, params)
+    N = int(np.prod(shape))
+    worst = 0.0
+    for _ in range(nsamp):
+        c = [int(rng.integers(0, n)) for n in shape]
+        fw, gw = window(f0, shape, c), window(g0, shape, c)
+        assert o.step(fw, gw, 1) == 0
+        mid = (w ** D) // 2
+        n = c[0] + shape[0] * (c[1] + (shape[1] * c[2] if D == 3 else 0))
+        for ref, got in ((fw[:, mid], f1[:, n]), (gw[:, mid], g1[:, n])):
+            err = np.max(np.abs(ref - got)) / max(np.max(np.abs(ref)), 1e-300)
+            worst = max(worst, err)
+    assert worst < tol, worst
+    return worst
+
+
+def test_d3q27_256_fp32_bench_configuration(orc):
+    import bench
+    n = 256
+    w = bench.workload_c3(1710, n=n)
+    T = tel.temperature_for_ratio(A_, B_, R_, w["ratio"])
+    rg, rl = tel.coexistence(A_, B_, R_, T)[:2]
+    p, V, R = bench.c3_params(w, T, rg, rl)
+    rho, phi, u = inputs.off_centre_3d(1710, n, rg, rl, p["chi"], V, w["B"], R=R, width=10.0)
+    lat = tel.Lattice(tel.D3Q27, n, n, n, dict(p, precision=tel.FP32_SHIFTED))
+    lat.init(rho, phi, u)
+    lat.step(2)
+    f0, g0 = lat.get_state()
+    m0 = lat.fields(with_p=False)["rho"].sum()
+    lat.step(1)
+    f1, g1 = lat.get_state()
+    rng = np.random.default_rng(11)
+    po = dict(p, rho_ref=0.0)
+    check_samples(orc, 1, (n, n, n), po, f0, g0, f1, g1, rng, 24, 2e-5)
+    # samples through the drops' interfaces, where every term is active
+    cz = n // 2
+    pts = rng.integers(cz - 40, cz + 40, size=(12, 3))
+    worst = 0.0
+    o = orc.Oracle(1, 7, 7, 7, po)
+    for c in pts:
+        fw, gw = window(f0, (n, n, n), list(c)), window(g0, (n, n, n), list(c))
+        assert o.step(fw, gw, 1) == 0
+        idx = c[0] + n * (c[1] + n * c[2])
+        for ref, got in ((fw[:, 171], f1[:, idx]), (gw[:, 171], g1[:, idx])):
+            worst = max(worst, np.max(np.abs(ref - got)) / np.max(np.abs(ref)))
+    assert worst < 2e-5, worst
+    lat.step(7)
+    m1 = lat.fields(with_p=False)["rho"].sum()
+    assert abs(m1 / m0 - 1) < 1e-6
+
+
+def test_d2q9_512_fp64_head_on(orc):
+    n = 512
+    T = tel.temperature_for_ratio(A_, B_, R_, 1000.0)
+    rg, rl = tel.coexistence(A_, B_, R_, T)[:2]
+    p = dict(a=A_, b=B_, R=R_, T=T, lambda1=0.02, lambda2=0.4, lambda3=0.4, kappa1=0.001, kappa2=4.0,
+             kappa3=4.0, chi=5.0, nu=0.2, Gamma=1.0, tau_g=1.0, force_form=1)
+    rho, phi, u = inputs.head_on_2d(1710, n, rg, rl, p["chi"], 0.05, width=10.0)
+    lat = tel.Lattice(tel.D2Q9, n, n, 1, p)
+    lat.init(rho, phi, u)
+    lat.step(3)
+    f0, g0 = lat.get_state()
+    lat.step(1)
+    f1, g1 = lat.get_state()
+    check_samples(orc, 0, (n, n), p, f0, g0, f1, g1, np.random.default_rng(5), 64, 1e-12)

@@ -261,3 +261,26 @@ def test_bounce_back_channel_at_rest(orc, T10):
     assert o.step(f, g, 10) == 0
     fl = o.fields(f, g)
     assert np.allclose(fl["rho"], o.rho_l, rtol=1e-14) and np.abs(fl["u"]).max() < 1e-15
+
+
+@pytest.mark.parametrize("lattice,n", [(0, 12), (1, 9)])
+def test_update_depends_on_radius_three_only(orc, T10, lattice, n):
+    """The premise of the full-size sampled parity test: one step of a node
+    reads the state within 3 lattice units, so a periodic 7-wide window around
+    the node reproduces the node's update exactly."""
+    from tests.test_gpu_fullsize import window
+    o, rho, phi, u = drop_case(orc, lattice, T10, n)
+    f, g = o.init(rho, phi, u)
+    o.step(f, g, 2)
+    shape = (n,) * o.D
+    f0, g0 = f.copy(), g.copy()
+    o.step(f, g, 1)
+    w = orc.Oracle(lattice, 7, 7, 1 if lattice == 0 else 7, o.params)
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        c = [int(rng.integers(0, n)) for _ in range(o.D)]
+        fw, gw = window(f0, shape, c), window(g0, shape, c)
+        w.step(fw, gw, 1)
+        mid = (7 ** o.D) // 2
+        node = c[0] + n * (c[1] + (n * c[2] if o.D == 3 else 0))
+        assert np.array_equal(fw[:, mid], f[:, node]) and np.array_equal(gw[:, mid], g[:, node])
