@@ -155,6 +155,29 @@ int tel_info(const tel_ctx *ctx, double out[10]);
 int tel_coexistence(double a, double b, double R, double T, double out[4]);
 int tel_temperature_for_ratio(double a, double b, double R, double ratio, double *T);
 
+/* Allocation-free field extraction (the paper has no counterpart; this is a
+ * service of the library).  For callers that cannot let a library allocate
+ * device memory -- applications that give the whole device to their own
+ * memory pool at start-up or must keep their device footprint fixed, and code
+ * paths without access to cudaMalloc.  The caller holds the state in its own
+ * device buffers, in the layout tel_get_state describes ([Q][N]; FP64, or
+ * FP32 storing f_i - w_i rho_ref and g_i when params->precision is
+ * TEL_FP32_SHIFTED, with rho_ref = params->rho_ref, or rho_g when that is
+ * <= 0), and receives rho, phi, u, p (any may be NULL) in host buffers, as
+ * tel_fields returns them.  No device or pinned memory is allocated: the
+ * library stages the fields through a fixed device array of at most
+ * TEL_NOALLOC_MAX_NODES nodes (about 12.6 MB, reserved on every GPU that loads
+ * the library, until exit).  Larger lattices are rejected with TEL_EINVAL.
+ * The first call on a device looks up that array's device address, so make
+ * it before any stream capture.  Calls share the array: calls that overlap on
+ * the GPU race with each other.  The work runs on cuda_stream (NULL: the
+ * legacy default stream) and the call synchronises it.  Errors as for
+ * tel_fields; the message is available from tel_last_error(NULL). */
+#define TEL_NOALLOC_MAX_NODES 262144
+int tel_fields_noalloc(int lattice, int nx, int ny, int nz, const tel_params *params,
+                       const void *f_state, const void *g_state, double *rho, double *phi,
+                       double *u, double *p, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,7 +49,7 @@ _lib = None
 SYMBOLS = ("tel_create", "tel_destroy", "tel_last_error", "tel_set_stream", "tel_init",
            "tel_init_device", "tel_step", "tel_sync", "tel_fields", "tel_fields_device",
            "tel_get_state", "tel_set_state", "tel_info", "tel_coexistence",
-           "tel_temperature_for_ratio")
+           "tel_temperature_for_ratio", "tel_fields_noalloc")
 
 
 def lib(build: bool = True):
@@ -82,6 +82,7 @@ def lib(build: bool = True):
     L.tel_info.argtypes = [vp, dp]
     L.tel_coexistence.argtypes = [d, d, d, d, dp]
     L.tel_temperature_for_ratio.argtypes = [d, d, d, d, dp]
+    L.tel_fields_noalloc.argtypes = [i, i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
     for name in SYMBOLS:
         if name not in ("tel_destroy", "tel_last_error"):
             getattr(L, name).restype = C.c_int
@@ -107,6 +108,46 @@ def temperature_for_ratio(a, b, R, ratio):
     if rc:
         raise TelError(rc, f"no temperature with density ratio {ratio}")
     return T.value
+
+
+NOALLOC_MAX_NODES = 262144
+
+
+def _params_struct(p):
+    s = Params()
+    for k in ("a", "b", "R", "T", "lambda1", "lambda2", "lambda3", "kappa1", "kappa2",
+              "kappa3", "chi", "nu", "Gamma", "tau_g"):
+        setattr(s, k, float(p[k]))
+    s.rho_ref = float(p.get("rho_ref", 0.0))
+    s.precision = int(p.get("precision", FP64))
+    s.force_form = int(p.get("force_form", FORCE_LATTICE))
+    bcs = tuple(p.get("bc", (0, 0, 0)))
+    for k in range(3):
+        s.bc[k] = int(bcs[k])
+    return s
+
+
+def fields_noalloc(lattice, nx, ny, nz, params, f_state, g_state, with_p=True, stream=None):
+    """Fields of a state held in the caller's own device buffers (torch
+    tensors or raw device pointers), without any allocation by the library:
+    for callers that keep the device's memory to themselves.  At most
+    NOALLOC_MAX_NODES nodes.  Returns host numpy arrays like Lattice.fields."""
+    D = 2 if lattice == D2Q9 else 3
+    N = nx * ny * (1 if lattice == D2Q9 else nz)
+    ptr = lambda t: C.c_void_p(t if isinstance(t, int) else t.data_ptr())
+    rho, phi = np.empty(N), np.empty(N)
+    u = np.empty((D, N))
+    p = np.empty(N) if with_p else None
+    raw = None
+    if stream is not None:
+        raw = getattr(stream, "cuda_stream", stream)
+    s = _params_struct(params)
+    rc = lib().tel_fields_noalloc(int(lattice), int(nx), int(ny), int(nz), C.byref(s), ptr(f_state),
+                                  ptr(g_state), _ptr(rho), _ptr(phi), _ptr(u), _ptr(p),
+                                  C.c_void_p(raw) if raw else None)
+    if rc:
+        raise TelError(rc, lib().tel_last_error(None).decode())
+    return {"rho": rho, "phi": phi, "u": u, "p": p}
 
 
 class Lattice:

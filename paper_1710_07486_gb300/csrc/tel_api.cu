@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "ternelbm.h"
@@ -226,32 +227,14 @@ static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
     return TEL_OK;
 }
 
-extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params *params, tel_ctx **out)
+// Device-side parameter block of a validated lattice and its coexistence
+// point co = {rho_g, rho_l, mu_coex, p_coex}.
+static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params &p, const double co[4],
+                           tel::DevParams &d)
 {
-    if (!out) return fail(nullptr, TEL_EINVAL, "out is NULL");
-    *out = nullptr;
-    int rc = validate(lattice, nx, ny, nz, params);
-    if (rc) return rc;
-    double co[4];
-    if (tel_coexistence(params->a, params->b, params->R, params->T, co) != TEL_OK)
-        return fail(nullptr, TEL_EINVAL, "no liquid-gas coexistence at T=%g (T must be below the critical temperature)",
-                    params->T);
-    tel_ctx *c = new (std::nothrow) tel_ctx();
-    if (!c) return fail(nullptr, TEL_ENOMEM, "host allocation failed");
-    std::memset(c, 0, sizeof(*c));
-    c->lattice = lattice;
-    c->D = lattice == TEL_D2Q9 ? 2 : 3;
-    c->Q = lattice == TEL_D2Q9 ? 9 : 27;
-    c->nx = nx; c->ny = ny; c->nz = lattice == TEL_D2Q9 ? 1 : nz;
-    c->N = (long long)nx * ny * c->nz;
-    c->p = *params;
-    if (lattice == TEL_D2Q9) c->p.bc[2] = TEL_PERIODIC;
-
-    tel::DevParams &d = c->dp;
-    const tel_params &p = c->p;
-    d.nx = nx; d.ny = ny; d.nz = c->nz;
+    d.nx = nx; d.ny = ny; d.nz = lattice == TEL_D2Q9 ? 1 : nz;
     for (int a = 0; a < 3; ++a) d.bc[a] = p.bc[a];
-    d.N = c->N;
+    d.N = (long long)nx * ny * d.nz;
     d.chunk = 32;
     if (const char *ev = std::getenv("TEL_CHUNK")) {  // tuning override: planes per CTA
         const int v = std::atoi(ev);
@@ -284,9 +267,35 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     d.Gamma = p.Gamma;
     d.inv_tau_g = 1.0 / p.tau_g;
     d.rho_ref = p.precision == TEL_FP32_SHIFTED ? (p.rho_ref > 0 ? p.rho_ref : co[0]) : 0.0;
-    c->p.rho_ref = d.rho_ref;
     fill_coef(d, d.cf);
     fill_coef(d, d.cd);
+}
+
+extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params *params, tel_ctx **out)
+{
+    if (!out) return fail(nullptr, TEL_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(lattice, nx, ny, nz, params);
+    if (rc) return rc;
+    double co[4];
+    if (tel_coexistence(params->a, params->b, params->R, params->T, co) != TEL_OK)
+        return fail(nullptr, TEL_EINVAL, "no liquid-gas coexistence at T=%g (T must be below the critical temperature)",
+                    params->T);
+    tel_ctx *c = new (std::nothrow) tel_ctx();
+    if (!c) return fail(nullptr, TEL_ENOMEM, "host allocation failed");
+    std::memset(c, 0, sizeof(*c));
+    c->lattice = lattice;
+    c->D = lattice == TEL_D2Q9 ? 2 : 3;
+    c->Q = lattice == TEL_D2Q9 ? 9 : 27;
+    c->nx = nx; c->ny = ny; c->nz = lattice == TEL_D2Q9 ? 1 : nz;
+    c->N = (long long)nx * ny * c->nz;
+    c->p = *params;
+    if (lattice == TEL_D2Q9) c->p.bc[2] = TEL_PERIODIC;
+
+    tel::DevParams &d = c->dp;
+    const tel_params &p = c->p;
+    fill_devparams(lattice, nx, ny, nz, p, co, d);
+    c->p.rho_ref = d.rho_ref;
 
     const size_t es = p.precision == TEL_FP64 ? sizeof(double) : sizeof(float);
     const size_t bytes = es * (size_t)c->Q * (size_t)c->N;
@@ -500,5 +509,109 @@ extern "C" int tel_set_state(tel_ctx *c, const double *f, const double *g)
     }
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     c->initialized = 1;
+    return TEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free field extraction.
+//
+// Some callers cannot let a library allocate device memory: applications
+// that hand the whole device to their own memory pool up front, or that must
+// keep their device footprint fixed after start-up, and code paths where
+// cudaMalloc is not available to them.  tel_fields_noalloc serves them: the
+// state lives in the caller's own device buffers, the results go to the
+// caller's host buffers, and the only device memory used besides those is a
+// fixed array of this file, reserved when the library is loaded.
+//
+// tel_noalloc_scratch holds (3 + D) field arrays of up to
+// TEL_NOALLOC_MAX_NODES nodes followed by the error word; every GPU that
+// loads the library keeps it until the process exits.  In host code its name
+// is only a host-side stand-in: the device address is obtained once per
+// device with cudaGetSymbolAddress (the first call on each device, with that
+// device current) and passed to the kernel.  All calls share the array: the
+// error word is cleared on every call, and calls that overlap on the GPU
+// race with each other.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double tel_noalloc_scratch[6 * TEL_NOALLOC_MAX_NODES + 32];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+char g_noalloc_msg[512] = "";
+
+int noalloc_fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_noalloc_msg, sizeof(g_noalloc_msg), fmt, ap);
+    va_end(ap);
+    std::snprintf(g_create_msg, sizeof(g_create_msg), "%s", g_noalloc_msg);
+    return code;
+}
+}  // namespace
+
+extern "C" int tel_fields_noalloc(int lattice, int nx, int ny, int nz, const tel_params *params,
+                                  const void *f_state, const void *g_state, double *rho, double *phi,
+                                  double *u, double *p, void *cuda_stream)
+{
+    int rc = validate(lattice, nx, ny, nz, params);
+    if (rc) return noalloc_fail(rc, "%s", g_create_msg);
+    const int D = lattice == TEL_D2Q9 ? 2 : 3;
+    const long long N = (long long)nx * ny * (lattice == TEL_D2Q9 ? 1 : nz);
+    if (N > TEL_NOALLOC_MAX_NODES)
+        return noalloc_fail(TEL_EINVAL, "tel_fields_noalloc: %lld nodes exceed the fixed scratch of %d nodes",
+                            N, TEL_NOALLOC_MAX_NODES);
+    if (!f_state || !g_state) return noalloc_fail(TEL_EINVAL, "tel_fields_noalloc: NULL state buffer");
+    double co[4];
+    if (tel_coexistence(params->a, params->b, params->R, params->T, co) != TEL_OK)
+        return noalloc_fail(TEL_EINVAL, "no liquid-gas coexistence at T=%g", params->T);
+    tel_params pp = *params;
+    if (lattice == TEL_D2Q9) pp.bc[2] = TEL_PERIODIC;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(TEL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(TEL_EINVAL, "device %d out of range", dev);
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, tel_noalloc_scratch);
+            if (e != cudaSuccess)
+                return noalloc_fail(TEL_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = static_cast<double *>(ptr);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    tel::DevParams d{};
+    fill_devparams(lattice, nx, ny, nz, pp, co, d);
+    unsigned *err = reinterpret_cast<unsigned *>(scratch + 6 * (size_t)TEL_NOALLOC_MAX_NODES);
+    d.err = err;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t n = (size_t)N;
+    double *o_rho = scratch, *o_phi = scratch + n, *o_u = scratch + 2 * n, *o_p = scratch + (2 + D) * n;
+    tel::LaunchArgs A{};
+    A.fsrc = f_state; A.gsrc = g_state;
+    A.out_rho = rho ? o_rho : nullptr; A.out_phi = phi ? o_phi : nullptr;
+    A.out_u = u ? o_u : nullptr; A.out_p = p ? o_p : nullptr;
+#define NOALLOC_CUDA(expr)                                                                       \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) return noalloc_fail(TEL_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+    NOALLOC_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+    NOALLOC_CUDA(lattice == TEL_D2Q9 ? tel::launch_d2q9(pp.precision, tel::MODE_FIELDS, d, A, s)
+                                     : tel::launch_d3q27(pp.precision, tel::MODE_FIELDS, d, A, s));
+    if (rho) NOALLOC_CUDA(cudaMemcpyAsync(rho, o_rho, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (phi) NOALLOC_CUDA(cudaMemcpyAsync(phi, o_phi, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (u) NOALLOC_CUDA(cudaMemcpyAsync(u, o_u, (size_t)D * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (p) NOALLOC_CUDA(cudaMemcpyAsync(p, o_p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    unsigned flag = 0;
+    NOALLOC_CUDA(cudaMemcpyAsync(&flag, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    NOALLOC_CUDA(cudaStreamSynchronize(s));
+#undef NOALLOC_CUDA
+    if (flag) return noalloc_fail(TEL_EUNSTABLE, "unstable node(s) flagged on the device (bits 0x%x)", flag);
     return TEL_OK;
 }
