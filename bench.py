@@ -119,13 +119,28 @@ def peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("tel_kernels.cuh", "tel_launch.cuh", "tel_d3q27.cu")
+
+
+def kernel_sources_sha16():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1710_07486_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic():
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary
-    (profiles/fused_step_d3q27_fp32.json), or None."""
+    """Per-launch DRAM bytes (read + write) of the step kernel at the full
+    size, from the committed ncu summary (profiles/fused_step_d3q27_fp32.json);
+    None when that summary was taken on other kernel sources."""
     fn = os.path.join(ROOT, "profiles", "fused_step_d3q27_fp32.json")
     try:
         with open(fn) as fh:
             d = json.load(fh)
+        if d.get("kernel_sources_sha16") != kernel_sources_sha16():
+            return None
         return d.get("dram_bytes_per_launch_full_size")
     except Exception:
         return None
@@ -270,14 +285,20 @@ def cpu_baseline(args, steps=None, n=None):
     rg, rl = orc.coexistence(A_, B_, R_, T)[:2]
     p, V, R = c3_params(w, T, rg, rl)
     o = orc.Oracle(orc.D3Q27, n, n, n, p)
-    rho, phi, u = inputs.off_centre_3d(args.seed, n, rg, rl, p["chi"], V, w["B"], R=R * n / 256.0, width=10.0 * n / 256.0)
+    rho, phi, u = inputs.off_centre_3d(args.seed, n, rg, rl, p["chi"], V, w["B"], R=R * n / 256.0, width=10.0)
     f, g = o.init(rho, phi, u)
-    t0 = time.perf_counter()
-    o.step(f, g, steps)
-    dt = time.perf_counter() - t0
-    return {"value": round(n ** 3 * steps / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"D3Q27 {n}^3 periodic box, same collision scaled (R={R * n / 256.0:g}), {steps} steps, "
-                      f"FP64, single thread, {dt:.1f} s"}
+    done, dt = 0, 0.0
+    while done < steps:  # one step at a time: only completed, stable steps count
+        t0 = time.perf_counter()
+        rc = o.step(f, g, 1)
+        dt += time.perf_counter() - t0
+        if rc != 0:
+            break
+        done += 1
+    note = "" if done == steps else f" (oracle flagged the state unstable after {done} steps)"
+    return {"value": round(n ** 3 * max(done, 1) / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"D3Q27 {n}^3 periodic box, same collision scaled (R={R * n / 256.0:g}, interface width 10), "
+                      f"{done} steps, FP64, single thread, {dt:.1f} s{note}"}
 
 
 def run_reference(args):

@@ -522,26 +522,24 @@ struct Fused {
 #pragma unroll
         for (int a = 0; a < D; ++a) { up[a] = (j[a] + (CT)0.5 * F[a]) / rho; uu += up[a] * up[a]; }
         const CT Gm3 = K.Gamma3 * mu_phi;
-        CT others = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (i == L::REST) continue;
-            others += geq_of(i, Gm3, phi, up, uu);
-        }
+        // sum of g^eq over the moving velocities, by lattice isotropy
+        // (sum_{i != 0} w_i = 1 - w_0, sum w_i (c_i.u)^2 = u.u/3)
+        const CT w0 = (CT)L::w(L::REST);
+        const CT others = ((CT)1 - w0) * Gm3 + (CT)1.5 * w0 * phi * uu;
         const CT itg = K.inv_tau_g;
         ST *gd = reinterpret_cast<ST *>(A.gdst);
-        CT goth = 0, gothc = 0;
+        CT goth = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             if (StoreTraits<ST>::shifted && i == L::REST) continue;
             const CT ge = (i == L::REST) ? phi - others : geq_of(i, Gm3, phi, up, uu);
             const CT gi = (CT)__ldg(gs + src_index(nb, P.N, i));
             const CT go = gi - (gi - ge) * itg;
-            if (StoreTraits<ST>::shifted) two_sum_acc<CT>(goth, gothc, (CT)(ST)go);
+            if (StoreTraits<ST>::shifted) goth += (CT)(ST)go;
             gd[(long long)i * P.N + n] = (ST)go;
         }
         // FP32 storage: the rest population closes the node's phase-field sum
-        if (StoreTraits<ST>::shifted) gd[(long long)L::REST * P.N + n] = (ST)((phi - goth) - gothc);
+        if (StoreTraits<ST>::shifted) gd[(long long)L::REST * P.N + n] = (ST)(phi - goth);
 
         CT uF[3] = {0, 0, 0};
 #pragma unroll
@@ -618,7 +616,7 @@ struct Fused {
         // FP32 storage: the rest population closes the node's mass so that the
         // stored set sums to the pulled mass; rounding of the other outputs
         // is then unbiased and the total mass does not drift.
-        CT oth = 0, othc = 0;
+        CT oth = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const CT fi = fq[i * NT];
@@ -629,10 +627,10 @@ struct Fused {
             const CT dh = dl - ds;
             const CT out = fi - ((CT)2 * bet * ds + gb * dh) + (feqF - feq);
             if (StoreTraits<ST>::shifted && i == L::REST) continue;
-            if (StoreTraits<ST>::shifted) two_sum_acc<CT>(oth, othc, out);
+            if (StoreTraits<ST>::shifted) oth += (CT)(ST)out;
             fd[(long long)i * P.N + n] = (ST)out;
         }
-        if (StoreTraits<ST>::shifted) fd[(long long)L::REST * P.N + n] = (ST)((fsum - oth) - othc);
+        if (StoreTraits<ST>::shifted) fd[(long long)L::REST * P.N + n] = (ST)(fsum - oth);
 
         if (bad) atomicOr(P.err, bad);
     }
