@@ -236,19 +236,22 @@ struct Fused {
     static constexpr int OY2 = (D == 3 ? 2 : 0), OY1 = (D == 3 ? 1 : 0);
 
     // shared memory layout (in CT units)
+    // ring buffers over planes: RS slots of rho, phi (tile + ring 2), MS of
+    // mu and grad rho (tile + ring 1)
+    static constexpr int RS = 6, MS = 4;
     static constexpr int OFF_RHO = 0;
-    static constexpr int OFF_PHI = OFF_RHO + 5 * NA;
-    static constexpr int OFF_MR = OFF_PHI + 5 * NA;
-    static constexpr int OFF_MP = OFF_MR + 3 * NB;
-    static constexpr int OFF_G = OFF_MP + 3 * NB;
-    static constexpr int OFF_F = OFF_G + 3 * D * NB;   // per-thread population stash [Q][NT]
+    static constexpr int OFF_PHI = OFF_RHO + RS * NA;
+    static constexpr int OFF_MR = OFF_PHI + RS * NA;
+    static constexpr int OFF_MP = OFF_MR + MS * NB;
+    static constexpr int OFF_G = OFF_MP + MS * NB;
+    static constexpr int OFF_F = OFF_G + MS * (D + 1) * NB;  // per-thread population stash [Q][NT]
     static constexpr int SMEM_ELEMS = OFF_F + (MODE == MODE_STEP ? Q * NT : 0);
     static constexpr size_t SMEM_BYTES = sizeof(CT) * SMEM_ELEMS;
 
     __device__ static __forceinline__ int idx2(int ox, int oy) { return (ox + 2) + R2X * (oy + OY2); }
     __device__ static __forceinline__ int idx1(int ox, int oy) { return (ox + 1) + R1X * (oy + OY1); }
-    __device__ static __forceinline__ int slot5(int m) { int s = m % 5; return s < 0 ? s + 5 : s; }
-    __device__ static __forceinline__ int slot3(int m) { int s = m % 3; return s < 0 ? s + 3 : s; }
+    __device__ static __forceinline__ int slot5(int m) { int s = m % RS; return s < 0 ? s + RS : s; }
+    __device__ static __forceinline__ int slot3(int m) { int s = m % MS; return s < 0 ? s + MS : s; }
 
     // Sources of the populations pulled into node (x, y, m): per axis the
     // source coordinate x - c for c = -1, 0, 1 (periodic wrap) as an offset,
@@ -310,14 +313,27 @@ struct Fused {
         const ST *fs = reinterpret_cast<const ST *>(A.fsrc);
         const ST *gs = reinterpret_cast<const ST *>(A.gsrc);
 
-        const int iters = (m1 - m0) + 4;
+        // Software pipeline over planes, one barrier per plane.  Iteration it
+        // works on three planes: moments of mA (phase A) and chemical
+        // potentials of mB = mA - 2 (phase B, from moments completed in earlier
+        // iterations) in one load-balanced pass, then, after the barrier, the
+        // collision of mC = mA - 3 (phase C).  With RS = 6 moment slots and
+        // MS = 4 potential slots, the next iteration's A/B pass never writes a
+        // slot that phase C is still reading, so no second barrier is needed.
+        const int iters = (m1 - m0) + 5;
         for (int it = 0; it < iters; ++it) {
-            // ---------------- phase A: moments of plane mA on tile + ring 2
             const int mA = m0 - 2 + it;
-            if (mA <= m1 + 1) {
-                const int mm = map_coord(mA, PM, bM);
-                CT *rs = rho_s + slot5(mA) * NA, *ps = phi_s + slot5(mA) * NA;
-                for (int r = tid; r < NA; r += NT) {
+            const int mB = mA - 2;
+            const int mC = mA - 3;
+            const bool doA = mA <= m1 + 1;
+            const bool doB = mB >= m0 - 1 && mB <= m1;
+            const int nA = doA ? NA : 0;
+            const int nW = nA + (doB ? NB : 0);
+            const int mm = map_coord(mA, PM, bM);
+            for (int w = tid; w < nW; w += NT) {
+                if (w < nA) {
+                    // ---------------- phase A: moments of plane mA on tile + ring 2
+                    const int r = w;
                     const int ox = r % R2X - 2, oy = (D == 3 ? r / R2X - 2 : 0);
                     const int xx = map_coord(x0 + ox, PX, bX);
                     const int yy = (D == 3 ? map_coord(y0 + oy, PY, bY) : 0);
@@ -337,16 +353,12 @@ struct Fused {
                         rho = StoreTraits<ST>::shifted ? shift + sr : sr;
                         phi = sp;
                     }
-                    rs[r] = rho;
-                    ps[r] = phi;
-                }
-            }
-            __syncthreads();
-            // ---------------- phase B: chemical potentials of plane mB on tile + ring 1
-            const int mB = mA - 1;
-            if (mB >= m0 - 1 && mB <= m1) {
-                const int sB = slot3(mB);
-                for (int s = tid; s < NB; s += NT) {
+                    rho_s[slot5(mA) * NA + r] = rho;
+                    phi_s[slot5(mA) * NA + r] = phi;
+                } else {
+                    // ---------------- phase B: chemical potentials of plane mB on tile + ring 1
+                    const int s = w - nA;
+                    const int sB = slot3(mB);
                     const int ox = s % R1X - 1, oy = (D == 3 ? s / R1X - 1 : 0);
                     const int c0 = idx2(ox, oy);
                     const CT r0 = rho_s[slot5(mB) * NA + c0], p0 = phi_s[slot5(mB) * NA + c0];
@@ -373,15 +385,16 @@ struct Fused {
                     mr_s[sB * NB + s] = mr - coef<CT>(P).Kr * lr - coef<CT>(P).Kx * lp;
                     mp_s[sB * NB + s] = mp - coef<CT>(P).Kp * lp - coef<CT>(P).Kx * lr;
                     if (P.force_form == 1) {
-                        g_s[(sB * D + 0) * NB + s] = (CT)3 * gx;
-                        g_s[(sB * D + 1) * NB + s] = (CT)3 * gy;
-                        if (D == 3) g_s[(sB * D + 2) * NB + s] = (CT)3 * gz;
+                        // grad rho and c_s^4/(4 rho) of this ring-1 node (lattice-consistent force)
+                        g_s[(sB * (D + 1) + 0) * NB + s] = (CT)3 * gx;
+                        g_s[(sB * (D + 1) + 1) * NB + s] = (CT)3 * gy;
+                        if (D == 3) g_s[(sB * (D + 1) + 2) * NB + s] = (CT)3 * gz;
+                        g_s[(sB * (D + 1) + D) * NB + s] = (CT)(1.0 / 36.0) / r0;
                     }
                 }
             }
             __syncthreads();
             // ---------------- phase C: collide plane mC
-            const int mC = mA - 2;
             if (mC >= m0 && mC < m1) {
                 const int tx = tid % TX, ty = tid / TX;
                 const int x = x0 + tx, y = y0 + ty;
@@ -435,41 +448,37 @@ struct Fused {
 #pragma unroll
             for (int a = 0; a < D; ++a) F[a] += cs2 * gr[a];
         } else {
-            // A[G]_a = sum_i 3 w_i c_ia c_i.G(x - c_i);  div T with T = c_s^4 G G/(4 rho) at x + c_i
+            // A[G]_a = sum_i 3 w_i c_ia c_i.G(x - c_i) = sum_j 3 w_j c_ja c_j.G(x + c_j)
+            // (j the opposite of i), and div T with T = c_s^4 G G/(4 rho):
+            // sum_b c_jb T_ab(x + c_j) = s_j G_a (c_j.G) with s = c_s^4/(4 rho).
+            // Both read the same 26 neighbours (G and s stored per ring-1 node).
             CT AG[3] = {0, 0, 0}, dT[3] = {0, 0, 0};
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if (L::nnz(i) == 0) continue;
                 const CT wi3 = (CT)(3.0 * L::w(i));
-                const int sm_ = slot3(m - L::pM(i));
-                const int km = idx1(ox - L::pX(i), oy - L::pY(i));
+                const int sp_ = slot3(m + L::pM(i));
+                const int kp = idx1(ox + L::pX(i), oy + L::pY(i));
+                CT Gp[3];
+#pragma unroll
+                for (int b = 0; b < D; ++b) Gp[b] = g_s[(sp_ * (D + 1) + b) * NB + kp];
+                const CT sj = g_s[(sp_ * (D + 1) + D) * NB + kp];
                 CT cG = 0;
 #pragma unroll
                 for (int b = 0; b < D; ++b)
-                    if (L::c(i, b)) cG += (CT)L::c(i, b) * g_s[(sm_ * D + b) * NB + km];
+                    if (L::c(i, b)) cG += (CT)L::c(i, b) * Gp[b];
+                const CT t = wi3 * cG;
 #pragma unroll
                 for (int a = 0; a < D; ++a)
-                    if (L::c(i, a)) AG[a] += wi3 * (CT)L::c(i, a) * cG;
-                const int sp_ = slot3(m + L::pM(i));
-                const int kp = idx1(ox + L::pX(i), oy + L::pY(i));
-                const CT rp = rho_s[slot5(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
-                CT Gp[3];
-#pragma unroll
-                for (int b = 0; b < D; ++b) Gp[b] = g_s[(sp_ * D + b) * NB + kp];
-                CT cGp = 0;
-#pragma unroll
-                for (int b = 0; b < D; ++b)
-                    if (L::c(i, b)) cGp += (CT)L::c(i, b) * Gp[b];
-                // sum_b c_ib T_ab = c_s^4 G_a (c.G) / (4 rho)
-                const CT q = wi3 * cs2 * cs2 * cGp / ((CT)4 * rp);
+                    if (L::c(i, a)) AG[a] += (CT)L::c(i, a) * t;
+                const CT q = t * sj;
 #pragma unroll
                 for (int a = 0; a < D; ++a) dT[a] += q * Gp[a];
             }
-            const CT *G0 = g_s;  // G at the node itself
             const int s0 = slot3(m), k0 = idx1(ox, oy);
 #pragma unroll
             for (int a = 0; a < D; ++a)
-                F[a] += cs2 * ((CT)1.5 * G0[(s0 * D + a) * NB + k0] - (CT)0.5 * AG[a]) + dT[a];
+                F[a] += cs2 * ((CT)1.5 * g_s[(s0 * (D + 1) + a) * NB + k0] - (CT)0.5 * AG[a]) + dT[a];
         }
         const CT mu_phi = mp_s[slot3(m) * NB + idx1(ox, oy)];
 
@@ -576,7 +585,7 @@ struct Fused {
         // sums.  FP32 storage: the FP32 terms are summed with Knuth's
         // error-free two-sum (the sum of the terms exact to ~2^-48).
         double shd = 0.0, hhd = 0.0;
-        CT sh = 0, hh = 0, shc = 0, hhc = 0;
+        CT sh = 0, hh = 0, shc = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const CT fi = fq[i * NT];
@@ -584,13 +593,16 @@ struct Fused {
             const CT dl = StoreTraits<ST>::shifted ? fi - (feq - (CT)L::w(i) * shift) : fi - feq;
             const CT ds = ds_of(i, dev, dPi);
             const CT dh = dl - ds;
+            // <dh|dh> sums non-negative terms (no cancellation); <ds|dh> has
+            // terms only where ds != 0 (one or two non-zero components of c_i)
+            const bool has_ds = L::nnz(i) == 1 || L::nnz(i) == 2;
             if (StoreTraits<ST>::shifted) {
                 const CT r = __frcp_rn((float)feq);
-                two_sum_acc<CT>(sh, shc, ds * dh * r);
-                two_sum_acc<CT>(hh, hhc, dh * dh * r);
+                if (has_ds) two_sum_acc<CT>(sh, shc, ds * dh * r);
+                hh += dh * dh * r;
             } else {
                 const CT r = (CT)1 / feq;
-                shd += (double)(ds * dh * r);
+                if (has_ds) shd += (double)(ds * dh * r);
                 hhd += (double)(dh * dh * r);
             }
         }
@@ -599,7 +611,7 @@ struct Fused {
         // FP32 reciprocal refined by one Newton-Raphson step in FP64)
         double gamma = 2.0;
         if (StoreTraits<ST>::shifted) {
-            const CT shs = sh + shc, hhs = hh + hhc;
+            const CT shs = sh + shc, hhs = hh;
             if (hhs > (CT)1e-30 * rho * rho) {
                 const double H = (double)hhs;
                 double rH = (double)__frcp_rn((float)hhs);

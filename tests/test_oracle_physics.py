@@ -34,3 +34,30 @@ def test_flat_interface_coexistence(orc, ratio):
     assert np.abs(fl["u"]).max() < 1e-3
     # the bulk thermodynamic pressure of both phases matches (p = 0 at coexistence)
     assert abs(fl["p"][0] - fl["p"][nx // 2]) < 2e-3 * o.rho_l / 3
+
+
+@pytest.mark.slow
+def test_laplace_law_oracle(orc):
+    """Laplace's law in 2D, dp = sigma/R, for two liquid drops in gas at density
+    ratio 10; sigma measured on a relaxed flat interface as int kappa1 rho'^2.
+    Coarse (64^2 box, 3000 steps): within 20%.  The GPU test runs the same law
+    on larger drops to 6%."""
+    o, fl = flat_interface(orc, 10.0, form=1, steps=3000, nx=128, width=8.0)
+    G = o.gradient(fl["rho"])[0]
+    sigma = 0.5 * np.sum(0.05 * G * G)
+    T = orc.temperature_for_ratio(A, B, RGAS, 10.0)
+    p = base(T, lambda2=0.0, lambda3=0.0, kappa1=0.05, kappa2=0.0, kappa3=0.0, force_form=1)
+    n = 64
+    from paper_1710_07486_gb300 import inputs
+    for R in (11.0, 15.0):
+        d = orc.Oracle(orc.D2Q9, n, n, 1, p)
+        rho, phi, u = inputs.drops((n, n), d.rho_g, d.rho_l, 5.0, [dict(center=(n / 2, n / 2), R=R, kind=1)],
+                                   width=8.0)
+        f, g = d.init(rho, 0 * phi, u)
+        assert d.step(f, g, 3000) == 0
+        out = d.fields(f, g)
+        rr = out["rho"].reshape(n, n)
+        P = out["p"].reshape(n, n)
+        Re = np.sqrt((rr - d.rho_g).sum() / (d.rho_l - d.rho_g) / np.pi)
+        ratio = (P[n // 2, n // 2] - P[0, 0]) * Re / sigma
+        assert 0.8 < ratio < 1.2, (R, ratio)
