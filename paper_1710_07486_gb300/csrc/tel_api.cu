@@ -235,7 +235,17 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
     d.nx = nx; d.ny = ny; d.nz = lattice == TEL_D2Q9 ? 1 : nz;
     for (int a = 0; a < 3; ++a) d.bc[a] = p.bc[a];
     d.N = (long long)nx * ny * d.nz;
-    d.chunk = 32;
+    {
+        // planes per CTA along the marching axis: long enough to amortise the
+        // five warm-up planes of the pipeline, short enough to give about four
+        // CTAs per SM (152 SMs): 8..32 planes
+        const long long tiles = lattice == TEL_D2Q9 ? (nx + 63) / 64 : (long long)((nx + 31) / 32) * ((ny + 7) / 8);
+        const long long planes = lattice == TEL_D2Q9 ? ny : nz;
+        const long long want = (4 * 152 + tiles - 1) / tiles;
+        long long ch = (planes + want - 1) / want;
+        ch = ch < 8 ? 8 : (ch > 32 ? 32 : ch);
+        d.chunk = (int)ch;
+    }
     if (const char *ev = std::getenv("TEL_CHUNK")) {  // tuning override: planes per CTA
         const int v = std::atoi(ev);
         if (v >= 1) d.chunk = v;

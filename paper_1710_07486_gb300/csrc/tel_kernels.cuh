@@ -133,6 +133,27 @@ __device__ __forceinline__ void two_sum_acc(T &s, T &c, T v)
     s = t;
 }
 
+// Pairs and quads of the compute type.  In FP32, pair arithmetic uses the
+// packed FP32x2 instructions of sm_100+ (__ffma2_rn, __fadd2_rn).
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    typedef float2 v2;
+    typedef float4 v4;
+    __device__ static __forceinline__ v2 pair(float a, float b) { return make_float2(a, b); }
+    __device__ static __forceinline__ v2 fma(v2 a, v2 b, v2 c) { return __ffma2_rn(a, b, c); }
+    __device__ static __forceinline__ v2 add(v2 a, v2 b) { return __fadd2_rn(a, b); }
+    __device__ static __forceinline__ v4 quad(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+struct __align__(16) dquad { double x, y, z, w; };
+template <> struct Vec<double> {
+    typedef double2 v2;
+    typedef dquad v4;
+    __device__ static __forceinline__ v2 pair(double a, double b) { return make_double2(a, b); }
+    __device__ static __forceinline__ v2 fma(v2 a, v2 b, v2 c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+    __device__ static __forceinline__ v2 add(v2 a, v2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+    __device__ static __forceinline__ v4 quad(double a, double b, double c, double d) { v4 q; q.x = a; q.y = b; q.z = c; q.w = d; return q; }
+};
+
 template <typename T> __device__ __forceinline__ T log_(T x);
 template <> __device__ __forceinline__ double log_<double>(double x) { return log(x); }
 template <> __device__ __forceinline__ float log_<float>(float x) { return logf(x); }
@@ -229,6 +250,9 @@ template <int D, int TX, int TY, typename ST, int MODE>
 struct Fused {
     typedef Lat<D> L;
     typedef typename StoreTraits<ST>::CT CT;
+    typedef Vec<CT> V;
+    typedef typename V::v2 V2;
+    typedef typename V::v4 V4;
     static constexpr int Q = L::Q;
     static constexpr int NT = TX * TY;
     static constexpr int R2X = TX + 4, R2Y = (D == 3 ? TY + 4 : 1), NA = R2X * R2Y;
@@ -238,13 +262,13 @@ struct Fused {
     // shared memory layout (in CT units)
     // ring buffers over planes: RS slots of rho, phi (tile + ring 2), MS of
     // mu and grad rho (tile + ring 1)
+    // (rho, phi) and (mu_rho, mu_phi) are stored as pairs, (grad rho,
+    // c_s^4/(4 rho)) as quads, so that a stencil neighbour is one load.
     static constexpr int RS = 6, MS = 4;
-    static constexpr int OFF_RHO = 0;
-    static constexpr int OFF_PHI = OFF_RHO + RS * NA;
-    static constexpr int OFF_MR = OFF_PHI + RS * NA;
-    static constexpr int OFF_MP = OFF_MR + MS * NB;
-    static constexpr int OFF_G = OFF_MP + MS * NB;
-    static constexpr int OFF_F = OFF_G + MS * (D + 1) * NB;  // per-thread population stash [Q][NT]
+    static constexpr int OFF_RP = 0;                         // pairs [RS][NA]
+    static constexpr int OFF_MU = OFF_RP + 2 * RS * NA;      // pairs [MS][NB]
+    static constexpr int OFF_G = OFF_MU + 2 * MS * NB;       // quads [MS][NB]
+    static constexpr int OFF_F = OFF_G + 4 * MS * NB;        // per-thread population stash [Q][NT]
     static constexpr int SMEM_ELEMS = OFF_F + (MODE == MODE_STEP ? Q * NT : 0);
     static constexpr size_t SMEM_BYTES = sizeof(CT) * SMEM_ELEMS;
 
@@ -299,8 +323,9 @@ struct Fused {
     {
         extern __shared__ __align__(16) unsigned char smem_raw[];
         CT *sm = reinterpret_cast<CT *>(smem_raw);
-        CT *rho_s = sm + OFF_RHO, *phi_s = sm + OFF_PHI, *mr_s = sm + OFF_MR, *mp_s = sm + OFF_MP;
-        CT *g_s = sm + OFF_G;
+        V2 *rp_s = reinterpret_cast<V2 *>(sm + OFF_RP);
+        V2 *mu_s = reinterpret_cast<V2 *>(sm + OFF_MU);
+        V4 *g_s = reinterpret_cast<V4 *>(sm + OFF_G);
 
         const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
         const int bX = P.bc[0], bY = (D == 3 ? P.bc[1] : 0), bM = (D == 3 ? P.bc[2] : P.bc[1]);
@@ -353,44 +378,41 @@ struct Fused {
                         rho = StoreTraits<ST>::shifted ? shift + sr : sr;
                         phi = sp;
                     }
-                    rho_s[slot5(mA) * NA + r] = rho;
-                    phi_s[slot5(mA) * NA + r] = phi;
+                    rp_s[slot5(mA) * NA + r] = V::pair(rho, phi);
                 } else {
                     // ---------------- phase B: chemical potentials of plane mB on tile + ring 1
                     const int s = w - nA;
                     const int sB = slot3(mB);
                     const int ox = s % R1X - 1, oy = (D == 3 ? s / R1X - 1 : 0);
                     const int c0 = idx2(ox, oy);
-                    const CT r0 = rho_s[slot5(mB) * NA + c0], p0 = phi_s[slot5(mB) * NA + c0];
-                    CT lr = 0, lp = 0, gx = 0, gy = 0, gz = 0;
+                    const V2 cp = rp_s[slot5(mB) * NA + c0];
+                    const CT r0 = cp.x, p0 = cp.y;
+                    const V2 ncp = V::pair(-r0, -p0);
+                    V2 lap = V::pair((CT)0, (CT)0);
+                    CT gx = 0, gy = 0, gz = 0;
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
+                        if (L::nnz(i) == 0) continue;
                         const int k = slot5(mB + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i));
                         const CT wi = (CT)L::w(i);
-                        const CT rv = rho_s[k];
-                        lr += wi * (rv - r0);
-                        lp += wi * (phi_s[k] - p0);
-                        if (L::cx(i)) gx += wi * (CT)L::cx(i) * rv;
-                        if (L::cy(i)) gy += wi * (CT)L::cy(i) * rv;
-                        if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * rv;
+                        const V2 v = rp_s[k];
+                        lap = V::fma(V::pair(wi, wi), V::add(v, ncp), lap);
+                        if (L::cx(i)) gx += wi * (CT)L::cx(i) * v.x;
+                        if (L::cy(i)) gy += wi * (CT)L::cy(i) * v.x;
+                        if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * v.x;
                     }
-                    lr *= (CT)6;
-                    lp *= (CT)6;
+                    const CT lr = (CT)6 * lap.x;
+                    const CT lp = (CT)6 * lap.y;
                     CT mr, mp;
                     mu_wells<CT>(P, r0, p0, mr, mp);
                     if (StoreTraits<ST>::shifted && r0 < coef<CT>(P).rho_switch)
                         mr = (CT)mu_eos_gas(P, (float)r0) + mr;  // FP64 gas side
                     else
                         mr = mu_eos<CT>(P, r0) + mr;
-                    mr_s[sB * NB + s] = mr - coef<CT>(P).Kr * lr - coef<CT>(P).Kx * lp;
-                    mp_s[sB * NB + s] = mp - coef<CT>(P).Kp * lp - coef<CT>(P).Kx * lr;
-                    if (P.force_form == 1) {
-                        // grad rho and c_s^4/(4 rho) of this ring-1 node (lattice-consistent force)
-                        g_s[(sB * (D + 1) + 0) * NB + s] = (CT)3 * gx;
-                        g_s[(sB * (D + 1) + 1) * NB + s] = (CT)3 * gy;
-                        if (D == 3) g_s[(sB * (D + 1) + 2) * NB + s] = (CT)3 * gz;
-                        g_s[(sB * (D + 1) + D) * NB + s] = (CT)(1.0 / 36.0) / r0;
-                    }
+                    mu_s[sB * NB + s] = V::pair(mr - coef<CT>(P).Kr * lr - coef<CT>(P).Kx * lp,
+                                                mp - coef<CT>(P).Kp * lp - coef<CT>(P).Kx * lr);
+                    if (P.force_form == 1)  // grad rho and c_s^4/(4 rho) (lattice-consistent force)
+                        g_s[sB * NB + s] = V::quad((CT)3 * gx, (CT)3 * gy, (CT)3 * gz, (CT)(1.0 / 36.0) / r0);
                 }
             }
             __syncthreads();
@@ -399,43 +421,53 @@ struct Fused {
                 const int tx = tid % TX, ty = tid / TX;
                 const int x = x0 + tx, y = y0 + ty;
                 if (x < PX && (D == 2 || y < PY))
-                    node(P, A, fs, gs, rho_s, phi_s, mr_s, mp_s, g_s, sm + OFF_F + tid, x, y, mC, tx, ty);
+                    node(P, A, fs, gs, rp_s, mu_s, g_s, sm + OFF_F + tid, x, y, mC, tx, ty);
             }
         }
     }
 
     __device__ static void node(const DevParams &P, const LaunchArgs &A, const ST *fs, const ST *gs,
-                                const CT *rho_s, const CT *phi_s, const CT *mr_s, const CT *mp_s,
-                                const CT *g_s, CT *fq, int x, int y, int m, int tx, int ty)
+                                const V2 *rp_s, const V2 *mu_s, const V4 *g_s, CT *fq, int x, int y, int m,
+                                int tx, int ty)
     {
         const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
         const long long n = (long long)x + (long long)PX * ((long long)y + (long long)PY * m);
         const int ox = tx, oy = (D == 3 ? ty : 0);
-        const CT rho = rho_s[slot5(m) * NA + idx2(ox, oy)];
-        const CT phi = phi_s[slot5(m) * NA + idx2(ox, oy)];
+        const V2 rp0 = rp_s[slot5(m) * NA + idx2(ox, oy)];
+        const CT rho = rp0.x, phi = rp0.y;
         const Coef<CT> &K = coef<CT>(P);
         const CT shift = K.rho_ref;
 
-        // gradients at the node: grad mu_rho, grad mu_phi (ring-1 tiles),
-        // grad rho and grad phi (ring-2 tiles)
-        CT gm[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, gr[3] = {0, 0, 0}, gf[3] = {0, 0, 0};
+        // gradients at the node: grad (mu_rho, mu_phi) from the ring-1 pairs,
+        // grad (rho, phi) from the ring-2 pairs (the latter only for the
+        // potential-form force and the field output), as packed pairs
+        V2 gmu[3], grp[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { gmu[a] = V::pair((CT)0, (CT)0); grp[a] = V::pair((CT)0, (CT)0); }
+        const bool need_grp = (MODE == MODE_FIELDS) || P.force_form == 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             if (L::nnz(i) == 0) continue;
-            const int k1 = slot3(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i));
-            const int k2 = slot5(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i));
+            const V2 vm = mu_s[slot3(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i))];
             const CT wi = (CT)L::w(i);
-            const CT vm = mr_s[k1], vp = mp_s[k1], vr = rho_s[k2], vf = phi_s[k2];
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 const int ca = L::c(i, a);
-                if (ca) {
-                    gm[a] += wi * (CT)ca * vm;
-                    gp[a] += wi * (CT)ca * vp;
-                    gr[a] += wi * (CT)ca * vr;
-                    gf[a] += wi * (CT)ca * vf;
+                if (ca) gmu[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vm, gmu[a]);
+            }
+            if (need_grp) {
+                const V2 vr = rp_s[slot5(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const int ca = L::c(i, a);
+                    if (ca) grp[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vr, grp[a]);
                 }
             }
+        }
+        CT gm[3], gp[3], gr[3], gf[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gm[a] = gmu[a].x; gp[a] = gmu[a].y; gr[a] = grp[a].x; gf[a] = grp[a].y;
         }
         CT F[3] = {0, 0, 0};
 #pragma unroll
@@ -459,10 +491,9 @@ struct Fused {
                 const CT wi3 = (CT)(3.0 * L::w(i));
                 const int sp_ = slot3(m + L::pM(i));
                 const int kp = idx1(ox + L::pX(i), oy + L::pY(i));
-                CT Gp[3];
-#pragma unroll
-                for (int b = 0; b < D; ++b) Gp[b] = g_s[(sp_ * (D + 1) + b) * NB + kp];
-                const CT sj = g_s[(sp_ * (D + 1) + D) * NB + kp];
+                const V4 gq = g_s[sp_ * NB + kp];
+                const CT Gp[3] = {gq.x, gq.y, gq.z};
+                const CT sj = gq.w;
                 CT cG = 0;
 #pragma unroll
                 for (int b = 0; b < D; ++b)
@@ -475,12 +506,14 @@ struct Fused {
 #pragma unroll
                 for (int a = 0; a < D; ++a) dT[a] += q * Gp[a];
             }
-            const int s0 = slot3(m), k0 = idx1(ox, oy);
+            const V4 g0 = g_s[slot3(m) * NB + idx1(ox, oy)];
+            const CT G0[3] = {g0.x, g0.y, g0.z};
 #pragma unroll
             for (int a = 0; a < D; ++a)
-                F[a] += cs2 * ((CT)1.5 * g_s[(s0 * (D + 1) + a) * NB + k0] - (CT)0.5 * AG[a]) + dT[a];
+                F[a] += cs2 * ((CT)1.5 * G0[a] - (CT)0.5 * AG[a]) + dT[a];
         }
-        const CT mu_phi = mp_s[slot3(m) * NB + idx1(ox, oy)];
+        const V2 mu0 = mu_s[slot3(m) * NB + idx1(ox, oy)];
+        const CT mu_phi = mu0.y;
 
         if (MODE == MODE_INIT) {
             init_node(P, A, n, x, y, m, rho, phi, mu_phi, F);
@@ -519,7 +552,7 @@ struct Fused {
         if (!(rho > (CT)0)) bad |= ERR_RHO;
 
         if (MODE == MODE_FIELDS) {
-            fields_node(P, A, n, rho, phi, j, F, gr, gf, mr_s[slot3(m) * NB + idx1(ox, oy)], mu_phi);
+            fields_node(P, A, n, rho, phi, j, F, gr, gf, mu0.x, mu_phi);
             if (bad) atomicOr(P.err, bad);
             return;
         }
