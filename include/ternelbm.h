@@ -155,6 +155,32 @@ int tel_info(const tel_ctx *ctx, double out[10]);
 int tel_coexistence(double a, double b, double R, double T, double out[4]);
 int tel_temperature_for_ratio(double a, double b, double R, double ratio, double *T);
 
+/* Batched D2Q9 lattices (SURVEY "next" row: many uneven cases in one
+ * persistent launch).  ncases independent D2Q9 lattices of nx[c] x ny[c]
+ * nodes with their own parameters (one precision for all) live in one set of
+ * device buffers; each tel_batch_step step is ONE launch of a persistent
+ * kernel that walks a work list of (case, tile, chunk) items, largest cases
+ * first, so that small lattices no longer leave the GPU idle.  Pairs of steps
+ * are replayed from a captured CUDA graph.  Each case evolves exactly as a
+ * tel_create lattice with the same parameters would (same per-node
+ * arithmetic).  tel_batch_tune times every (tile width 32/64, chunk
+ * 8/16/32/64) configuration on steps_per_config real steps (plus one warm-up
+ * step each: they advance the state) and keeps the fastest; out = {tile width,
+ * chunk, steps advanced}.  tel_batch_init must come before any step (fields as
+ * for tel_init); tel_batch_fields returns host fields of case c and reports
+ * TEL_EUNSTABLE if any case flagged a node.  tel_batch_info out = {ncases,
+ * total nodes, tile width, chunk, work items, persistent CTAs}. */
+typedef struct tel_batch tel_batch;
+int tel_batch_create(int ncases, const int *nx, const int *ny, const tel_params *params, tel_batch **out);
+void tel_batch_destroy(tel_batch *b);
+const char *tel_batch_last_error(const tel_batch *b);
+int tel_batch_init(tel_batch *b, int c, const double *rho, const double *phi, const double *u);
+int tel_batch_step(tel_batch *b, int nsteps);
+int tel_batch_sync(tel_batch *b);
+int tel_batch_fields(tel_batch *b, int c, double *rho, double *phi, double *u, double *p);
+int tel_batch_tune(tel_batch *b, int steps_per_config, int out[3]);
+int tel_batch_info(const tel_batch *b, double out[6]);
+
 /* Allocation-free field extraction (the paper has no counterpart; this is a
  * service of the library).  For callers that cannot let a library allocate
  * device memory -- applications that give the whole device to their own

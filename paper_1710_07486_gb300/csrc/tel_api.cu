@@ -625,3 +625,368 @@ extern "C" int tel_fields_noalloc(int lattice, int nx, int ny, int nz, const tel
     if (flag) return noalloc_fail(TEL_EUNSTABLE, "unstable node(s) flagged on the device (bits 0x%x)", flag);
     return TEL_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched D2Q9 lattices: many independent cases advanced by one persistent
+// kernel launch per step (see batch_kernel), with an autotuned tile width and
+// chunk length, and CUDA-graph replay of pairs of steps.
+// ---------------------------------------------------------------------------
+struct tel_batch {
+    int ncases, precision;
+    bool fast;
+    int *nx, *ny;
+    long long *off;              // element offset of each case's arrays in one buffer
+    long long total;             // total nodes
+    tel::DevParams *hP;          // host copies (chunk set by the tuner)
+    tel::DevParams *dP;          // device parameter blocks
+    tel::LaunchArgs *dA[2];      // device launch arguments: src = buffer k, dst = buffer 1-k
+    void *f[2], *g[2];
+    unsigned *d_err;             // one error word per case
+    int4 *d_items;
+    int nitems, grid, tx, chunk;
+    int cur;
+    double *scratch;             // fields staging (largest case)
+    size_t scratch_elems;
+    cudaStream_t stream;
+    cudaGraphExec_t graph[2];    // two steps starting from buffer 0 / 1
+    int initialized;
+    char msg[512];
+};
+
+static int bfail(tel_batch *b, int code, const char *fmt, ...)
+{
+    char *dst = b ? b->msg : g_create_msg;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define BCUDA(b, expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) return bfail((b), TEL_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+static void batch_free_graphs(tel_batch *b)
+{
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) { cudaGraphExecDestroy(b->graph[k]); b->graph[k] = nullptr; }
+}
+
+// Work list for tile width tx and chunk length ch: every (case, tile, chunk),
+// largest cases first so that the tail of the persistent loop is short.
+static int batch_build(tel_batch *b, int tx, int ch)
+{
+    int n = 0;
+    for (int c = 0; c < b->ncases; ++c) n += ((b->nx[c] + tx - 1) / tx) * ((b->ny[c] + ch - 1) / ch);
+    int4 *h = new (std::nothrow) int4[n];
+    int *order = new (std::nothrow) int[b->ncases];
+    if (!h || !order) { delete[] h; delete[] order; return bfail(b, TEL_ENOMEM, "host allocation failed"); }
+    for (int c = 0; c < b->ncases; ++c) order[c] = c;
+    for (int i = 1; i < b->ncases; ++i)  // insertion sort by node count, descending
+        for (int j = i; j > 0 && (long long)b->nx[order[j]] * b->ny[order[j]] >
+                                     (long long)b->nx[order[j - 1]] * b->ny[order[j - 1]]; --j) {
+            const int t = order[j]; order[j] = order[j - 1]; order[j - 1] = t;
+        }
+    int k = 0;
+    for (int oi = 0; oi < b->ncases; ++oi) {
+        const int c = order[oi];
+        const int tiles = (b->nx[c] + tx - 1) / tx, chunks = (b->ny[c] + ch - 1) / ch;
+        for (int bm = 0; bm < chunks; ++bm)
+            for (int bx = 0; bx < tiles; ++bx) h[k++] = make_int4(c, bx, bm, 0);
+    }
+    delete[] order;
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_items, sizeof(int4) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_items, h, sizeof(int4) * (size_t)n, cudaMemcpyHostToDevice);
+    delete[] h;
+    if (e != cudaSuccess) return bfail(b, TEL_ECUDA, "work list upload: %s", cudaGetErrorString(e));
+    for (int c = 0; c < b->ncases; ++c) b->hP[c].chunk = ch;
+    BCUDA(b, cudaMemcpy(b->dP, b->hP, sizeof(tel::DevParams) * (size_t)b->ncases, cudaMemcpyHostToDevice));
+    int nb = tel::batch_blocks_per_sm(b->precision, tx, b->fast);
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = nb * nsm < n ? nb * nsm : n;
+    b->nitems = n;
+    b->tx = tx;
+    b->chunk = ch;
+    batch_free_graphs(b);
+    return TEL_OK;
+}
+
+extern "C" int tel_batch_create(int ncases, const int *nx, const int *ny, const tel_params *params, tel_batch **out)
+{
+    if (!out) return bfail(nullptr, TEL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ncases < 1 || !nx || !ny || !params) return bfail(nullptr, TEL_EINVAL, "bad batch arguments");
+    const int prec = params[0].precision;
+    bool walls = false;
+    long long total = 0;
+    for (int c = 0; c < ncases; ++c) {
+        int rc = validate(TEL_D2Q9, nx[c], ny[c], 1, &params[c]);
+        if (rc) return bfail(nullptr, rc, "case %d: %s", c, g_create_msg);
+        if (params[c].precision != prec) return bfail(nullptr, TEL_EINVAL, "all cases must share one precision");
+        walls = walls || params[c].bc[0] || params[c].bc[1];
+        total += (long long)nx[c] * ny[c];
+    }
+    tel_batch *b = new (std::nothrow) tel_batch();
+    if (!b) return bfail(nullptr, TEL_ENOMEM, "host allocation failed");
+    std::memset(b, 0, sizeof(*b));
+    b->ncases = ncases;
+    b->precision = prec;
+    b->total = total;
+    b->fast = !walls && 9LL * total < (1LL << 31);
+    b->nx = new (std::nothrow) int[ncases];
+    b->ny = new (std::nothrow) int[ncases];
+    b->off = new (std::nothrow) long long[ncases];
+    b->hP = new (std::nothrow) tel::DevParams[ncases];
+    if (!b->nx || !b->ny || !b->off || !b->hP) { tel_batch_destroy(b); return bfail(nullptr, TEL_ENOMEM, "host allocation failed"); }
+    const size_t es = prec == TEL_FP64 ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&b->f[k], es * 9 * (size_t)total);
+        if (e == cudaSuccess) e = cudaMalloc(&b->g[k], es * 9 * (size_t)total);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(unsigned) * (size_t)ncases);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dP, sizeof(tel::DevParams) * (size_t)ncases);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&b->dA[k], sizeof(tel::LaunchArgs) * (size_t)ncases);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(unsigned) * (size_t)ncases);
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        tel_batch_destroy(b);
+        return bfail(nullptr, oom ? TEL_ENOMEM : TEL_ECUDA, "batch device setup: %s", cudaGetErrorString(e));
+    }
+    long long o = 0;
+    tel::LaunchArgs *hA[2];
+    hA[0] = new (std::nothrow) tel::LaunchArgs[ncases];
+    hA[1] = new (std::nothrow) tel::LaunchArgs[ncases];
+    if (!hA[0] || !hA[1]) { delete[] hA[0]; delete[] hA[1]; tel_batch_destroy(b); return bfail(nullptr, TEL_ENOMEM, "host allocation failed"); }
+    for (int c = 0; c < ncases; ++c) {
+        b->nx[c] = nx[c];
+        b->ny[c] = ny[c];
+        b->off[c] = o;
+        double co[4];
+        if (tel_coexistence(params[c].a, params[c].b, params[c].R, params[c].T, co) != TEL_OK) {
+            delete[] hA[0]; delete[] hA[1]; tel_batch_destroy(b);
+            return bfail(nullptr, TEL_EINVAL, "case %d: no liquid-gas coexistence at T=%g", c, params[c].T);
+        }
+        tel_params pp = params[c];
+        pp.bc[2] = TEL_PERIODIC;
+        fill_devparams(TEL_D2Q9, nx[c], ny[c], 1, pp, co, b->hP[c]);
+        b->hP[c].err = b->d_err + c;
+        const size_t base = es * 9 * (size_t)o;
+        for (int k = 0; k < 2; ++k) {
+            tel::LaunchArgs A{};
+            A.fsrc = (char *)b->f[k] + base; A.gsrc = (char *)b->g[k] + base;
+            A.fdst = (char *)b->f[1 - k] + base; A.gdst = (char *)b->g[1 - k] + base;
+            hA[k][c] = A;
+        }
+        o += (long long)nx[c] * ny[c];
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = cudaMemcpy(b->dA[k], hA[k], sizeof(tel::LaunchArgs) * (size_t)ncases, cudaMemcpyHostToDevice);
+    delete[] hA[0];
+    delete[] hA[1];
+    if (e != cudaSuccess) { tel_batch_destroy(b); return bfail(nullptr, TEL_ECUDA, "batch upload: %s", cudaGetErrorString(e)); }
+    int rc = batch_build(b, 64, 16);
+    if (rc) { std::snprintf(g_create_msg, sizeof(g_create_msg), "%s", b->msg); tel_batch_destroy(b); return rc; }
+    *out = b;
+    return TEL_OK;
+}
+
+extern "C" void tel_batch_destroy(tel_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free_graphs(b);
+    for (int k = 0; k < 2; ++k) {
+        if (b->f[k]) cudaFree(b->f[k]);
+        if (b->g[k]) cudaFree(b->g[k]);
+        if (b->dA[k]) cudaFree(b->dA[k]);
+    }
+    if (b->d_err) cudaFree(b->d_err);
+    if (b->dP) cudaFree(b->dP);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->scratch) cudaFree(b->scratch);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete[] b->nx; delete[] b->ny; delete[] b->off; delete[] b->hP;
+    delete b;
+}
+
+extern "C" const char *tel_batch_last_error(const tel_batch *b) { return b ? b->msg : g_create_msg; }
+
+static tel::LaunchArgs batch_case_args(const tel_batch *b, int c, int k)
+{
+    const size_t es = b->precision == TEL_FP64 ? sizeof(double) : sizeof(float);
+    const size_t base = es * 9 * (size_t)b->off[c];
+    tel::LaunchArgs A{};
+    A.fsrc = (char *)b->f[k] + base; A.gsrc = (char *)b->g[k] + base;
+    A.fdst = (char *)b->f[1 - k] + base; A.gdst = (char *)b->g[1 - k] + base;
+    return A;
+}
+
+static int batch_scratch(tel_batch *b, size_t elems)
+{
+    if (b->scratch_elems >= elems) return TEL_OK;
+    if (b->scratch) { BCUDA(b, cudaStreamSynchronize(b->stream)); cudaFree(b->scratch); b->scratch = nullptr; }
+    cudaError_t e = cudaMalloc(&b->scratch, elems * sizeof(double));
+    if (e != cudaSuccess) { cudaGetLastError(); return bfail(b, TEL_ENOMEM, "scratch: %s", cudaGetErrorString(e)); }
+    b->scratch_elems = elems;
+    return TEL_OK;
+}
+
+extern "C" int tel_batch_init(tel_batch *b, int c, const double *rho, const double *phi, const double *u)
+{
+    if (!b) return TEL_EINVAL;
+    if (c < 0 || c >= b->ncases || !rho || !phi || !u) return bfail(b, TEL_EINVAL, "tel_batch_init: bad case or NULL field");
+    if (b->cur != 0) return bfail(b, TEL_ESTATE, "tel_batch_init after stepping with an odd step count");
+    const size_t N = (size_t)b->nx[c] * b->ny[c];
+    int rc = batch_scratch(b, 4 * N);
+    if (rc) return rc;
+    double *d = b->scratch;
+    BCUDA(b, cudaMemcpyAsync(d, rho, N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    BCUDA(b, cudaMemcpyAsync(d + N, phi, N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    BCUDA(b, cudaMemcpyAsync(d + 2 * N, u, 2 * N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    tel::LaunchArgs A = batch_case_args(b, c, 1);  // writes buffer 0
+    A.in_rho = d; A.in_phi = d + N; A.in_u = d + 2 * N;
+    A.fsrc = A.gsrc = nullptr;
+    BCUDA(b, tel::launch_d2q9(b->precision, tel::MODE_INIT, b->hP[c], A, b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    b->initialized = 1;
+    return TEL_OK;
+}
+
+static int batch_launch(tel_batch *b, int k)
+{
+    BCUDA(b, tel::launch_d2q9_batch(b->precision, b->tx, b->fast, b->dP, b->dA[k], b->d_items, b->nitems, b->grid,
+                                    b->stream));
+    return TEL_OK;
+}
+
+extern "C" int tel_batch_step(tel_batch *b, int nsteps)
+{
+    if (!b) return TEL_EINVAL;
+    if (nsteps < 0) return bfail(b, TEL_EINVAL, "nsteps must be >= 0");
+    if (!b->initialized) return bfail(b, TEL_ESTATE, "tel_batch_step before tel_batch_init");
+    int s = 0;
+    if (nsteps >= 2) {
+        // two steps (cur -> 1-cur -> cur) as one captured graph, replayed
+        const int k = b->cur;
+        if (!b->graph[k]) {
+            int rc = batch_launch(b, k);  // first launch outside capture (kernel attributes)
+            if (rc) return rc;
+            rc = batch_launch(b, 1 - k);
+            if (rc) return rc;
+            s = 2;
+            cudaGraph_t gr;
+            BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            int r1 = batch_launch(b, k), r2 = r1 ? r1 : batch_launch(b, 1 - k);
+            cudaError_t ec = cudaStreamEndCapture(b->stream, &gr);
+            if (r1 || r2) return r1 ? r1 : r2;
+            if (ec != cudaSuccess) return bfail(b, TEL_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+            cudaError_t ei = cudaGraphInstantiate(&b->graph[k], gr, 0);
+            cudaGraphDestroy(gr);
+            if (ei != cudaSuccess) return bfail(b, TEL_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+        }
+        for (; s + 2 <= nsteps; s += 2) BCUDA(b, cudaGraphLaunch(b->graph[k], b->stream));
+    }
+    for (; s < nsteps; ++s) {
+        int rc = batch_launch(b, b->cur);
+        if (rc) return rc;
+        b->cur = 1 - b->cur;
+    }
+    return TEL_OK;
+}
+
+extern "C" int tel_batch_sync(tel_batch *b)
+{
+    if (!b) return TEL_EINVAL;
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    unsigned *h = new (std::nothrow) unsigned[b->ncases];
+    if (!h) return bfail(b, TEL_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaMemcpy(h, b->d_err, sizeof(unsigned) * (size_t)b->ncases, cudaMemcpyDeviceToHost);
+    int bad = -1;
+    for (int c = 0; c < b->ncases && e == cudaSuccess; ++c)
+        if (h[c]) { bad = c; break; }
+    delete[] h;
+    if (e != cudaSuccess) return bfail(b, TEL_ECUDA, "error words: %s", cudaGetErrorString(e));
+    if (bad >= 0) {
+        cudaMemset(b->d_err, 0, sizeof(unsigned) * (size_t)b->ncases);
+        return bfail(b, TEL_EUNSTABLE, "case %d flagged an unstable node", bad);
+    }
+    return TEL_OK;
+}
+
+extern "C" int tel_batch_fields(tel_batch *b, int c, double *rho, double *phi, double *u, double *p)
+{
+    if (!b) return TEL_EINVAL;
+    if (c < 0 || c >= b->ncases) return bfail(b, TEL_EINVAL, "tel_batch_fields: bad case");
+    if (!b->initialized) return bfail(b, TEL_ESTATE, "tel_batch_fields before tel_batch_init");
+    const size_t N = (size_t)b->nx[c] * b->ny[c];
+    int rc = batch_scratch(b, 5 * N);
+    if (rc) return rc;
+    double *d = b->scratch;
+    tel::LaunchArgs A = batch_case_args(b, c, b->cur);
+    A.fdst = A.gdst = nullptr;
+    A.out_rho = rho ? d : nullptr; A.out_phi = phi ? d + N : nullptr;
+    A.out_u = u ? d + 2 * N : nullptr; A.out_p = p ? d + 4 * N : nullptr;
+    BCUDA(b, tel::launch_d2q9(b->precision, tel::MODE_FIELDS, b->hP[c], A, b->stream));
+    if (rho) BCUDA(b, cudaMemcpyAsync(rho, d, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    if (phi) BCUDA(b, cudaMemcpyAsync(phi, d + N, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    if (u) BCUDA(b, cudaMemcpyAsync(u, d + 2 * N, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    if (p) BCUDA(b, cudaMemcpyAsync(p, d + 4 * N, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    return tel_batch_sync(b);
+}
+
+extern "C" int tel_batch_tune(tel_batch *b, int steps_per_config, int out[3])
+{
+    if (!b) return TEL_EINVAL;
+    if (steps_per_config < 1) return bfail(b, TEL_EINVAL, "steps_per_config must be >= 1");
+    if (!b->initialized) return bfail(b, TEL_ESTATE, "tel_batch_tune before tel_batch_init");
+    static const int txs[2] = {32, 64}, chs[4] = {8, 16, 32, 64};
+    cudaEvent_t e0, e1;
+    BCUDA(b, cudaEventCreate(&e0));
+    BCUDA(b, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int btx = 64, bch = 16, done = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int q = 0; q < 4; ++q) {
+            int rc = batch_build(b, txs[a], chs[q]);
+            if (rc) return rc;
+            rc = batch_launch(b, b->cur);  // warm-up (also a real step)
+            if (rc) return rc;
+            b->cur = 1 - b->cur;
+            ++done;
+            BCUDA(b, cudaEventRecord(e0, b->stream));
+            for (int s = 0; s < steps_per_config; ++s) {
+                rc = batch_launch(b, b->cur);
+                if (rc) return rc;
+                b->cur = 1 - b->cur;
+                ++done;
+            }
+            BCUDA(b, cudaEventRecord(e1, b->stream));
+            BCUDA(b, cudaEventSynchronize(e1));
+            float ms = 0;
+            BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; btx = txs[a]; bch = chs[q]; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc = batch_build(b, btx, bch);
+    if (rc) return rc;
+    if (out) { out[0] = btx; out[1] = bch; out[2] = done; }
+    return TEL_OK;
+}
+
+extern "C" int tel_batch_info(const tel_batch *b, double out[6])
+{
+    if (!b || !out) return TEL_EINVAL;
+    out[0] = b->ncases; out[1] = (double)b->total; out[2] = b->tx; out[3] = b->chunk; out[4] = b->nitems; out[5] = b->grid;
+    return TEL_OK;
+}

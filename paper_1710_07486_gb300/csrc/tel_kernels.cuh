@@ -246,7 +246,9 @@ template <> struct StoreTraits<float> { typedef float CT; static constexpr bool 
 // ---------------------------------------------------------------------------
 // The fused kernel.
 // ---------------------------------------------------------------------------
-template <int D, int TX, int TY, typename ST, int MODE>
+// FAST: no bounce-back axis and Q N < 2^31, so pulls need no wall test and
+// their indices fit 32 bits.
+template <int D, int TX, int TY, typename ST, int MODE, bool FAST>
 struct Fused {
     typedef Lat<D> L;
     typedef typename StoreTraits<ST>::CT CT;
@@ -302,12 +304,28 @@ struct Fused {
                 int sc = q[a] - c;
                 if (a == 1 && D == 2) sc = 0;
                 bool o = false;
-                if (sc < 0) { if (wall[a]) o = true; else sc += ext[a]; }
-                else if (sc >= ext[a]) { if (wall[a]) o = true; else sc -= ext[a]; }
+                if (FAST) {
+                    if (sc < 0) sc += ext[a];
+                    else if (sc >= ext[a]) sc -= ext[a];
+                } else {
+                    if (sc < 0) { if (wall[a]) o = true; else sc += ext[a]; }
+                    else if (sc >= ext[a]) { if (wall[a]) o = true; else sc -= ext[a]; }
+                }
                 b.off[a][c + 1] = sc * stride[a];
                 if (o) b.out |= 1u << (3 * a + c + 1);
             }
         }
+    }
+
+    // population i pulled into the node described by b
+    __device__ static __forceinline__ CT pull(const ST *base, const Nbr &b, long long N, int i)
+    {
+        if (FAST) {
+            const int cX = L::pX(i) + 1, cY = L::pY(i) + 1, cM = L::pM(i) + 1;
+            const unsigned k = (unsigned)i * (unsigned)N + (unsigned)(b.off[0][cX] + b.off[1][cY] + b.off[2][cM]);
+            return (CT)__ldg(base + k);
+        }
+        return (CT)__ldg(base + src_index(b, N, i));
     }
 
     // global index of population i pulled into the node described by b
@@ -319,7 +337,14 @@ struct Fused {
         return (long long)i * N + (b.off[0][cX] + b.off[1][cY] + b.off[2][cM]);
     }
 
-    __device__ static void run(const DevParams P, const LaunchArgs A)
+    __device__ static void run(const DevParams &P, const LaunchArgs &A)
+    {
+        run_tile(P, A, blockIdx.x, D == 3 ? blockIdx.y : 0, D == 3 ? blockIdx.z : blockIdx.y);
+    }
+
+    // One CTA's work: the tile (bx, by) of the plane normal to the marching
+    // axis, through chunk bm of planes.
+    __device__ static void run_tile(const DevParams &P, const LaunchArgs &A, int bx, int by, int bm)
     {
         extern __shared__ __align__(16) unsigned char smem_raw[];
         CT *sm = reinterpret_cast<CT *>(smem_raw);
@@ -330,9 +355,9 @@ struct Fused {
         const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
         const int bX = P.bc[0], bY = (D == 3 ? P.bc[1] : 0), bM = (D == 3 ? P.bc[2] : P.bc[1]);
         const int tid = threadIdx.x;
-        const int x0 = blockIdx.x * TX;
-        const int y0 = (D == 3 ? blockIdx.y * TY : 0);
-        const int m0 = (D == 3 ? blockIdx.z : blockIdx.y) * P.chunk;
+        const int x0 = bx * TX;
+        const int y0 = (D == 3 ? by * TY : 0);
+        const int m0 = bm * P.chunk;
         const int m1 = min(m0 + P.chunk, PM);
         const CT shift = coef<CT>(P).rho_ref;
         const ST *fs = reinterpret_cast<const ST *>(A.fsrc);
@@ -372,9 +397,9 @@ struct Fused {
                         make_nbr(P, PX, PY, PM, xx, yy, mm, nb);
                         CT sr = 0, sp = 0;
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) sr += (CT)__ldg(fs + src_index(nb, P.N, i));
+                        for (int i = 0; i < Q; ++i) sr += pull(fs, nb, P.N, i);
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) sp += (CT)__ldg(gs + src_index(nb, P.N, i));
+                        for (int i = 0; i < Q; ++i) sp += pull(gs, nb, P.N, i);
                         rho = StoreTraits<ST>::shifted ? shift + sr : sr;
                         phi = sp;
                     }
@@ -530,7 +555,7 @@ struct Fused {
         CT Pi[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const CT fi = (CT)__ldg(fs + src_index(nb, P.N, i));
+            const CT fi = pull(fs, nb, P.N, i);
             if (MODE == MODE_STEP) fq[i * NT] = fi;
             fsum += fi;
             if (L::cx(i)) { j[0] += (CT)L::cx(i) * fi; Pi[0] += fi; }
@@ -575,7 +600,7 @@ struct Fused {
         for (int i = 0; i < Q; ++i) {
             if (StoreTraits<ST>::shifted && i == L::REST) continue;
             const CT ge = (i == L::REST) ? phi - others : geq_of(i, Gm3, phi, up, uu);
-            const CT gi = (CT)__ldg(gs + src_index(nb, P.N, i));
+            const CT gi = pull(gs, nb, P.N, i);
             const CT go = gi - (gi - ge) * itg;
             if (StoreTraits<ST>::shifted) goth += (CT)(ST)go;
             gd[(long long)i * P.N + n] = (ST)go;
@@ -789,11 +814,42 @@ struct Fused {
 template <typename ST> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<float> { static constexpr int value = TEL_MIN_BLOCKS_FP32; };
 
-template <int D, int TX, int TY, typename ST, int MODE>
+template <int D, int TX, int TY, typename ST, int MODE, bool FAST>
 __global__ void __launch_bounds__(TX * TY, MinBlocks<ST>::value) fused_kernel(const DevParams P, const LaunchArgs A)
 {
-    Fused<D, TX, TY, ST, MODE>::run(P, A);
+    Fused<D, TX, TY, ST, MODE, FAST>::run(P, A);
 }
+
+// Batched persistent D2Q9 step: each CTA walks a work list of (case, tile,
+// chunk) items over many independent lattices; each case's parameter block
+// and buffers are copied into shared memory before its item runs.
+template <int TX, typename ST, bool FAST>
+__global__ void __launch_bounds__(TX, MinBlocks<ST>::value)
+    batch_kernel(const DevParams *Ps, const LaunchArgs *As, const int4 *items, int nitems)
+{
+    __shared__ DevParams Psh;
+    __shared__ LaunchArgs Ash;
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const int4 it = items[w];  // (case, tile along x, chunk along y, -)
+        __syncthreads();           // the previous item is done with shared memory
+        {
+            const int *src = reinterpret_cast<const int *>(Ps + it.x);
+            int *dst = reinterpret_cast<int *>(&Psh);
+            for (int k = threadIdx.x; k < (int)(sizeof(DevParams) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+            const int *sa = reinterpret_cast<const int *>(As + it.x);
+            int *da = reinterpret_cast<int *>(&Ash);
+            for (int k = threadIdx.x; k < (int)(sizeof(LaunchArgs) / sizeof(int)); k += blockDim.x) da[k] = sa[k];
+        }
+        __syncthreads();
+        Fused<2, TX, 1, ST, MODE_STEP, FAST>::run_tile(Psh, Ash, it.y, 0, it.z);
+    }
+}
+
+// Batched launcher (tel_d2q9.cu): tx in {32, 64}; grid = persistent CTAs.
+cudaError_t launch_d2q9_batch(int precision, int tx, bool fast, const DevParams *Ps, const LaunchArgs *As,
+                              const int4 *items, int nitems, int grid, cudaStream_t s);
+// Resident CTAs per SM of the batched kernel with shape tx.
+int batch_blocks_per_sm(int precision, int tx, bool fast);
 
 // Tile shapes and launcher (defined per lattice in tel_d2q9.cu / tel_d3q27.cu).
 cudaError_t launch_d2q9(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s);

@@ -5,13 +5,13 @@
 
 namespace tel {
 
-template <int D, int TX, int TY, typename ST, int MODE>
+template <int D, int TX, int TY, typename ST, int MODE, bool FAST>
 static cudaError_t launch_one(const DevParams &P, const LaunchArgs &A, cudaStream_t s)
 {
-    typedef Fused<D, TX, TY, ST, MODE> K;
+    typedef Fused<D, TX, TY, ST, MODE, FAST> K;
     static bool configured = false;  // per-instantiation: opt in to > 48 KB of shared memory
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(fused_kernel<D, TX, TY, ST, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(fused_kernel<D, TX, TY, ST, MODE, FAST>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -25,21 +25,31 @@ static cudaError_t launch_one(const DevParams &P, const LaunchArgs &A, cudaStrea
     } else {
         grid.y = nch;
     }
-    fused_kernel<D, TX, TY, ST, MODE><<<grid, K::NT, K::SMEM_BYTES, s>>>(P, A);
+    fused_kernel<D, TX, TY, ST, MODE, FAST><<<grid, K::NT, K::SMEM_BYTES, s>>>(P, A);
     return cudaGetLastError();
+}
+
+template <int D, int TX, int TY, bool FAST>
+static cudaError_t launch_prec(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s)
+{
+    if (precision == 0) {
+        if (mode == MODE_STEP) return launch_one<D, TX, TY, double, MODE_STEP, FAST>(P, A, s);
+        if (mode == MODE_INIT) return launch_one<D, TX, TY, double, MODE_INIT, FAST>(P, A, s);
+        return launch_one<D, TX, TY, double, MODE_FIELDS, FAST>(P, A, s);
+    }
+    if (mode == MODE_STEP) return launch_one<D, TX, TY, float, MODE_STEP, FAST>(P, A, s);
+    if (mode == MODE_INIT) return launch_one<D, TX, TY, float, MODE_INIT, FAST>(P, A, s);
+    return launch_one<D, TX, TY, float, MODE_FIELDS, FAST>(P, A, s);
 }
 
 template <int D, int TX, int TY>
 static cudaError_t launch_lattice(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s)
 {
-    if (precision == 0) {
-        if (mode == MODE_STEP) return launch_one<D, TX, TY, double, MODE_STEP>(P, A, s);
-        if (mode == MODE_INIT) return launch_one<D, TX, TY, double, MODE_INIT>(P, A, s);
-        return launch_one<D, TX, TY, double, MODE_FIELDS>(P, A, s);
-    }
-    if (mode == MODE_STEP) return launch_one<D, TX, TY, float, MODE_STEP>(P, A, s);
-    if (mode == MODE_INIT) return launch_one<D, TX, TY, float, MODE_INIT>(P, A, s);
-    return launch_one<D, TX, TY, float, MODE_FIELDS>(P, A, s);
+    // fast pulls: no bounce-back axis and 32-bit population indices
+    const bool walls = P.bc[0] || P.bc[1] || (D == 3 && P.bc[2]);
+    const bool fast = !walls && (long long)Lat<D>::Q * P.N < (1LL << 31);
+    if (fast) return launch_prec<D, TX, TY, true>(precision, mode, P, A, s);
+    return launch_prec<D, TX, TY, false>(precision, mode, P, A, s);
 }
 
 }  // namespace tel
