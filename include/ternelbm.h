@@ -155,7 +155,7 @@ int tel_info(const tel_ctx *ctx, double out[10]);
 int tel_coexistence(double a, double b, double R, double T, double out[4]);
 int tel_temperature_for_ratio(double a, double b, double R, double ratio, double *T);
 
-/* Batched D2Q9 lattices (SURVEY "next" row: many uneven cases in one
+/* Batched D2Q9 lattices (many uneven, independent cases advanced in one
  * persistent launch).  ncases independent D2Q9 lattices of nx[c] x ny[c]
  * nodes with their own parameters (one precision for all) live in one set of
  * device buffers; each tel_batch_step step is ONE launch of a persistent
@@ -174,6 +174,10 @@ typedef struct tel_batch tel_batch;
 int tel_batch_create(int ncases, const int *nx, const int *ny, const tel_params *params, tel_batch **out);
 void tel_batch_destroy(tel_batch *b);
 const char *tel_batch_last_error(const tel_batch *b);
+/* As tel_set_stream: later batch work is issued on cuda_stream (NULL: the
+ * batch's own stream).  The stream must not be the legacy default stream
+ * (step pairs are captured into a graph on it). */
+int tel_batch_set_stream(tel_batch *b, void *cuda_stream);
 int tel_batch_init(tel_batch *b, int c, const double *rho, const double *phi, const double *u);
 int tel_batch_step(tel_batch *b, int nsteps);
 int tel_batch_sync(tel_batch *b);

@@ -49,7 +49,9 @@ _lib = None
 SYMBOLS = ("tel_create", "tel_destroy", "tel_last_error", "tel_set_stream", "tel_init",
            "tel_init_device", "tel_step", "tel_sync", "tel_fields", "tel_fields_device",
            "tel_get_state", "tel_set_state", "tel_info", "tel_coexistence",
-           "tel_temperature_for_ratio", "tel_fields_noalloc")
+           "tel_temperature_for_ratio", "tel_fields_noalloc", "tel_batch_create",
+           "tel_batch_destroy", "tel_batch_last_error", "tel_batch_set_stream", "tel_batch_init", "tel_batch_step",
+           "tel_batch_sync", "tel_batch_fields", "tel_batch_tune", "tel_batch_info")
 
 
 def lib(build: bool = True):
@@ -83,8 +85,20 @@ def lib(build: bool = True):
     L.tel_coexistence.argtypes = [d, d, d, d, dp]
     L.tel_temperature_for_ratio.argtypes = [d, d, d, d, dp]
     L.tel_fields_noalloc.argtypes = [i, i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
+    L.tel_batch_create.argtypes = [i, vp, vp, vp, C.POINTER(vp)]
+    L.tel_batch_destroy.argtypes = [vp]
+    L.tel_batch_destroy.restype = None
+    L.tel_batch_last_error.argtypes = [vp]
+    L.tel_batch_last_error.restype = C.c_char_p
+    L.tel_batch_set_stream.argtypes = [vp, vp]
+    L.tel_batch_init.argtypes = [vp, i, vp, vp, vp]
+    L.tel_batch_step.argtypes = [vp, i]
+    L.tel_batch_sync.argtypes = [vp]
+    L.tel_batch_fields.argtypes = [vp, i, vp, vp, vp, vp]
+    L.tel_batch_tune.argtypes = [vp, i, vp]
+    L.tel_batch_info.argtypes = [vp, dp]
     for name in SYMBOLS:
-        if name not in ("tel_destroy", "tel_last_error"):
+        if name not in ("tel_destroy", "tel_last_error", "tel_batch_destroy", "tel_batch_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -148,6 +162,91 @@ def fields_noalloc(lattice, nx, ny, nz, params, f_state, g_state, with_p=True, s
     if rc:
         raise TelError(rc, lib().tel_last_error(None).decode())
     return {"rho": rho, "phi": phi, "u": u, "p": p}
+
+
+class Batch:
+    """Many independent D2Q9 lattices (own sizes and parameters, one precision)
+    advanced together: one persistent kernel launch per step.
+
+    ``shapes``: list of (nx, ny); ``params``: one dict or a list of dicts, as
+    for Lattice (bc along z is ignored).
+    """
+
+    def __init__(self, shapes, params):
+        shapes = [(int(a), int(b)) for a, b in shapes]
+        n = len(shapes)
+        plist = params if isinstance(params, (list, tuple)) else [params] * n
+        if len(plist) != n:
+            raise ValueError("one parameter dict per case")
+        P = (Params * n)(*[_params_struct(p) for p in plist])
+        nx = (C.c_int * n)(*[a for a, _ in shapes])
+        ny = (C.c_int * n)(*[b for _, b in shapes])
+        self._L = lib()
+        h = C.c_void_p()
+        rc = self._L.tel_batch_create(n, nx, ny, P, C.byref(h))
+        if rc:
+            raise TelError(rc, self._L.tel_batch_last_error(None).decode())
+        self._h = h
+        self.shapes = shapes
+        self.ncases = n
+
+    def _check(self, rc):
+        if rc:
+            raise TelError(rc, self._L.tel_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.tel_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        """``stream``: a torch.cuda.Stream (not the default stream), a raw
+        cudaStream_t int, or None for the batch's own stream."""
+        raw = None
+        if stream is not None:
+            raw = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.tel_batch_set_stream(self._h, C.c_void_p(raw) if raw else None))
+
+    def init(self, c, rho, phi, u):
+        nx, ny = self.shapes[c]
+        N = nx * ny
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (rho, phi, u)]
+        if a[0].size != N or a[1].size != N or a[2].size != 2 * N:
+            raise ValueError(f"case {c}: expected fields of {N}, {N} and {2 * N} values")
+        self._check(self._L.tel_batch_init(self._h, int(c), _ptr(a[0]), _ptr(a[1]), _ptr(a[2])))
+
+    def step(self, n=1):
+        self._check(self._L.tel_batch_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._L.tel_batch_sync(self._h))
+
+    def tune(self, steps_per_config=5):
+        """Times every tile width / chunk length on real steps (which advance
+        the state) and keeps the fastest.  Returns (tile width, chunk, steps)."""
+        out = (C.c_int * 3)()
+        self._check(self._L.tel_batch_tune(self._h, int(steps_per_config), out))
+        return tuple(out)
+
+    def info(self):
+        out = (C.c_double * 6)()
+        self._check(self._L.tel_batch_info(self._h, out))
+        keys = ("ncases", "nodes", "tile_x", "chunk", "items", "ctas")
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def fields(self, c, with_p=True):
+        nx, ny = self.shapes[c]
+        N = nx * ny
+        rho, phi, u = np.empty(N), np.empty(N), np.empty((2, N))
+        p = np.empty(N) if with_p else None
+        self._check(self._L.tel_batch_fields(self._h, int(c), _ptr(rho), _ptr(phi), _ptr(u), _ptr(p)))
+        return {"rho": rho, "phi": phi, "u": u, "p": p}
 
 
 class Lattice:

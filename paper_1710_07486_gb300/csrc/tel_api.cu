@@ -647,7 +647,7 @@ struct tel_batch {
     int cur;
     double *scratch;             // fields staging (largest case)
     size_t scratch_elems;
-    cudaStream_t stream;
+    cudaStream_t stream, own_stream;
     cudaGraphExec_t graph[2];    // two steps starting from buffer 0 / 1
     int initialized;
     char msg[512];
@@ -754,7 +754,8 @@ extern "C" int tel_batch_create(int ncases, const int *nx, const int *ny, const 
     if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(unsigned) * (size_t)ncases);
     if (e == cudaSuccess) e = cudaMalloc(&b->dP, sizeof(tel::DevParams) * (size_t)ncases);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&b->dA[k], sizeof(tel::LaunchArgs) * (size_t)ncases);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
+    b->stream = b->own_stream;
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(unsigned) * (size_t)ncases);
     if (e != cudaSuccess) {
         const bool oom = e == cudaErrorMemoryAllocation;
@@ -814,12 +815,19 @@ extern "C" void tel_batch_destroy(tel_batch *b)
     if (b->dP) cudaFree(b->dP);
     if (b->d_items) cudaFree(b->d_items);
     if (b->scratch) cudaFree(b->scratch);
-    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete[] b->nx; delete[] b->ny; delete[] b->off; delete[] b->hP;
     delete b;
 }
 
 extern "C" const char *tel_batch_last_error(const tel_batch *b) { return b ? b->msg : g_create_msg; }
+
+extern "C" int tel_batch_set_stream(tel_batch *b, void *s)
+{
+    if (!b) return TEL_EINVAL;
+    b->stream = s ? (cudaStream_t)s : b->own_stream;
+    return TEL_OK;
+}
 
 static tel::LaunchArgs batch_case_args(const tel_batch *b, int c, int k)
 {
@@ -857,9 +865,8 @@ extern "C" int tel_batch_init(tel_batch *b, int c, const double *rho, const doub
     A.in_rho = d; A.in_phi = d + N; A.in_u = d + 2 * N;
     A.fsrc = A.gsrc = nullptr;
     BCUDA(b, tel::launch_d2q9(b->precision, tel::MODE_INIT, b->hP[c], A, b->stream));
-    BCUDA(b, cudaStreamSynchronize(b->stream));
     b->initialized = 1;
-    return TEL_OK;
+    return tel_batch_sync(b);
 }
 
 static int batch_launch(tel_batch *b, int k)

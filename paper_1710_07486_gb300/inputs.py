@@ -99,6 +99,19 @@ def head_on_2d(seed, n, rho_g, rho_l, chi, V, R=40.0, gap=60.0, width=5.0):
                  width)
 
 
+def off_centre_2d(n, rho_g, rho_l, chi, V, B, R, width=5.0):
+    """Off-centre binary collision in a periodic square of edge n: drops of
+    radius R approach along x at +/-V/2 with centres offset along y by
+    B * 2R (impact parameter B)."""
+    c = n / 2.0
+    gap = R + 4.0
+    dy = B * 2.0 * R / 2.0
+    return drops((n, n), rho_g, rho_l, chi,
+                 [dict(center=(c - gap, c - dy), R=R, kind=+1, u=(V / 2, 0.0)),
+                  dict(center=(c + gap, c + dy), R=R, kind=-1, u=(-V / 2, 0.0))],
+                 width)
+
+
 def off_centre_3d(seed, n, rho_g, rho_l, chi, V, B, R=30.0, width=5.0):
     """Off-centre binary collision in a periodic cube of edge n: drops of
     radius R approach along x at +/-V/2 with centres offset along y by

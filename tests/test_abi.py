@@ -75,3 +75,22 @@ def test_invalid_parameters_rejected_before_any_device_work():
         assert ei.value.code == tel.TEL_EINVAL, (lat, nx, ny, nz, p)
     with pytest.raises(tel.TelError):
         tel.coexistence(A, B, RGAS, 1.0)
+
+
+def test_batch_create_validates_on_the_host():
+    """Bad batch arguments are rejected before any device call."""
+    T = tel.temperature_for_ratio(A, B, RGAS, 10.0)
+    p = base(T)
+    with pytest.raises(tel.TelError) as ei:
+        tel.Batch([(16, 16), (16, 16)], [p, dict(p, precision=tel.FP32_SHIFTED)])
+    assert ei.value.code == tel.TEL_EINVAL and "precision" in str(ei.value)
+    with pytest.raises(tel.TelError) as ei:
+        tel.Batch([(16, 16), (2, 16)], p)
+    assert ei.value.code == tel.TEL_EINVAL and "case 1" in str(ei.value)
+    with pytest.raises(tel.TelError) as ei:
+        tel.Batch([(16, 16)], dict(p, nu=-0.1))
+    assert ei.value.code == tel.TEL_EINVAL
+    with pytest.raises(ValueError):
+        tel.Batch([(16, 16), (16, 16)], [p])
+    L = tel.lib()
+    assert L.tel_batch_create(0, None, None, None, C.byref(C.c_void_p())) == tel.TEL_EINVAL
