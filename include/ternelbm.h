@@ -161,9 +161,9 @@ int tel_temperature_for_ratio(double a, double b, double R, double ratio, double
  * device buffers; each tel_batch_step step is ONE launch of a persistent
  * kernel that walks a work list of (case, tile, chunk) items, largest cases
  * first, so that small lattices no longer leave the GPU idle.  Pairs of steps
- * are replayed from a captured CUDA graph.  Each case evolves exactly as a
- * tel_create lattice with the same parameters would (same per-node
- * arithmetic).  tel_batch_tune times every (tile width 32/64, chunk
+ * are replayed from a captured CUDA graph.  Each case evolves as a
+ * tel_create lattice with the same parameters would, up to rounding (same
+ * per-node source, compiled separately).  tel_batch_tune times every (tile width 32/64, chunk
  * 8/16/32/64) configuration on steps_per_config real steps (plus one warm-up
  * step each: they advance the state) and keeps the fastest; out = {tile width,
  * chunk, steps advanced}.  tel_batch_init must come before any step (fields as
