@@ -4,8 +4,9 @@ as a single lattice with the same parameters does, whatever tile width and
 chunk length the work list uses: the per-node source is the same, but the two
 kernels are separate compilations, so the compiler may contract a*b+c into
 fused multiply-adds differently; the bar is therefore rounding level (FP64:
-1e-12 relative after 21 steps; FP32-shifted: 1e-5, ten times under the
-FP32-against-oracle bar), and the FP64 cases must keep the oracle's results
+1e-12 relative after 21 steps; FP32-shifted: 1e-5 on density and phase
+field, ten times under the FP32-against-oracle bar, 1e-4 on velocity and
+pressure), and the FP64 cases must keep the oracle's results
 (1e-10 after 20 steps)."""
 import numpy as np
 import pytest
@@ -59,21 +60,35 @@ def run_pair(precision, steps, walls=False, tune=False):
     return b, singles
 
 
+def errs(a, b):
+    return {"rho": np.max(np.abs(a["rho"] - b["rho"]) / np.abs(b["rho"])),
+            "phi": np.max(np.abs(a["phi"] - b["phi"])) / 5.0,
+            "u": np.max(np.abs(a["u"] - b["u"])) / max(np.abs(b["u"]).max(), 1e-3),
+            "p": np.max(np.abs(a["p"] - b["p"])) / max(np.abs(b["p"]).max(), 1e-6)}
+
+
 def max_rel(a, b):
-    return max(np.max(np.abs(a["rho"] - b["rho"]) / np.abs(b["rho"])),
-               np.max(np.abs(a["phi"] - b["phi"])) / 5.0,
-               np.max(np.abs(a["u"] - b["u"])),
-               np.max(np.abs(a["p"] - b["p"])) / max(np.abs(b["p"]).max(), 1e-6))
+    return max(errs(a, b).values())
+
+
+def close_fp32(a, b):
+    """FP32-shifted: density and phase field 1e-5 (ten times under the bar
+    against the oracle), velocity and pressure (differences of nearly equal
+    terms) 1e-4."""
+    e = errs(a, b)
+    return e["rho"] <= 1e-5 and e["phi"] <= 1e-5 and e["u"] <= 1e-4 and e["p"] <= 1e-4
 
 
 @pytest.mark.parametrize("precision", [tel.FP64, tel.FP32_SHIFTED])
 def test_batch_matches_single_lattices(precision):
     # odd and even step counts: single launches, graph replays of step pairs
     b, singles = run_pair(precision, [3, 6, 1, 11])
-    tol = 1e-12 if precision == tel.FP64 else 1e-5
     for k, s in enumerate(singles):
         got, ref = b.fields(k), s.fields()
-        assert max_rel(got, ref) <= tol, (k, max_rel(got, ref))
+        if precision == tel.FP64:
+            assert max_rel(got, ref) <= 1e-12, (k, errs(got, ref))
+        else:
+            assert close_fp32(got, ref), (k, errs(got, ref))
 
 
 def test_batch_with_walls_matches_single_lattices():
@@ -91,7 +106,7 @@ def test_batch_after_tuning_matches_single_lattices():
     assert 0 < info["ctas"] <= info["items"]
     for k, s in enumerate(singles):
         got, ref = b.fields(k), s.fields()
-        assert max_rel(got, ref) <= 1e-5, (k, max_rel(got, ref))
+        assert close_fp32(got, ref), (k, errs(got, ref))
 
 
 def test_batch_fp64_against_oracle(orc):
