@@ -182,6 +182,13 @@ int tel_batch_init(tel_batch *b, int c, const double *rho, const double *phi, co
 int tel_batch_step(tel_batch *b, int nsteps);
 int tel_batch_sync(tel_batch *b);
 int tel_batch_fields(tel_batch *b, int c, double *rho, double *phi, double *u, double *p);
+/* As tel_fields_device for case c: device FP64 arrays (rho[N], phi[N],
+ * u[2N], p[N], each may be NULL), asynchronous on the batch's stream; no
+ * error-word check (see tel_batch_errors). */
+int tel_batch_fields_device(tel_batch *b, int c, double *rho, double *phi, double *u, double *p);
+/* Synchronises, copies every case's error word to flags[ncases] (0 = no
+ * flagged node; else the TEL error bits) and clears them. */
+int tel_batch_errors(tel_batch *b, unsigned *flags);
 int tel_batch_tune(tel_batch *b, int steps_per_config, int out[3]);
 int tel_batch_info(const tel_batch *b, double out[6]);
 

@@ -107,6 +107,9 @@ int tel_sur_errors(const float *pred, const float *ref, double *acc, int B, int 
 int tel_sur_adam(float *w32, void *w16, const float *g, float *m, float *v, long long n, float lr, float beta1,
                  float beta2, float eps, int t, float grad_scale, void *stream);
 
+/* Zero n FP32 values (cudaMemsetAsync). */
+int tel_sur_zero(float *p, long long n, void *stream);
+
 /* w16 = bf16(w32), n elements. */
 int tel_sur_to_bf16(const float *w32, void *w16, long long n, void *stream);
 

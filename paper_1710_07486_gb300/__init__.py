@@ -51,7 +51,8 @@ SYMBOLS = ("tel_create", "tel_destroy", "tel_last_error", "tel_set_stream", "tel
            "tel_get_state", "tel_set_state", "tel_info", "tel_coexistence",
            "tel_temperature_for_ratio", "tel_fields_noalloc", "tel_batch_create",
            "tel_batch_destroy", "tel_batch_last_error", "tel_batch_set_stream", "tel_batch_init", "tel_batch_step",
-           "tel_batch_sync", "tel_batch_fields", "tel_batch_tune", "tel_batch_info")
+           "tel_batch_sync", "tel_batch_fields", "tel_batch_fields_device", "tel_batch_errors",
+           "tel_batch_tune", "tel_batch_info")
 
 
 def lib(build: bool = True):
@@ -95,6 +96,8 @@ def lib(build: bool = True):
     L.tel_batch_step.argtypes = [vp, i]
     L.tel_batch_sync.argtypes = [vp]
     L.tel_batch_fields.argtypes = [vp, i, vp, vp, vp, vp]
+    L.tel_batch_fields_device.argtypes = [vp, i, vp, vp, vp, vp]
+    L.tel_batch_errors.argtypes = [vp, vp]
     L.tel_batch_tune.argtypes = [vp, i, vp]
     L.tel_batch_info.argtypes = [vp, dp]
     for name in SYMBOLS:
@@ -239,6 +242,18 @@ class Batch:
         self._check(self._L.tel_batch_info(self._h, out))
         keys = ("ncases", "nodes", "tile_x", "chunk", "items", "ctas")
         return {k: int(v) for k, v in zip(keys, out)}
+
+    def fields_device(self, c, rho=None, phi=None, u=None, p=None):
+        """Case c's fields into device float64 tensors (asynchronous on the
+        batch's stream)."""
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(self._L.tel_batch_fields_device(self._h, int(c), ptr(rho), ptr(phi), ptr(u), ptr(p)))
+
+    def errors(self):
+        """Per-case error words (0 = stable), cleared after reading."""
+        out = (C.c_uint * self.ncases)()
+        self._check(self._L.tel_batch_errors(self._h, out))
+        return list(out)
 
     def fields(self, c, with_p=True):
         nx, ny = self.shapes[c]

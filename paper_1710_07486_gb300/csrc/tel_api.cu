@@ -951,6 +951,27 @@ extern "C" int tel_batch_fields(tel_batch *b, int c, double *rho, double *phi, d
     return tel_batch_sync(b);
 }
 
+extern "C" int tel_batch_fields_device(tel_batch *b, int c, double *rho, double *phi, double *u, double *p)
+{
+    if (!b) return TEL_EINVAL;
+    if (c < 0 || c >= b->ncases) return bfail(b, TEL_EINVAL, "tel_batch_fields_device: bad case");
+    if (!b->initialized) return bfail(b, TEL_ESTATE, "tel_batch_fields_device before tel_batch_init");
+    tel::LaunchArgs A = batch_case_args(b, c, b->cur);
+    A.fdst = A.gdst = nullptr;
+    A.out_rho = rho; A.out_phi = phi; A.out_u = u; A.out_p = p;
+    BCUDA(b, tel::launch_d2q9(b->precision, tel::MODE_FIELDS, b->hP[c], A, b->stream));
+    return TEL_OK;
+}
+
+extern "C" int tel_batch_errors(tel_batch *b, unsigned *flags)
+{
+    if (!b || !flags) return TEL_EINVAL;
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    BCUDA(b, cudaMemcpy(flags, b->d_err, sizeof(unsigned) * (size_t)b->ncases, cudaMemcpyDeviceToHost));
+    BCUDA(b, cudaMemset(b->d_err, 0, sizeof(unsigned) * (size_t)b->ncases));
+    return TEL_OK;
+}
+
 extern "C" int tel_batch_tune(tel_batch *b, int steps_per_config, int out[3])
 {
     if (!b) return TEL_EINVAL;

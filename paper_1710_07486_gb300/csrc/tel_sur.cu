@@ -868,3 +868,9 @@ extern "C" int tel_sur_to_bf16(const float *w32, void *w16, long long n, void *s
     to_bf16_kernel<<<blocks_for(n), 256, 0, S(stream)>>>(w32, (bf16 *)w16, n);
     return launched();
 }
+
+extern "C" int tel_sur_zero(float *p, long long n, void *stream)
+{
+    if (!p || n < 0) return TEL_EINVAL;
+    return ok(cudaMemsetAsync(p, 0, sizeof(float) * (size_t)n, S(stream)));
+}

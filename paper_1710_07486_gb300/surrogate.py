@@ -1,0 +1,462 @@
+"""Learned surrogate of the D2Q9 ternary lattice update (binding and driver).
+
+A small periodic convolutional encoder-decoder advances the normalised
+density, composition and velocity fields k lattice steps at a time.  Every
+operation of training and inference runs in libternelbm's kernels
+(include/ternelbm_sur.h): BF16 tensor-core convolutions with FP32
+accumulation, their input and weight gradients, pooling, the
+mass-conserving head, the loss and Adam.  This module only allocates device
+buffers (PyTorch tensors) and issues the calls in order.
+
+The lattice update itself produces the training snapshots (``Snapshots``),
+and stays the fallback and the judge of the surrogate's error
+(``Hybrid``): a surrogate step is rejected, and the lattice update runs
+instead, when the per-component mass residual or the field error against a
+periodic lattice check exceeds its threshold.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import Batch, TelError, lib
+
+CIN, COUT, NF = 16, 16, 4
+U_REF = 0.1  # velocity normalisation (lattice units)
+
+SUR_SYMBOLS = ("tel_sur_conv3x3", "tel_sur_flip_weights", "tel_sur_relu_bwd", "tel_sur_conv3x3_wgrad",
+               "tel_sur_pool2", "tel_sur_pool2_bwd", "tel_sur_up2", "tel_sur_up2_bwd", "tel_sur_add",
+               "tel_sur_pack", "tel_sur_unpack", "tel_sur_gather", "tel_sur_loss", "tel_sur_advance",
+               "tel_sur_errors", "tel_sur_adam", "tel_sur_zero", "tel_sur_to_bf16")
+
+
+def sur_lib():
+    L = lib()
+    if getattr(L, "_sur_ready", False):
+        return L
+    vp, i, ll, f = C.c_void_p, C.c_int, C.c_longlong, C.c_float
+    L.tel_sur_conv3x3.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp]
+    L.tel_sur_flip_weights.argtypes = [vp, vp, i, i, vp]
+    L.tel_sur_relu_bwd.argtypes = [vp, vp, vp, ll, vp]
+    L.tel_sur_conv3x3_wgrad.argtypes = [vp, vp, vp, vp, i, i, i, i, i, vp]
+    for n in ("tel_sur_pool2", "tel_sur_pool2_bwd", "tel_sur_up2", "tel_sur_up2_bwd"):
+        getattr(L, n).argtypes = [vp, vp, i, i, i, i, vp]
+    L.tel_sur_add.argtypes = [vp, vp, vp, ll, vp]
+    L.tel_sur_pack.argtypes = [vp, vp, vp, vp, vp, vp, i, i, i, vp]
+    L.tel_sur_unpack.argtypes = [vp, vp, vp, vp, vp, i, i, i, vp]
+    L.tel_sur_gather.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, vp]
+    L.tel_sur_loss.argtypes = [vp, vp, vp, vp, vp, i, i, i, vp]
+    L.tel_sur_advance.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, vp]
+    L.tel_sur_errors.argtypes = [vp, vp, vp, i, i, i, vp]
+    L.tel_sur_adam.argtypes = [vp, vp, vp, vp, vp, ll, f, f, f, f, i, f, vp]
+    L.tel_sur_zero.argtypes = [vp, ll, vp]
+    L.tel_sur_to_bf16.argtypes = [vp, vp, ll, vp]
+    for n in SUR_SYMBOLS:
+        getattr(L, n).restype = C.c_int
+    L._sur_ready = True
+    return L
+
+
+def _p(t, offset=0):
+    """Device pointer of a tensor (plus an element offset), or None."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr() + offset * t.element_size())
+
+
+def _ok(rc, what):
+    if rc:
+        raise TelError(rc, f"{what} failed")
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def layers(c0=32, c1=64, c2=128):
+    """Encoder-decoder op list: ('conv', cin, cout, relu), ('pool',), ('up',),
+    ('save', slot), ('add', slot).  Three levels (H, H/2, H/4)."""
+    return [("conv", CIN, c0, 1), ("conv", c0, c0, 1), ("save", 0), ("pool",),
+            ("conv", c0, c1, 1), ("conv", c1, c1, 1), ("save", 1), ("pool",),
+            ("conv", c1, c2, 1), ("conv", c2, c2, 1), ("conv", c2, c2, 1), ("up",),
+            ("conv", c2, c1, 1), ("add", 1), ("conv", c1, c1, 1), ("up",),
+            ("conv", c1, c0, 1), ("add", 0), ("conv", c0, c0, 1),
+            ("conv", c0, COUT, 0)]
+
+
+class Net:
+    """Parameters (FP32 master, BF16 working copy, Adam moments) and the
+    forward/backward sequence for one batch shape (B, H, W)."""
+
+    def __init__(self, widths=(32, 64, 128), seed=0):
+        import torch
+        self.torch = torch
+        self.L = sur_lib()
+        self.ops = layers(*widths)
+        self.convs = [op for op in self.ops if op[0] == "conv"]
+        # flat layout: per conv W [9][cout][cin] then b [cout]
+        self.woff, self.boff = [], []
+        n = 0
+        for _, ci, co, _ in self.convs:
+            self.woff.append(n)
+            n += 9 * co * ci
+            self.boff.append(n)
+            n += co
+        self.n = n
+        g = np.random.default_rng(seed)
+        host = np.zeros(n, dtype=np.float32)
+        for k, (_, ci, co, relu) in enumerate(self.convs):
+            std = math.sqrt(2.0 / (9 * ci)) * (1.0 if relu else 0.1)
+            host[self.woff[k]:self.woff[k] + 9 * co * ci] = g.normal(0.0, std, 9 * co * ci)
+        dev = torch.device("cuda")
+        self.w32 = torch.from_numpy(host).to(dev)
+        self.w16 = torch.empty(n, dtype=torch.bfloat16, device=dev)
+        self.wt16 = torch.empty(n, dtype=torch.bfloat16, device=dev)  # flipped weights (same offsets)
+        self.g = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.m = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.v = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.t = 0
+        self.sync_bf16()
+        self._plans = {}
+
+    @property
+    def params(self):
+        return self.n
+
+    def sync_bf16(self):
+        _ok(self.L.tel_sur_to_bf16(_p(self.w32), _p(self.w16), self.n, _stream()), "to_bf16")
+
+    def set_host_weights(self, host):
+        """Replace the FP32 master weights by a host array (flat layout)."""
+        self.w32.copy_(self.torch.from_numpy(np.ascontiguousarray(host, dtype=np.float32)))
+        self.sync_bf16()
+
+    def host_layers(self):
+        """(W [9][cout][cin], b [cout]) per conv as float64 host arrays."""
+        h = self.w32.cpu().numpy().astype(np.float64)
+        out = []
+        for k, (_, ci, co, _) in enumerate(self.convs):
+            out.append((h[self.woff[k]:self.woff[k] + 9 * co * ci].reshape(9, co, ci),
+                        h[self.boff[k]:self.boff[k] + co].copy()))
+        return out
+
+    # ------------------------------------------------------------ buffers
+    def plan(self, B, H, W):
+        key = (B, H, W)
+        if key not in self._plans:
+            self._plans[key] = _Plan(self, B, H, W)
+        return self._plans[key]
+
+    def forward(self, x16, B, H, W):
+        """Network output (bf16 [B][H][W][16]) for input x16; keeps the
+        activations for backward."""
+        return self.plan(B, H, W).forward(x16)
+
+    def backward(self, dout, B, H, W):
+        """Accumulates the parameter gradient into self.g."""
+        self.plan(B, H, W).backward(dout)
+
+    def zero_grad(self):
+        _ok(self.L.tel_sur_zero(_p(self.g), self.n, _stream()), "zero")
+
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8, grad_scale=1.0):
+        self.t += 1
+        _ok(self.L.tel_sur_adam(_p(self.w32), _p(self.w16), _p(self.g), _p(self.m), _p(self.v), self.n,
+                                float(lr), float(b1), float(b2), float(eps), self.t, float(grad_scale),
+                                _stream()), "adam")
+
+
+class _Plan:
+    """Preallocated activations and gradients for one (B, H, W)."""
+
+    def __init__(self, net, B, H, W):
+        torch = net.torch
+        self.net, self.B, self.H, self.W = net, B, H, W
+        L = net.L
+        dev = torch.device("cuda")
+        bf = torch.bfloat16
+        # forward records: (kind, ...) with the tensors each op reads/writes
+        self.recs = []
+        h, w, c = H, W, CIN
+        saved = {}
+        k = 0
+        self.x_in = None
+        for op in net.ops:
+            if op[0] == "conv":
+                _, ci, co, relu = op
+                y = torch.empty((B, h, w, co), dtype=bf, device=dev)
+                self.recs.append(["conv", k, ci, co, relu, h, w, None, y])
+                c = co
+                k += 1
+            elif op[0] == "pool":
+                y = torch.empty((B, h // 2, w // 2, c), dtype=bf, device=dev)
+                self.recs.append(["pool", c, h, w, y])
+                h, w = h // 2, w // 2
+            elif op[0] == "up":
+                y = torch.empty((B, 2 * h, 2 * w, c), dtype=bf, device=dev)
+                self.recs.append(["up", c, 2 * h, 2 * w, y])
+                h, w = 2 * h, 2 * w
+            elif op[0] == "save":
+                self.recs.append(["save", op[1], c, h, w])
+            elif op[0] == "add":
+                y = torch.empty((B, h, w, c), dtype=bf, device=dev)
+                self.recs.append(["add", op[1], c, h, w, y])
+        self.out = self.recs[-1][-1]
+        # gradient buffers: one per record output shape, plus dz per conv
+        self.dz = [torch.empty_like(r[8]) for r in self.recs if r[0] == "conv"]
+        self.dx = {}
+        for r in self.recs:
+            if r[0] == "conv":
+                self.dx[id(r)] = torch.empty((B, r[5], r[6], r[2]), dtype=bf, device=dev)
+            elif r[0] == "pool":
+                self.dx[id(r)] = torch.empty((B, r[2], r[3], r[1]), dtype=bf, device=dev)
+            elif r[0] == "up":
+                self.dx[id(r)] = torch.empty((B, r[2] // 2, r[3] // 2, r[1]), dtype=bf, device=dev)
+            elif r[0] == "save":
+                self.dx[id(r)] = torch.empty((B, r[3], r[4], r[2]), dtype=bf, device=dev)
+
+    def forward(self, x16):
+        net, L, B = self.net, self.net.L, self.B
+        s = _stream()
+        a = x16
+        saved = {}
+        for r in self.recs:
+            kind = r[0]
+            if kind == "conv":
+                _, k, ci, co, relu, h, w, _, y = r
+                r[7] = a
+                _ok(L.tel_sur_conv3x3(_p(a), _p(net.w16, net.woff[k]), _p(net.w32, net.boff[k]), _p(y),
+                                      B, h, w, ci, co, relu, s), "conv3x3")
+                a = y
+            elif kind == "pool":
+                _, c, h, w, y = r
+                _ok(L.tel_sur_pool2(_p(a), _p(y), B, h, w, c, s), "pool2")
+                a = y
+            elif kind == "up":
+                _, c, h, w, y = r
+                _ok(L.tel_sur_up2(_p(a), _p(y), B, h, w, c, s), "up2")
+                a = y
+            elif kind == "save":
+                saved[r[1]] = a
+            elif kind == "add":
+                _, slot, c, h, w, y = r
+                _ok(L.tel_sur_add(_p(a), _p(saved[slot]), _p(y), B * h * w * c, s), "add")
+                a = y
+        return a
+
+    def backward(self, dout):
+        net, L, B = self.net, self.net.L, self.B
+        s = _stream()
+        d = dout
+        gsaved = {}
+        convs = [r for r in self.recs if r[0] == "conv"]
+        for r in reversed(self.recs):
+            kind = r[0]
+            if kind == "conv":
+                _, k, ci, co, relu, h, w, a_in, y = r
+                dz = self.dz[k]
+                if relu:
+                    _ok(L.tel_sur_relu_bwd(_p(y), _p(d), _p(dz), B * h * w * co, s), "relu_bwd")
+                else:
+                    dz = d
+                _ok(L.tel_sur_conv3x3_wgrad(_p(a_in), _p(dz), _p(net.g, net.woff[k]), _p(net.g, net.boff[k]),
+                                            B, h, w, ci, co, s), "wgrad")
+                if k > 0:
+                    _ok(L.tel_sur_flip_weights(_p(net.w16, net.woff[k]), _p(net.wt16, net.woff[k]), ci, co, s),
+                        "flip")
+                    dx = self.dx[id(r)]
+                    _ok(L.tel_sur_conv3x3(_p(dz), _p(net.wt16, net.woff[k]), None, _p(dx), B, h, w, co, ci, 0, s),
+                        "conv3x3 (input gradient)")
+                    d = dx
+            elif kind == "pool":
+                _, c, h, w, _ = r
+                dx = self.dx[id(r)]
+                _ok(L.tel_sur_pool2_bwd(_p(d), _p(dx), B, h, w, c, s), "pool2_bwd")
+                d = dx
+            elif kind == "up":
+                _, c, h, w, _ = r
+                dx = self.dx[id(r)]
+                _ok(L.tel_sur_up2_bwd(_p(d), _p(dx), B, h, w, c, s), "up2_bwd")
+                d = dx
+            elif kind == "add":
+                gsaved[r[1]] = d
+            elif kind == "save":
+                _, slot, c, h, w = r
+                dx = self.dx[id(r)]
+                _ok(L.tel_sur_add(_p(d), _p(gsaved.pop(slot)), _p(dx), B * h * w * c, s), "add (gradient)")
+                d = dx
+        del convs
+
+
+# ---------------------------------------------------------------------------
+# snapshots of the lattice update
+# ---------------------------------------------------------------------------
+class Snapshots:
+    """Normalised fields of ``ntraj`` D2Q9 trajectories (same H x W, own
+    parameters), every ``k`` steps, ``nsnap`` snapshots each, generated by
+    the batched lattice update and kept on the device as FP32
+    [nsnap][ntraj][H][W][4].  Trajectories whose lattice flagged an unstable
+    node are marked bad and left out of training and evaluation."""
+
+    def __init__(self, shape, params, fields, k, nsnap, tune=True):
+        import torch
+        L = sur_lib()
+        H, W = shape
+        self.H, self.W, self.k, self.nsnap = H, W, k, nsnap
+        self.ntraj = n = len(params)
+        dev = torch.device("cuda")
+        b = Batch([(W, H)] * n, params)
+        for c, (rho, phi, u) in enumerate(fields):
+            b.init(c, rho, phi, u)
+        if tune:
+            b.tune(1)  # advances every case by the same number of steps
+        N = H * W
+        self.norm_host = np.array([[1.0 / coex_rho_l(p), 1.0 / p["chi"], 1.0 / U_REF] for p in params],
+                                  dtype=np.float32)
+        self.norm = torch.from_numpy(self.norm_host).to(dev)
+        self.store = torch.empty((nsnap, n, H, W, NF), dtype=torch.float32, device=dev)
+        rho = torch.empty((n, N), dtype=torch.float64, device=dev)
+        phi = torch.empty((n, N), dtype=torch.float64, device=dev)
+        u = torch.empty((n, 2, N), dtype=torch.float64, device=dev)
+        bad = np.zeros(n, dtype=bool)
+        stream = torch.cuda.Stream()
+        b.set_stream(stream)
+        for s in range(nsnap):
+            if s:
+                b.step(k)
+            for c in range(n):
+                b.fields_device(c, rho[c], phi[c], u[c])
+            with torch.cuda.stream(stream):
+                _ok(L.tel_sur_pack(_p(rho), _p(phi), _p(u), _p(self.norm), _p(self.store[s]), None, n, H, W,
+                                   C.c_void_p(stream.cuda_stream)), "pack")
+            bad |= np.array(b.errors()) != 0
+        stream.synchronize()
+        b.close()
+        self.bad = bad
+        self.good = np.flatnonzero(~bad)
+
+    def pairs(self, snaps=None):
+        """(src, dst) flat store indices of consecutive snapshots of good
+        trajectories (store index = s * ntraj + traj)."""
+        src, dst = [], []
+        snaps = range(self.nsnap - 1) if snaps is None else snaps
+        for s in snaps:
+            for t in self.good:
+                src.append(s * self.ntraj + t)
+                dst.append((s + 1) * self.ntraj + t)
+        return np.array(src, dtype=np.int32), np.array(dst, dtype=np.int32)
+
+    def delta_scale(self, src, dst, sample=256, seed=0):
+        """Per-field RMS of the k-step change, from a host sample of pairs."""
+        g = np.random.default_rng(seed)
+        idx = g.choice(len(src), size=min(sample, len(src)), replace=False)
+        flat = self.store.view(-1, self.H, self.W, NF)
+        a = flat[src[idx]].cpu().numpy().astype(np.float64)
+        z = flat[dst[idx]].cpu().numpy().astype(np.float64)
+        rms = np.sqrt(((z - a) ** 2).mean(axis=(0, 1, 2)))
+        return np.maximum(rms, 1e-8).astype(np.float32)
+
+
+def coex_rho_l(p):
+    from . import coexistence
+    return coexistence(p["a"], p["b"], p["R"], p["T"])[1]
+
+
+# ---------------------------------------------------------------------------
+# training and inference
+# ---------------------------------------------------------------------------
+class Trainer:
+    """Adam on the mean squared error of the projected k-step change."""
+
+    def __init__(self, net, snaps, B=8, seed=0, scale=None):
+        import torch
+        self.net, self.snaps, self.B = net, snaps, B
+        self.torch = torch
+        L = net.L
+        H, W = snaps.H, snaps.W
+        dev = torch.device("cuda")
+        self.src, self.dst = snaps.pairs()
+        self.scale_host = snaps.delta_scale(self.src, self.dst) if scale is None else np.asarray(scale, np.float32)
+        self.scale = torch.from_numpy(self.scale_host).to(dev)
+        self.f32 = torch.empty((B, H, W, NF), dtype=torch.float32, device=dev)
+        self.x16 = torch.empty((B, H, W, CIN), dtype=torch.bfloat16, device=dev)
+        self.tgt = torch.empty((B, H, W, NF), dtype=torch.float32, device=dev)
+        self.dout = torch.empty((B, H, W, COUT), dtype=torch.bfloat16, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.work = torch.zeros(4 * B, dtype=torch.float32, device=dev)
+        self.idx = torch.empty((2, B), dtype=torch.int32, device=dev)
+        self.rng = np.random.default_rng(seed)
+        self.L = L
+
+    def step(self, lr):
+        """One training step on a random batch; returns the device loss
+        tensor (read it only when needed: reading synchronises)."""
+        B, H, W = self.B, self.snaps.H, self.snaps.W
+        L, net = self.L, self.net
+        s = _stream()
+        pick = self.rng.integers(0, len(self.src), size=B)
+        self.idx.copy_(self.torch.from_numpy(np.stack([self.src[pick], self.dst[pick]])), non_blocking=False)
+        flat = self.snaps.store.view(-1, H, W, NF)
+        _ok(L.tel_sur_gather(_p(flat), _p(self.idx[0]), _p(self.idx[1]), _p(self.scale), _p(self.f32),
+                             _p(self.x16), _p(self.tgt), B, H, W, s), "gather")
+        out = net.forward(self.x16, B, H, W)
+        _ok(L.tel_sur_zero(_p(self.loss), 1, s), "zero")
+        _ok(L.tel_sur_loss(_p(out), _p(self.tgt), _p(self.dout), _p(self.loss), _p(self.work), B, H, W, s), "loss")
+        net.zero_grad()
+        net.backward(self.dout, B, H, W)
+        net.adam(lr)
+        return self.loss
+
+    def train(self, steps, lr=1e-3, lr_min=1e-5, log_every=0):
+        hist = []
+        for i in range(steps):
+            cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * i / max(steps, 1)))
+            l = self.step(cur)
+            if log_every and (i % log_every == 0 or i == steps - 1):
+                hist.append((i, float(l.item())))
+        return hist
+
+
+class Predictor:
+    """Surrogate inference for B states of H x W: advance normalised FP32
+    fields by k lattice steps per call."""
+
+    def __init__(self, net, B, H, W, scale):
+        import torch
+        self.net, self.B, self.H, self.W = net, B, H, W
+        self.L = net.L
+        dev = torch.device("cuda")
+        self.scale = torch.from_numpy(np.asarray(scale, dtype=np.float32)).to(dev)
+        self.x16 = torch.empty((B, H, W, CIN), dtype=torch.bfloat16, device=dev)
+        self.work = torch.zeros(4 * B, dtype=torch.float32, device=dev)
+        self.mass = torch.zeros(2 * B, dtype=torch.float64, device=dev)
+        self.err = torch.zeros(6 * B, dtype=torch.float64, device=dev)
+        self.torch = torch
+
+    def load(self, f32):
+        """Network input from normalised FP32 fields (via the gather kernel
+        with the identity index list)."""
+        import torch
+        idx = torch.arange(self.B, dtype=torch.int32, device=f32.device)
+        _ok(self.L.tel_sur_gather(_p(f32), _p(idx), None, None, None, _p(self.x16), None, self.B, self.H, self.W,
+                                  _stream()), "gather")
+
+    def advance(self, f32, f32_next, mass=True):
+        """f32_next = surrogate(f32); self.x16 must hold f32's network input
+        (load() or the previous advance).  Also writes the next input."""
+        out = self.net.forward(self.x16, self.B, self.H, self.W)
+        if mass:
+            _ok(self.L.tel_sur_zero(_p(self.mass), 4 * self.B, _stream()), "zero")  # 2B doubles = 4B floats
+        _ok(self.L.tel_sur_advance(_p(f32), _p(out), _p(self.scale), _p(f32_next), _p(self.x16),
+                                   _p(self.mass) if mass else None, _p(self.work), self.B, self.H, self.W,
+                                   _stream()), "advance")
+
+    def errors(self, pred, ref):
+        """Relative L2 errors (rho, phi, u) per sample, host array [B][3]."""
+        _ok(self.L.tel_sur_zero(_p(self.err), 12 * self.B, _stream()), "zero")  # 6B doubles = 12B floats
+        _ok(self.L.tel_sur_errors(_p(pred), _p(ref), _p(self.err), self.B, self.H, self.W, _stream()), "errors")
+        e = self.err.cpu().numpy().reshape(self.B, 3, 2)
+        return np.sqrt(e[:, :, 0] / np.maximum(e[:, :, 1], 1e-300))

@@ -1,0 +1,262 @@
+"""The surrogate's kernels (through the C ABI) against the FP64 oracle of
+oracle/surrogate.py on the same BF16-representable inputs.
+
+Tolerances follow from the arithmetic: products of BF16 values are exact in
+FP32, sums are FP32 (relative ~1e-6), and outputs stored as BF16 carry a
+relative rounding of 2^-9; so BF16 outputs are checked at 2^-8 relative to
+the output's scale, FP32 outputs (weight gradients, Adam) at 1e-4.  The whole
+network's gradients pass through a dozen BF16 roundings of activations and
+gradients: 5e-2 relative in norm per layer.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import surrogate as so  # noqa: E402
+from paper_1710_07486_gb300 import surrogate as S  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+BF = torch.bfloat16
+
+
+def bf16_values(g, shape, scale=1.0):
+    """Random values exactly representable in BF16 (as float64 host array)."""
+    x = torch.from_numpy(g.normal(0.0, scale, size=shape).astype(np.float32)).to(BF)
+    return x.float().numpy().astype(np.float64)
+
+
+def dev_bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(BF).cuda()
+
+
+def host(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def close_bf16(got, ref):
+    scale = max(np.abs(ref).max(), 1e-6)
+    return np.max(np.abs(got - ref)) <= 2.0 ** -8 * scale
+
+
+L = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    global L
+    L = S.sur_lib()
+    return L
+
+
+def s():
+    return S._stream()
+
+
+CH = [16, 32, 64, 128]
+
+
+@pytest.mark.parametrize("cin", CH)
+@pytest.mark.parametrize("cout", CH)
+def test_conv_forward_against_oracle(cin, cout):
+    g = np.random.default_rng(cin * 1000 + cout)
+    B, H, W = 2, 8, 24  # 384 pixels: three 128-pixel tiles
+    x = bf16_values(g, (B, H, W, cin))
+    Wo = bf16_values(g, (9, cin, cout), 1.0 / np.sqrt(9 * cin))  # oracle layout [t][i][o]
+    b = g.normal(size=cout).astype(np.float32).astype(np.float64)
+    for relu in (0, 1):
+        ref = so.conv_fwd(x, Wo, b, bool(relu))
+        y = torch.empty((B, H, W, cout), dtype=BF, device="cuda")
+        wk = dev_bf16(Wo.transpose(0, 2, 1))  # kernel layout [t][o][i]
+        bd = torch.from_numpy(b.astype(np.float32)).cuda()
+        assert L.tel_sur_conv3x3(S._p(dev_bf16(x)), S._p(wk), S._p(bd), S._p(y), B, H, W, cin, cout, relu, s()) == 0
+        torch.cuda.synchronize()
+        assert close_bf16(host(y), ref), (cin, cout, relu, np.max(np.abs(host(y) - ref)))
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 16), (64, 128), (128, 64), (128, 128), (16, 16)])
+def test_conv_gradients_against_oracle(cin, cout):
+    g = np.random.default_rng(7 + cin + cout)
+    B, H, W = 2, 16, 16  # 512 pixels: eight 64-pixel stages
+    x = bf16_values(g, (B, H, W, cin))
+    Wo = bf16_values(g, (9, cin, cout), 1.0 / np.sqrt(9 * cin))
+    dz = bf16_values(g, (B, H, W, cout))
+    # oracle with relu=False: dz is the pre-activation gradient
+    y = so.conv_fwd(x, Wo, np.zeros(cout), False)
+    dx_ref, dW_ref, db_ref = so.conv_bwd(x, Wo, y, dz, False)
+    wk = dev_bf16(Wo.transpose(0, 2, 1))
+    dw = torch.zeros(9 * cout * cin, dtype=torch.float32, device="cuda")
+    db = torch.zeros(cout, dtype=torch.float32, device="cuda")
+    dzd = dev_bf16(dz)
+    assert L.tel_sur_conv3x3_wgrad(S._p(dev_bf16(x)), S._p(dzd), S._p(dw), S._p(db), B, H, W, cin, cout, s()) == 0
+    wt = torch.empty_like(wk)
+    assert L.tel_sur_flip_weights(S._p(wk), S._p(wt), cin, cout, s()) == 0
+    dx = torch.empty((B, H, W, cin), dtype=BF, device="cuda")
+    assert L.tel_sur_conv3x3(S._p(dzd), S._p(wt), None, S._p(dx), B, H, W, cout, cin, 0, s()) == 0
+    torch.cuda.synchronize()
+    got_dW = dw.cpu().numpy().reshape(9, cout, cin).transpose(0, 2, 1)
+    assert np.max(np.abs(got_dW - dW_ref)) <= 1e-4 * np.abs(dW_ref).max()
+    assert np.max(np.abs(db.cpu().numpy() - db_ref)) <= 1e-4 * np.abs(db_ref).max()
+    assert close_bf16(host(dx), dx_ref)
+
+
+def test_pool_up_add_relu_bwd():
+    g = np.random.default_rng(3)
+    B, H, W, C = 2, 8, 12, 32
+    x = bf16_values(g, (B, H, W, C))
+    c = bf16_values(g, (B, H // 2, W // 2, C))
+    xd, cd = dev_bf16(x), dev_bf16(c)
+    p = torch.empty((B, H // 2, W // 2, C), dtype=BF, device="cuda")
+    pb = torch.empty((B, H, W, C), dtype=BF, device="cuda")
+    u = torch.empty((B, H, W, C), dtype=BF, device="cuda")
+    ub = torch.empty((B, H // 2, W // 2, C), dtype=BF, device="cuda")
+    assert L.tel_sur_pool2(S._p(xd), S._p(p), B, H, W, C, s()) == 0
+    assert L.tel_sur_pool2_bwd(S._p(cd), S._p(pb), B, H, W, C, s()) == 0
+    assert L.tel_sur_up2(S._p(cd), S._p(u), B, H, W, C, s()) == 0
+    assert L.tel_sur_up2_bwd(S._p(xd), S._p(ub), B, H, W, C, s()) == 0
+    a = torch.empty_like(xd)
+    assert L.tel_sur_add(S._p(xd), S._p(xd), S._p(a), x.size, s()) == 0
+    r = torch.empty_like(xd)
+    assert L.tel_sur_relu_bwd(S._p(xd), S._p(u), S._p(r), x.size, s()) == 0
+    torch.cuda.synchronize()
+    assert close_bf16(host(p), so.pool_fwd(x))
+    assert close_bf16(host(pb), so.pool_bwd(c))
+    assert np.array_equal(host(u), so.up_fwd(c))
+    assert close_bf16(host(ub), so.up_bwd(x))
+    assert np.array_equal(host(a), 2 * x)
+    assert np.array_equal(host(r), so.up_fwd(c) * (x > 0))
+
+
+def test_network_gradients_against_oracle():
+    """Whole encoder-decoder: forward output, loss and every layer's weight
+    and bias gradient from the library's kernels against the oracle."""
+    widths = (16, 16, 32)
+    assert [(ci, co) for _, ci, co, _ in [op for op in S.layers(*widths) if op[0] == "conv"]] == \
+        so.conv_shapes(so.arch(*widths))
+    net = S.Net(widths, seed=11)
+    # round the master weights to BF16 so that both sides use the same values
+    w = net.w32.cpu().numpy()
+    w = torch.from_numpy(w).to(BF).float().numpy()
+    g = np.random.default_rng(12)
+    for k in range(len(net.convs)):  # non-zero biases
+        co = net.convs[k][2]
+        w[net.boff[k]:net.boff[k] + co] = g.normal(0, 0.05, co)
+    net.set_host_weights(w)
+    B, H, W = 2, 32, 32
+    x = bf16_values(g, (B, H, W, so.CIN))
+    x[..., 4:] = 0.0
+    T = g.normal(0, 1.0, size=(B, H, W, so.NF))
+    lay = net.host_layers()
+    Ws = [Wk.transpose(0, 2, 1) for Wk, _ in lay]
+    bs = [bk for _, bk in lay]
+    out_ref, cache = so.forward(so.arch(*widths), Ws, bs, x)
+    L_ref, dout_ref = so.loss(out_ref, T)
+    dWs, dbs, _ = so.backward(cache, Ws, dout_ref)
+
+    x16 = dev_bf16(x)
+    out = net.forward(x16, B, H, W)
+    tg = torch.from_numpy(T.astype(np.float32)).cuda()
+    dout = torch.empty((B, H, W, 16), dtype=BF, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    work = torch.zeros(4 * B, dtype=torch.float32, device="cuda")
+    assert L.tel_sur_loss(S._p(out), S._p(tg), S._p(dout), S._p(loss), S._p(work), B, H, W, s()) == 0
+    net.zero_grad()
+    net.backward(dout, B, H, W)
+    torch.cuda.synchronize()
+    o = host(out)
+    assert np.linalg.norm(o - out_ref) <= 2e-2 * np.linalg.norm(out_ref)
+    assert abs(float(loss.item()) - L_ref) <= 1e-2 * L_ref
+    gh = net.g.cpu().numpy().astype(np.float64)
+    for k, (_, ci, co, _) in enumerate(net.convs):
+        gW = gh[net.woff[k]:net.woff[k] + 9 * co * ci].reshape(9, co, ci).transpose(0, 2, 1)
+        gb = gh[net.boff[k]:net.boff[k] + co]
+        assert np.linalg.norm(gW - dWs[k]) <= 5e-2 * np.linalg.norm(dWs[k]), k
+        assert np.linalg.norm(gb - dbs[k]) <= 5e-2 * max(np.linalg.norm(dbs[k]), 1e-12), k
+
+
+def test_adam_and_bf16_copy_against_oracle():
+    g = np.random.default_rng(5)
+    n = 5000
+    w = g.normal(size=n)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    wd = torch.from_numpy(w.astype(np.float32)).cuda()
+    md = torch.zeros(n, dtype=torch.float32, device="cuda")
+    vd = torch.zeros(n, dtype=torch.float32, device="cuda")
+    w16 = torch.empty(n, dtype=BF, device="cuda")
+    wr = w.astype(np.float32).astype(np.float64)
+    for t in range(1, 4):
+        gr = g.normal(size=n).astype(np.float32)
+        gd = torch.from_numpy(gr).cuda()
+        assert L.tel_sur_adam(S._p(wd), S._p(w16), S._p(gd), S._p(md), S._p(vd), n, 1e-2, 0.9, 0.999, 1e-8, t, 1.0,
+                              s()) == 0
+        wr, m, v = so.adam(wr, gr.astype(np.float64), m, v, t, 1e-2)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(wd.cpu().numpy() - wr)) <= 1e-5 * np.abs(wr).max()
+    assert np.array_equal(w16.float().cpu().numpy(), wd.to(BF).float().cpu().numpy())
+
+
+def test_pack_gather_advance_and_mass():
+    g = np.random.default_rng(6)
+    B, H, W = 3, 16, 16
+    N = H * W
+    rho = g.uniform(0.5, 8.0, size=(B, N))
+    phi = g.uniform(-5.0, 5.0, size=(B, N))
+    u = g.normal(0, 0.05, size=(B, 2, N))
+    norm = np.array([[1 / 8.0, 1 / 5.0, 1 / S.U_REF]] * B, dtype=np.float32)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    f32 = torch.empty((B, H, W, 4), dtype=torch.float32, device="cuda")
+    x16 = torch.empty((B, H, W, 16), dtype=BF, device="cuda")
+    assert L.tel_sur_pack(S._p(d(rho)), S._p(d(phi)), S._p(d(u)), S._p(d(norm)), S._p(f32), S._p(x16), B, H, W,
+                          s()) == 0
+    ref = so.pack(rho.reshape(B, H, W), phi.reshape(B, H, W), u[:, 0].reshape(B, H, W), u[:, 1].reshape(B, H, W),
+                  8.0, 5.0, S.U_REF)
+    torch.cuda.synchronize()
+    assert np.allclose(f32.cpu().numpy(), ref[..., :4], rtol=1e-6, atol=1e-7)
+    assert close_bf16(host(x16), ref)
+    # unpack is the inverse of pack (to FP32 rounding)
+    r2 = torch.empty((B, N), dtype=torch.float64, device="cuda")
+    p2 = torch.empty((B, N), dtype=torch.float64, device="cuda")
+    u2 = torch.empty((B, 2, N), dtype=torch.float64, device="cuda")
+    assert L.tel_sur_unpack(S._p(f32), S._p(d(norm)), S._p(r2), S._p(p2), S._p(u2), B, H, W, s()) == 0
+    torch.cuda.synchronize()
+    assert np.allclose(r2.cpu().numpy(), rho, rtol=1e-6) and np.allclose(u2.cpu().numpy(), u, rtol=1e-6, atol=1e-9)
+    # advance: f + scale * P(out) against the oracle, and mass of rho and phi kept
+    out = bf16_values(g, (B, H, W, 16))
+    scale = np.array([0.01, 0.02, 0.05, 0.05], dtype=np.float32)
+    nxt = torch.empty_like(f32)
+    mass = torch.zeros(2 * B, dtype=torch.float64, device="cuda")
+    work = torch.zeros(4 * B, dtype=torch.float32, device="cuda")
+    assert L.tel_sur_advance(S._p(f32), S._p(dev_bf16(out)), S._p(d(scale)), S._p(nxt), None, S._p(mass),
+                             S._p(work), B, H, W, s()) == 0
+    torch.cuda.synchronize()
+    f = f32.cpu().numpy().astype(np.float64)
+    want = so.advance(f, out, scale.astype(np.float64))
+    assert np.allclose(nxt.cpu().numpy(), want, rtol=1e-5, atol=1e-6)
+    ms = mass.cpu().numpy().reshape(B, 2)
+    assert np.allclose(ms, f[..., :2].sum(axis=(1, 2)), rtol=1e-6, atol=1e-4)
+
+
+def test_loss_against_oracle():
+    g = np.random.default_rng(8)
+    B, H, W = 2, 8, 16
+    out = bf16_values(g, (B, H, W, 16))
+    T = g.normal(size=(B, H, W, 4))
+    Lr, dref = so.loss(out, T)
+    dout = torch.empty((B, H, W, 16), dtype=BF, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    work = torch.zeros(4 * B, dtype=torch.float32, device="cuda")
+    tg = torch.from_numpy(T.astype(np.float32)).cuda()
+    assert L.tel_sur_loss(S._p(dev_bf16(out)), S._p(tg), S._p(dout), S._p(loss), S._p(work), B, H, W, s()) == 0
+    torch.cuda.synchronize()
+    assert abs(loss.item() - Lr) <= 1e-5 * Lr
+    assert close_bf16(host(dout), dref)
+
+
+def test_shape_errors_are_rejected_on_the_host():
+    assert L.tel_sur_conv3x3(None, None, None, None, 1, 8, 8, 16, 16, 0, s()) == -1
+    x = torch.empty(1, device="cuda")
+    assert L.tel_sur_conv3x3(S._p(x), S._p(x), None, S._p(x), 1, 8, 8, 24, 16, 0, s()) == -1  # cin 24
+    assert L.tel_sur_conv3x3(S._p(x), S._p(x), None, S._p(x), 1, 5, 5, 16, 16, 0, s()) == -1  # 25 pixels
+    assert L.tel_sur_pool2(S._p(x), S._p(x), 1, 5, 8, 16, s()) == -1
