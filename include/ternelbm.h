@@ -166,8 +166,9 @@ int tel_temperature_for_ratio(double a, double b, double R, double ratio, double
  * per-node source, compiled separately).  tel_batch_tune times every (tile width 32/64, chunk
  * 8/16/32/64) configuration on steps_per_config real steps (plus one warm-up
  * step each: they advance the state) and keeps the fastest; out = {tile width,
- * chunk, steps advanced}.  tel_batch_init must come before any step (fields as
- * for tel_init); tel_batch_fields returns host fields of case c and reports
+ * chunk, steps advanced}.  tel_batch_init (fields as for tel_init) must come
+ * before the first step; called later it restarts case c from the given
+ * fields; tel_batch_fields returns host fields of case c and reports
  * TEL_EUNSTABLE if any case flagged a node.  tel_batch_info out = {ncases,
  * total nodes, tile width, chunk, work items, persistent CTAs}. */
 typedef struct tel_batch tel_batch;

@@ -101,6 +101,10 @@ int tel_sur_advance(const float *f32, const void *out, const float *scale, float
  * sum ref^2 for rho, phi and u (u over both components). */
 int tel_sur_errors(const float *pred, const float *ref, double *acc, int B, int H, int W, void *stream);
 
+/* sums[2B] (FP64, overwritten) = per sample the sums of channels 0 and 1
+ * (density and composition) of FP32 fields [B][H][W][4]. */
+int tel_sur_sums(const float *f32, double *sums, int B, int H, int W, void *stream);
+
 /* One Adam step (bias-corrected, step t >= 1) on n FP32 master weights w32
  * with gradient g and moments m, v; w16 (bf16, may be NULL) receives the
  * updated weights rounded to bf16.  grad_scale multiplies g first. */

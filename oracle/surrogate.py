@@ -125,19 +125,28 @@ def init_params(ops, seed):
     return Ws, bs
 
 
-def forward(ops, Ws, bs, x):
-    """Returns the output and the cache the backward pass needs."""
+def _keep(a):
+    return a
+
+
+def forward(ops, Ws, bs, x, rnd=None):
+    """Returns the output and the cache the backward pass needs.
+
+    ``rnd`` (default: none) is applied to every stored activation (conv,
+    pool and add outputs); a test passes a rounding to a storage format to
+    follow a reduced-precision implementation step by step."""
+    rnd = rnd or _keep
     cache, saved = [], {}
     a = x
     for op in ops:
         if op[0] == "conv":
             _, k, ci, co, relu = op
-            y = conv_fwd(a, Ws[k], bs[k], relu)
+            y = rnd(conv_fwd(a, Ws[k], bs[k], relu))
             cache.append(("conv", k, a, y, relu))
             a = y
         elif op[0] == "pool":
             cache.append(("pool",))
-            a = pool_fwd(a)
+            a = rnd(pool_fwd(a))
         elif op[0] == "up":
             cache.append(("up",))
             a = up_fwd(a)
@@ -146,12 +155,14 @@ def forward(ops, Ws, bs, x):
             saved[op[1]] = a
         elif op[0] == "add":
             cache.append(("add", op[1]))
-            a = a + saved[op[1]]
+            a = rnd(a + saved[op[1]])
     return a, cache
 
 
-def backward(cache, Ws, dout):
-    """Gradients of every weight and bias from dL/d(output)."""
+def backward(cache, Ws, dout, rnd=None):
+    """Gradients of every weight and bias from dL/d(output); ``rnd`` as in
+    forward, applied to every stored activation gradient."""
+    rnd = rnd or _keep
     dWs = [None] * len(Ws)
     dbs = [None] * len(Ws)
     grads_saved = {}
@@ -161,15 +172,16 @@ def backward(cache, Ws, dout):
         if kind == "conv":
             _, k, a_in, y, relu = entry
             d, dWs[k], dbs[k] = conv_bwd(a_in, Ws[k], y, d, relu)
+            d = rnd(d)
         elif kind == "pool":
-            d = pool_bwd(d)
+            d = rnd(pool_bwd(d))
         elif kind == "up":
-            d = up_bwd(d)
+            d = rnd(up_bwd(d))
         elif kind == "add":
             # y = a + s: the saved activation receives the same gradient
             grads_saved[entry[1]] = d
         elif kind == "save":
-            d = d + grads_saved.pop(entry[1])
+            d = rnd(d + grads_saved.pop(entry[1]))
     return dWs, dbs, d
 
 
@@ -184,9 +196,10 @@ def project(delta):
     return p
 
 
-def loss(out, target):
+def loss(out, target, rnd=None):
     """Mean squared error of the projected change against the target change
-    (both in units of scale); returns (L, dL/d out)."""
+    (both in units of scale); returns (L, dL/d out), ``rnd`` applied to the
+    latter."""
     p = project(out)
     r = p - target
     n = r.size
@@ -194,7 +207,7 @@ def loss(out, target):
     g = 2.0 * r / n
     dout = np.zeros_like(out)
     dout[..., :NF] = project(np.concatenate([g, np.zeros(out.shape[:-1] + (out.shape[-1] - NF,))], axis=-1))
-    return L, dout
+    return L, (rnd(dout) if rnd else dout)
 
 
 def adam(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):

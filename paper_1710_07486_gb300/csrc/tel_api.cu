@@ -853,7 +853,6 @@ extern "C" int tel_batch_init(tel_batch *b, int c, const double *rho, const doub
 {
     if (!b) return TEL_EINVAL;
     if (c < 0 || c >= b->ncases || !rho || !phi || !u) return bfail(b, TEL_EINVAL, "tel_batch_init: bad case or NULL field");
-    if (b->cur != 0) return bfail(b, TEL_ESTATE, "tel_batch_init after stepping with an odd step count");
     const size_t N = (size_t)b->nx[c] * b->ny[c];
     int rc = batch_scratch(b, 4 * N);
     if (rc) return rc;
@@ -861,7 +860,7 @@ extern "C" int tel_batch_init(tel_batch *b, int c, const double *rho, const doub
     BCUDA(b, cudaMemcpyAsync(d, rho, N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
     BCUDA(b, cudaMemcpyAsync(d + N, phi, N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
     BCUDA(b, cudaMemcpyAsync(d + 2 * N, u, 2 * N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
-    tel::LaunchArgs A = batch_case_args(b, c, 1);  // writes buffer 0
+    tel::LaunchArgs A = batch_case_args(b, c, 1 - b->cur);  // writes the buffer the next step reads
     A.in_rho = d; A.in_phi = d + N; A.in_u = d + 2 * N;
     A.fsrc = A.gsrc = nullptr;
     BCUDA(b, tel::launch_d2q9(b->precision, tel::MODE_INIT, b->hP[c], A, b->stream));

@@ -658,6 +658,19 @@ __global__ void errors_kernel(const float *__restrict__ pred, const float *__res
     for (int c = 0; c < 6; ++c) block_sum_atomic(s[c], acc + 6 * b + c);
 }
 
+__global__ void sums_kernel(const float *__restrict__ f32, double *sums, long long N)
+{
+    const int b = blockIdx.y;
+    double m0 = 0.0, m1 = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x) {
+        const float4 v = *reinterpret_cast<const float4 *>(f32 + 4 * ((long long)b * N + k));
+        m0 += (double)v.x;
+        m1 += (double)v.y;
+    }
+    block_sum_atomic(m0, sums + 2 * b);
+    block_sum_atomic(m1, sums + 2 * b + 1);
+}
+
 __global__ void adam_kernel(float *w32, bf16 *w16, const float *__restrict__ g, float *m, float *v, long long n, float lr,
                             float b1, float b2, float eps, float c1, float c2, float gs)
 {
@@ -873,4 +886,13 @@ extern "C" int tel_sur_zero(float *p, long long n, void *stream)
 {
     if (!p || n < 0) return TEL_EINVAL;
     return ok(cudaMemsetAsync(p, 0, sizeof(float) * (size_t)n, S(stream)));
+}
+
+extern "C" int tel_sur_sums(const float *f32, double *sums, int B, int H, int W, void *stream)
+{
+    if (!f32 || !sums || B < 1 || H < 1 || W < 1) return TEL_EINVAL;
+    const long long N = (long long)H * W;
+    if (cudaMemsetAsync(sums, 0, sizeof(double) * 2 * B, S(stream)) != cudaSuccess) return TEL_ECUDA;
+    sums_kernel<<<dim3(blocks_per_sample(N, B), B), 256, 0, S(stream)>>>(f32, sums, N);
+    return launched();
 }

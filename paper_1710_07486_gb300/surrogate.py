@@ -29,7 +29,7 @@ U_REF = 0.1  # velocity normalisation (lattice units)
 SUR_SYMBOLS = ("tel_sur_conv3x3", "tel_sur_flip_weights", "tel_sur_relu_bwd", "tel_sur_conv3x3_wgrad",
                "tel_sur_pool2", "tel_sur_pool2_bwd", "tel_sur_up2", "tel_sur_up2_bwd", "tel_sur_add",
                "tel_sur_pack", "tel_sur_unpack", "tel_sur_gather", "tel_sur_loss", "tel_sur_advance",
-               "tel_sur_errors", "tel_sur_adam", "tel_sur_zero", "tel_sur_to_bf16")
+               "tel_sur_errors", "tel_sur_sums", "tel_sur_adam", "tel_sur_zero", "tel_sur_to_bf16")
 
 
 def sur_lib():
@@ -50,6 +50,7 @@ def sur_lib():
     L.tel_sur_loss.argtypes = [vp, vp, vp, vp, vp, i, i, i, vp]
     L.tel_sur_advance.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, vp]
     L.tel_sur_errors.argtypes = [vp, vp, vp, i, i, i, vp]
+    L.tel_sur_sums.argtypes = [vp, vp, i, i, i, vp]
     L.tel_sur_adam.argtypes = [vp, vp, vp, vp, vp, ll, f, f, f, f, i, f, vp]
     L.tel_sur_zero.argtypes = [vp, ll, vp]
     L.tel_sur_to_bf16.argtypes = [vp, vp, ll, vp]
@@ -460,3 +461,92 @@ class Predictor:
         _ok(self.L.tel_sur_errors(_p(pred), _p(ref), _p(self.err), self.B, self.H, self.W, _stream()), "errors")
         e = self.err.cpu().numpy().reshape(self.B, 3, 2)
         return np.sqrt(e[:, :, 0] / np.maximum(e[:, :, 1], 1e-300))
+
+
+class Hybrid:
+    """Surrogate time stepping with the lattice update as fallback and judge.
+
+    ``advance()`` moves B states (normalised FP32 fields [B][H][W][4]) by k
+    lattice steps.  The surrogate's proposal is accepted unless
+      * its mass residual |sum(next) - sum(prev)| / (H W) for density or
+        composition exceeds ``mass_tol`` in any sample, or
+      * on every ``check_every``-th advance, its relative L2 error against
+        the lattice update from the same fields exceeds ``err_tol`` for
+        density or composition in any sample;
+    a rejected advance is replaced by the lattice update's result, and after
+    a failed error check the remaining advances use the lattice update only.
+    """
+
+    def __init__(self, net, params, H, W, k, scale, mass_tol=1e-4, err_tol=1e-2, check_every=4):
+        import torch
+        self.torch = torch
+        self.B, self.H, self.W, self.k = len(params), H, W, k
+        self.pred = Predictor(net, self.B, H, W, scale)
+        self.lbm = Batch([(W, H)] * self.B, params)
+        self.L = net.L
+        dev = torch.device("cuda")
+        self.norm_host = np.array([[1.0 / coex_rho_l(p), 1.0 / p["chi"], 1.0 / U_REF] for p in params],
+                                  dtype=np.float32)
+        self.norm = torch.from_numpy(self.norm_host).to(dev)
+        N = H * W
+        self.rho = torch.empty((self.B, N), dtype=torch.float64, device=dev)
+        self.phi = torch.empty((self.B, N), dtype=torch.float64, device=dev)
+        self.u = torch.empty((self.B, 2, N), dtype=torch.float64, device=dev)
+        self.prop = torch.empty((self.B, H, W, NF), dtype=torch.float32, device=dev)
+        self.ref = torch.empty_like(self.prop)
+        self.sums = torch.zeros(2 * self.B, dtype=torch.float64, device=dev)
+        self.mass_tol, self.err_tol, self.check_every = mass_tol, err_tol, check_every
+        self.n = 0
+        self.lbm_only = False
+        self.log = []
+
+    def lattice_advance(self, f32, out):
+        """out = the lattice update's k steps from the fields f32 (the
+        populations restart at their equilibrium for those fields)."""
+        L, B, H, W = self.L, self.B, self.H, self.W
+        _ok(L.tel_sur_unpack(_p(f32), _p(self.norm), _p(self.rho), _p(self.phi), _p(self.u), B, H, W, _stream()),
+            "unpack")
+        r, p, u = self.rho.cpu().numpy(), self.phi.cpu().numpy(), self.u.cpu().numpy()
+        for c in range(B):
+            self.lbm.init(c, r[c], p[c], u[c])
+        self.lbm.step(self.k)
+        for c in range(B):
+            self.lbm.fields_device(c, self.rho[c], self.phi[c], self.u[c])
+        self.lbm.sync()
+        _ok(L.tel_sur_pack(_p(self.rho), _p(self.phi), _p(self.u), _p(self.norm), _p(out), None, B, H, W,
+                           _stream()), "pack")
+
+    def advance(self, f32):
+        """Advance f32 in place by k steps; returns which path produced it."""
+        B, HW = self.B, self.H * self.W
+        self.n += 1
+        if self.lbm_only:
+            self.lattice_advance(f32, self.ref)
+            f32.copy_(self.ref)
+            self.log.append("lattice")
+            return "lattice"
+        _ok(self.L.tel_sur_sums(_p(f32), _p(self.sums), B, self.H, self.W, _stream()), "sums")
+        before = self.sums.cpu().numpy().reshape(B, 2)
+        self.pred.load(f32)
+        self.pred.advance(f32, self.prop)
+        after = self.pred.mass.cpu().numpy().reshape(B, 2)
+        resid = np.abs(after - before) / HW
+        path = "surrogate"
+        if np.any(resid > self.mass_tol):
+            self.lattice_advance(f32, self.ref)
+            f32.copy_(self.ref)
+            path = "lattice (mass residual)"
+        elif self.check_every and self.n % self.check_every == 0:
+            self.lattice_advance(f32, self.ref)
+            err = self.pred.errors(self.prop, self.ref)
+            if np.any(err[:, :2] > self.err_tol):
+                f32.copy_(self.ref)
+                self.lbm_only = True
+                path = "lattice (error check failed)"
+            else:
+                f32.copy_(self.prop)
+                path = "surrogate (checked)"
+        else:
+            f32.copy_(self.prop)
+        self.log.append(path)
+        return path

@@ -128,9 +128,20 @@ def test_pool_up_add_relu_bwd():
     assert np.array_equal(host(r), so.up_fwd(c) * (x > 0))
 
 
+def to_bf16(a):
+    """Round-to-nearest-even to BF16 through FP32, as the kernels store."""
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(BF).double().numpy()
+
+
 def test_network_gradients_against_oracle():
     """Whole encoder-decoder: forward output, loss and every layer's weight
-    and bias gradient from the library's kernels against the oracle."""
+    and bias gradient from the library's kernels against the oracle, twice:
+    (a) with the oracle rounding each stored activation and activation
+    gradient to BF16 where the kernels store BF16 -- then only FP32-vs-FP64
+    sums (and the rare rounding or ReLU decision they flip) differ: 1e-2 in
+    norm per layer; (b) against the exact FP64 oracle: the twenty-odd BF16
+    roundings of an untrained network add up to several per cent in the
+    first layers' gradients: 1.5e-1 in norm, with the last layer at 2e-2."""
     widths = (16, 16, 32)
     assert [(ci, co) for _, ci, co, _ in [op for op in S.layers(*widths) if op[0] == "conv"]] == \
         so.conv_shapes(so.arch(*widths))
@@ -153,6 +164,9 @@ def test_network_gradients_against_oracle():
     out_ref, cache = so.forward(so.arch(*widths), Ws, bs, x)
     L_ref, dout_ref = so.loss(out_ref, T)
     dWs, dbs, _ = so.backward(cache, Ws, dout_ref)
+    out_e, cache_e = so.forward(so.arch(*widths), Ws, bs, x, rnd=to_bf16)
+    _, dout_e = so.loss(out_e, T, rnd=to_bf16)
+    dWe, dbe, _ = so.backward(cache_e, Ws, dout_e, rnd=to_bf16)
 
     x16 = dev_bf16(x)
     out = net.forward(x16, B, H, W)
@@ -168,11 +182,15 @@ def test_network_gradients_against_oracle():
     assert np.linalg.norm(o - out_ref) <= 2e-2 * np.linalg.norm(out_ref)
     assert abs(float(loss.item()) - L_ref) <= 1e-2 * L_ref
     gh = net.g.cpu().numpy().astype(np.float64)
+    rel = lambda a, b: np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+    ew, ee = [], []
     for k, (_, ci, co, _) in enumerate(net.convs):
         gW = gh[net.woff[k]:net.woff[k] + 9 * co * ci].reshape(9, co, ci).transpose(0, 2, 1)
         gb = gh[net.boff[k]:net.boff[k] + co]
-        assert np.linalg.norm(gW - dWs[k]) <= 5e-2 * np.linalg.norm(dWs[k]), k
-        assert np.linalg.norm(gb - dbs[k]) <= 5e-2 * max(np.linalg.norm(dbs[k]), 1e-12), k
+        ee.append(max(rel(gW, dWe[k]), rel(gb, dbe[k])))
+        ew.append(max(rel(gW, dWs[k]), rel(gb, dbs[k])))
+    assert max(ee) <= 1e-2, np.round(ee, 4)
+    assert max(ew) <= 1.5e-1 and ew[-1] <= 2e-2, np.round(ew, 4)
 
 
 def test_adam_and_bf16_copy_against_oracle():
