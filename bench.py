@@ -187,6 +187,147 @@ def run_c4(args):
     print(json.dumps(line), flush=True)
 
 
+def c5_setup(seed, n, H, rmin=100.0, rmax=1000.0):
+    """n 2D collisions in H x H periodic boxes (the batched-case recipe at
+    one size): parameters and initial fields."""
+    import paper_1710_07486_gb300 as tel
+    from paper_1710_07486_gb300 import inputs
+    g = np.random.default_rng(seed)
+    params, fields = [], []
+    for _ in range(n):
+        w = dict(n=H, ratio=float(g.uniform(rmin, rmax)), B=float(g.uniform(0.0, 1.0)),
+                 We=float(g.uniform(1.0, 100.0)), sigma_ratio=float(g.choice([0.5, 1.0, 2.0])))
+        T = tel.temperature_for_ratio(A_, B_, R_, w["ratio"])
+        rho_g, rho_l = tel.coexistence(A_, B_, R_, T)[:2]
+        p, V, _ = c3_params(w, T, rho_g, rho_l, R=H / 8.0)
+        p["precision"] = tel.FP32_SHIFTED
+        params.append(p)
+        fields.append(inputs.off_centre_2d(H, rho_g, rho_l, p["chi"], V, w["B"], H / 8.0, width=10.0))
+    return params, fields
+
+
+def run_c5(args):
+    """Learned surrogate: snapshots from the batched lattice update, training
+    with the library's BF16 kernels, held-out field errors, and the time of
+    one surrogate advance against k lattice steps for the same states."""
+    import torch
+    import paper_1710_07486_gb300 as tel
+    from paper_1710_07486_gb300 import surrogate as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    H, k, nsnap = args.c5_n, args.c5_k, args.c5_snaps
+    ntrain, ntest = args.c5_train_traj, args.c5_test_traj
+    params, fields = c5_setup(args.seed, ntrain + ntest, H)
+    t0 = time.time()
+    sn = S.Snapshots((H, H), params, fields, k, nsnap)
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    good = sn.good
+    test = good[good >= ntrain]
+    sn.good = good[good < ntrain]
+    net = S.Net((32, 64, 128), seed=args.seed)
+    tr = S.Trainer(net, sn, B=args.c5_batch, seed=args.seed)
+    t0 = time.time()
+    hist = tr.train(args.c5_iters, lr=args.c5_lr, log_every=max(args.c5_iters // 8, 1))
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+
+    # held-out one-advance errors (every snapshot pair of the test trajectories)
+    Bt = len(test)
+    pr = S.Predictor(net, Bt, H, H, tr.scale_host)
+    e_net, e_per = [], []
+    nxt = torch.empty((Bt, H, H, S.NF), dtype=torch.float32, device="cuda")
+    resid = 0.0
+    sums = torch.zeros(2 * Bt, dtype=torch.float64, device="cuda")
+    for s in range(nsnap - 1):
+        src = sn.store[s, test].contiguous()
+        ref = sn.store[s + 1, test].contiguous()
+        pr.load(src)
+        pr.advance(src, nxt)
+        e_net.append(pr.errors(nxt, ref))
+        e_per.append(pr.errors(src, ref))
+        m1 = pr.mass.cpu().numpy().reshape(Bt, 2)
+        S.sur_lib().tel_sur_sums(S._p(src), S._p(sums), Bt, H, H, S._stream())
+        m0 = sums.cpu().numpy().reshape(Bt, 2)
+        resid = max(resid, float(np.abs(m1 - m0).max() / (H * H)))
+    e_net, e_per = np.array(e_net), np.array(e_per)
+    # rollout from the first snapshot
+    cur = sn.store[0, test].contiguous()
+    roll = []
+    pr.load(cur)
+    for s in range(nsnap - 1):
+        pr.advance(cur, nxt)
+        cur.copy_(nxt)
+        roll.append(pr.errors(cur, sn.store[s + 1, test].contiguous()).mean(axis=0))
+    roll = np.array(roll)
+    ok_adv = 0
+    for r in roll:
+        if r[0] <= 0.01 and r[1] <= 0.01:
+            ok_adv += 1
+        else:
+            break
+
+    # timing: surrogate advance vs k lattice steps, same Bt states, same GPU
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    src = sn.store[0, test].contiguous()
+    with torch.cuda.stream(stream):
+        pr.load(src)
+        for _ in range(3):
+            pr.advance(src, nxt, mass=False)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            pr.advance(src, nxt, mass=False)
+        e1.record(stream)
+    e1.synchronize()
+    ms_sur = e0.elapsed_time(e1) / args.steps
+    b = tel.Batch([(H, H)] * Bt, [params[i] for i in test])
+    for j, i in enumerate(test):
+        b.init(j, *fields[i])
+    b.set_stream(stream)
+    b.step(3)
+    b.step(3)
+    stream.synchronize()
+    e0.record(stream)
+    b.step(k * args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_lbm = e0.elapsed_time(e1) / args.steps
+    b.close()
+    mean_net = e_net.mean(axis=(0, 1))
+    max_net = e_net.max(axis=(0, 1))
+    mean_per = e_per.mean(axis=(0, 1))
+    within = bool(max_net[0] <= 0.01 and max_net[1] <= 0.01)
+    line = {
+        "metric": "surrogate speedup at <=1% field error (one k-step advance vs k lattice steps, same GPU)",
+        "value": round(ms_lbm / ms_sur, 3), "unit": "x", "n_gpus": 1, "steps": args.steps, "warmup": 3,
+        "ms_per_step": round(ms_sur, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (FP32 accumulation)", "data": "synthetic (snapshots of seeded LBM collisions; no dataset)",
+        "config": {"workload": f"D2Q9 {H}^2 periodic collisions, density ratio U[100,1000], FP32-shifted LBM, "
+                               f"k={k} steps per advance", "train_trajectories": int(len(sn.good)),
+                   "test_trajectories": int(Bt), "unstable_trajectories": int(sn.bad.sum()),
+                   "snapshots": nsnap, "params": net.n, "train_iters": args.c5_iters, "batch": args.c5_batch,
+                   "seed": args.seed},
+        "errors": {"one_advance_mean": {"rho": round(float(mean_net[0]), 6), "phi": round(float(mean_net[1]), 6),
+                                        "u": round(float(mean_net[2]), 6)},
+                   "one_advance_max": {"rho": round(float(max_net[0]), 6), "phi": round(float(max_net[1]), 6),
+                                       "u": round(float(max_net[2]), 6)},
+                   "persistence_mean": {"rho": round(float(mean_per[0]), 6), "phi": round(float(mean_per[1]), 6),
+                                        "u": round(float(mean_per[2]), 6)},
+                   "rollout_mean_last": [round(float(v), 6) for v in roll[-1]],
+                   "rollout_advances_within_1pct": ok_adv,
+                   "mass_residual_max": resid,
+                   "within_1pct_rho_phi": within},
+        "timing": {"surrogate_ms_per_advance": round(ms_sur, 4), "lattice_ms_per_k_steps": round(ms_lbm, 4),
+                   "data_s": round(t_data, 2), "train_s": round(t_train, 2),
+                   "train_ms_per_iter": round(1e3 * t_train / max(args.c5_iters, 1), 3)},
+        "loss": [[i, round(l, 6)] for i, l in hist],
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def sample_clocks(stop, out):
     cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -454,9 +595,18 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--ref-n", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c4"],
-                    help="c3: D3Q27 256^3 collision (default); c4: batched uneven D2Q9 cases")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5"],
+                    help="c3: D3Q27 256^3 collision (default); c4: batched uneven D2Q9 cases; "
+                         "c5: learned surrogate (train + evaluate)")
     ap.add_argument("--c4-cases", type=int, default=256)
+    ap.add_argument("--c5-n", type=int, default=256)
+    ap.add_argument("--c5-k", type=int, default=50)
+    ap.add_argument("--c5-snaps", type=int, default=24)
+    ap.add_argument("--c5-train-traj", type=int, default=48)
+    ap.add_argument("--c5-test-traj", type=int, default=8)
+    ap.add_argument("--c5-iters", type=int, default=2000)
+    ap.add_argument("--c5-batch", type=int, default=8)
+    ap.add_argument("--c5-lr", type=float, default=1e-3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -464,6 +614,8 @@ def main():
         run_reference(args)
     elif args.workload == "c4":
         run_c4(args)
+    elif args.workload == "c5":
+        run_c5(args)
     else:
         run_gpu(args)
 
