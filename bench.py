@@ -271,15 +271,16 @@ def run_c5(args):
     stream = torch.cuda.Stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     src = sn.store[0, test].contiguous()
-    with torch.cuda.stream(stream):
-        pr.load(src)
-        for _ in range(3):
-            pr.advance(src, nxt, mass=False)
-        stream.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            pr.advance(src, nxt, mass=False)
-        e1.record(stream)
+    pr.load(src)
+    graph = pr.capture(src, nxt)  # one advance = one graph replay
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
+    e0.record(cur)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(cur)
     e1.synchronize()
     ms_sur = e0.elapsed_time(e1) / args.steps
     b = tel.Batch([(H, H)] * Bt, [params[i] for i in test])

@@ -455,6 +455,22 @@ class Predictor:
                                    _p(self.mass) if mass else None, _p(self.work), self.B, self.H, self.W,
                                    _stream()), "advance")
 
+    def capture(self, f32, f32_next):
+        """CUDA graph of one advance from f32 into f32_next (network forward,
+        head, next input), replayed by replay().  Every kernel has run once
+        before capture (shared-memory attributes are set on first launch)."""
+        torch = self.torch
+        self.advance(f32, f32_next, mass=False)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.advance(f32, f32_next, mass=False)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
     def errors(self, pred, ref):
         """Relative L2 errors (rho, phi, u) per sample, host array [B][3]."""
         _ok(self.L.tel_sur_zero(_p(self.err), 12 * self.B, _stream()), "zero")  # 6B doubles = 12B floats
