@@ -77,9 +77,14 @@ int tel_sur_unpack(const float *f32, const float *norm, double *rho, double *phi
 
 /* Training batch from a snapshot store (FP32 [S][H][W][4]): for sample k,
  * input = store[src[k]] (written to f32 [B][H][W][4] and x16) and target
- * = (store[dst[k]] - store[src[k]]) / scale (FP32 [B][H][W][4]). */
-int tel_sur_gather(const float *store, const int *src, const int *dst, const float *scale, float *f32, void *x16,
-                   float *target, int B, int H, int W, void *stream);
+ * = (store[dst[k]] - store[src[k]]) / scale (FP32 [B][H][W][4]).  sym
+ * (may be NULL; square lattices only) gives per sample an element of the
+ * lattice's symmetry group applied to input and target alike: bit 0 mirrors
+ * x (u_x -> -u_x), bit 1 mirrors y (u_y -> -u_y), bit 2 transposes first
+ * (u_x <-> u_y); mirror images of a lattice trajectory are trajectories of
+ * the same update, so they augment the training set. */
+int tel_sur_gather(const float *store, const int *src, const int *dst, const int *sym, const float *scale,
+                   float *f32, void *x16, float *target, int B, int H, int W, void *stream);
 
 /* Head and loss.  The prediction is the network output's channels 0..3 with
  * the spatial mean of channels 0 and 1 removed per sample (mass-conserving

@@ -274,6 +274,7 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
     const double tau = 3.0 * p.nu + 0.5;
     d.beta = 1.0 / (2.0 * tau);
     d.inv_beta = 2.0 * tau;
+    d.c_gb = 2.0 * d.beta - 1.0;
     d.Gamma = p.Gamma;
     d.inv_tau_g = 1.0 / p.tau_g;
     d.rho_ref = p.precision == TEL_FP32_SHIFTED ? (p.rho_ref > 0 ? p.rho_ref : co[0]) : 0.0;

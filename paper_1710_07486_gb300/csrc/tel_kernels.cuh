@@ -63,6 +63,7 @@ struct DevParams {
     double h_g;                       // (24 - 2 b rho_g)/(b rho_g - 4)^3
     // collision
     double beta, inv_beta;            // beta = 1/(2 tau)
+    double c_gb;                      // 2 beta - 1: beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh>
     double Gamma, inv_tau_g;
     double rho_ref;                   // FP32 shift (0 in FP64)
     unsigned *err;                    // device error word
@@ -204,8 +205,9 @@ __device__ __forceinline__ float mu_eos_gas(const DevParams &P, float rho)
     const float L = log1pf((float)(dg * P.inv_rho_g));
     const double d = P.b * t - 4.0;
     const double d3 = d * d * d;
+    // FP32 seed (relative error ~2^-23) and one Newton-Raphson step in FP64:
+    // ~2^-46, far below the FP32 logarithm's share of the result
     double r = (double)__frcp_rn((float)d3);
-    r = r * (2.0 - d3 * r);
     r = r * (2.0 - d3 * r);
     const double h = (24.0 - 2.0 * P.b * t) * r;
     const double eos = P.RT * (double)L - 8.0 * P.RT * (h - P.h_g) - 2.0 * P.a * dg;
@@ -664,24 +666,27 @@ struct Fused {
                 hhd += (double)(dh * dh * r);
             }
         }
-        // stabiliser gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh> in FP64
-        // (FP32 storage: from the two compensated FP32 sums, with 1/<dh|dh> an
-        // FP32 reciprocal refined by one Newton-Raphson step in FP64)
-        double gamma = 2.0;
+        // stabiliser gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh> in FP64,
+        // applied as beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh> (gamma = 2,
+        // i.e. beta gamma = 2 beta, when <dh|dh> vanishes).  FP32 storage:
+        // <ds|dh> is the compensated pair (sum + correction) added in FP64,
+        // 1/<dh|dh> an FP32 reciprocal refined by one Newton-Raphson step in
+        // FP64.
+        double gbd = 2.0 * P.beta;
         if (StoreTraits<ST>::shifted) {
-            const CT shs = sh + shc, hhs = hh;
-            if (hhs > (CT)1e-30 * rho * rho) {
-                const double H = (double)hhs;
-                double rH = (double)__frcp_rn((float)hhs);
+            if (hh > (CT)1e-30 * rho * rho) {
+                const double shs = (double)sh + (double)shc;
+                const double H = (double)hh;
+                double rH = (double)__frcp_rn((float)hh);
                 rH = rH * (2.0 - H * rH);
-                gamma = P.inv_beta - (2.0 - P.inv_beta) * ((double)shs * rH);
+                gbd = 1.0 - P.c_gb * (shs * rH);
             }
         } else {
             const double rhod = (double)rho;
-            if (hhd > 1e-30 * rhod * rhod) gamma = P.inv_beta - (2.0 - P.inv_beta) * shd / hhd;
+            if (hhd > 1e-30 * rhod * rhod) gbd = 1.0 - P.c_gb * (shd / hhd);
         }
-        if (!isfinite(gamma)) bad |= ERR_NAN;
-        const CT bet = K.beta, gb = (CT)(gamma * P.beta);
+        if (!isfinite(gbd)) bad |= ERR_NAN;
+        const CT bet = K.beta, gb = (CT)gbd;
         ST *fd = reinterpret_cast<ST *>(A.fdst);
         // FP32 storage: the rest population closes the node's mass so that the
         // stored set sums to the pulled mass; rounding of the other outputs

@@ -520,14 +520,39 @@ __global__ void unpack_kernel(const float *__restrict__ f32, const float *__rest
     }
 }
 
-__global__ void gather_kernel(const float *__restrict__ store, const int *__restrict__ src, const int *__restrict__ dst,
-                              const float *__restrict__ scale, float *f32, bf16 *x16, float *target, int B, long long N)
+// Symmetry code s of the square lattice's dihedral group: bit 0 mirrors x,
+// bit 1 mirrors y, bit 2 transposes (applied first).  Output node (h, w)
+// reads source node (hs, ws); velocities transform with the coordinates.
+__device__ __forceinline__ long long sym_source(int s, long long k, int H, int W, float &sx, float &sy, bool &swap)
 {
+    const int h = (int)(k / W), w = (int)(k % W);
+    const int w1 = (s & 1) ? W - 1 - w : w;
+    const int h1 = (s & 2) ? H - 1 - h : h;
+    swap = (s & 4) != 0;
+    sx = (s & 1) ? -1.f : 1.f;
+    sy = (s & 2) ? -1.f : 1.f;
+    return swap ? (long long)w1 * W + h1 : (long long)h1 * W + w1;
+}
+
+__global__ void gather_kernel(const float *__restrict__ store, const int *__restrict__ src, const int *__restrict__ dst,
+                              const int *__restrict__ sym, const float *__restrict__ scale, float *f32, bf16 *x16,
+                              float *target, int B, int H, int W)
+{
+    const long long N = (long long)H * W;
     const long long n = (long long)B * N;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const long long b = e / N, k = e % N;
-        const float4 a = *reinterpret_cast<const float4 *>(store + 4 * ((long long)src[b] * N + k));
-        const float4 z = *reinterpret_cast<const float4 *>(store + 4 * ((long long)dst[b] * N + k));
+        const long long b = e / N;
+        float sx = 1.f, sy = 1.f;
+        bool swap = false;
+        const long long k = sym ? sym_source(sym[b] & 7, e % N, H, W, sx, sy, swap) : e % N;
+        float4 a = *reinterpret_cast<const float4 *>(store + 4 * ((long long)src[b] * N + k));
+        float4 z = dst ? *reinterpret_cast<const float4 *>(store + 4 * ((long long)dst[b] * N + k)) : a;
+        if (swap) {
+            float t = a.z; a.z = a.w; a.w = t;
+            t = z.z; z.z = z.w; z.w = t;
+        }
+        a.z *= sx; a.w *= sy;
+        z.z *= sx; z.w *= sy;
         if (f32) *reinterpret_cast<float4 *>(f32 + 4 * e) = a;
         if (target)
             *reinterpret_cast<float4 *>(target + 4 * e) =
@@ -817,13 +842,13 @@ extern "C" int tel_sur_unpack(const float *f32, const float *norm, double *rho, 
     return launched();
 }
 
-extern "C" int tel_sur_gather(const float *store, const int *src, const int *dst, const float *scale, float *f32,
-                              void *x16, float *target, int B, int H, int W, void *stream)
+extern "C" int tel_sur_gather(const float *store, const int *src, const int *dst, const int *sym, const float *scale,
+                              float *f32, void *x16, float *target, int B, int H, int W, void *stream)
 {
     if (!store || !src || (target && (!dst || !scale)) || B < 1 || H < 1 || W < 1) return TEL_EINVAL;
-    const long long N = (long long)H * W;
-    gather_kernel<<<blocks_for((long long)B * N), 256, 0, S(stream)>>>(store, src, dst, scale, f32, (bf16 *)x16,
-                                                                       target, B, N);
+    if (sym && H != W) return TEL_EINVAL;  // transposition needs a square lattice
+    gather_kernel<<<blocks_for((long long)B * H * W), 256, 0, S(stream)>>>(store, src, dst, sym, scale, f32,
+                                                                           (bf16 *)x16, target, B, H, W);
     return launched();
 }
 

@@ -46,7 +46,7 @@ def sur_lib():
     L.tel_sur_add.argtypes = [vp, vp, vp, ll, vp]
     L.tel_sur_pack.argtypes = [vp, vp, vp, vp, vp, vp, i, i, i, vp]
     L.tel_sur_unpack.argtypes = [vp, vp, vp, vp, vp, i, i, i, vp]
-    L.tel_sur_gather.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, vp]
+    L.tel_sur_gather.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, i, i, vp]
     L.tel_sur_loss.argtypes = [vp, vp, vp, vp, vp, i, i, i, vp]
     L.tel_sur_advance.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, vp]
     L.tel_sur_errors.argtypes = [vp, vp, vp, i, i, i, vp]
@@ -358,6 +358,7 @@ class Snapshots:
         a = flat[src[idx]].cpu().numpy().astype(np.float64)
         z = flat[dst[idx]].cpu().numpy().astype(np.float64)
         rms = np.sqrt(((z - a) ** 2).mean(axis=(0, 1, 2)))
+        rms[2] = rms[3] = np.sqrt(0.5 * (rms[2] ** 2 + rms[3] ** 2))  # one scale: symmetries mix u_x, u_y
         return np.maximum(rms, 1e-8).astype(np.float32)
 
 
@@ -372,7 +373,7 @@ def coex_rho_l(p):
 class Trainer:
     """Adam on the mean squared error of the projected k-step change."""
 
-    def __init__(self, net, snaps, B=8, seed=0, scale=None):
+    def __init__(self, net, snaps, B=8, seed=0, scale=None, augment=True):
         import torch
         self.net, self.snaps, self.B = net, snaps, B
         self.torch = torch
@@ -388,7 +389,8 @@ class Trainer:
         self.dout = torch.empty((B, H, W, COUT), dtype=torch.bfloat16, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.work = torch.zeros(4 * B, dtype=torch.float32, device=dev)
-        self.idx = torch.empty((2, B), dtype=torch.int32, device=dev)
+        self.idx = torch.empty((3, B), dtype=torch.int32, device=dev)
+        self.augment = augment and H == W
         self.rng = np.random.default_rng(seed)
         self.L = L
 
@@ -399,10 +401,11 @@ class Trainer:
         L, net = self.L, self.net
         s = _stream()
         pick = self.rng.integers(0, len(self.src), size=B)
-        self.idx.copy_(self.torch.from_numpy(np.stack([self.src[pick], self.dst[pick]])), non_blocking=False)
+        sym = self.rng.integers(0, 8, size=B).astype(np.int32)
+        self.idx.copy_(self.torch.from_numpy(np.stack([self.src[pick], self.dst[pick], sym])), non_blocking=False)
         flat = self.snaps.store.view(-1, H, W, NF)
-        _ok(L.tel_sur_gather(_p(flat), _p(self.idx[0]), _p(self.idx[1]), _p(self.scale), _p(self.f32),
-                             _p(self.x16), _p(self.tgt), B, H, W, s), "gather")
+        _ok(L.tel_sur_gather(_p(flat), _p(self.idx[0]), _p(self.idx[1]), _p(self.idx[2]) if self.augment else None,
+                             _p(self.scale), _p(self.f32), _p(self.x16), _p(self.tgt), B, H, W, s), "gather")
         out = net.forward(self.x16, B, H, W)
         _ok(L.tel_sur_zero(_p(self.loss), 1, s), "zero")
         _ok(L.tel_sur_loss(_p(out), _p(self.tgt), _p(self.dout), _p(self.loss), _p(self.work), B, H, W, s), "loss")
@@ -442,8 +445,8 @@ class Predictor:
         with the identity index list)."""
         import torch
         idx = torch.arange(self.B, dtype=torch.int32, device=f32.device)
-        _ok(self.L.tel_sur_gather(_p(f32), _p(idx), None, None, None, _p(self.x16), None, self.B, self.H, self.W,
-                                  _stream()), "gather")
+        _ok(self.L.tel_sur_gather(_p(f32), _p(idx), None, None, None, None, _p(self.x16), None, self.B, self.H,
+                                  self.W, _stream()), "gather")
 
     def advance(self, f32, f32_next, mass=True):
         """f32_next = surrogate(f32); self.x16 must hold f32's network input

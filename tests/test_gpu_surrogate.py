@@ -353,3 +353,41 @@ def test_hybrid_hands_back_to_the_lattice_update(snaps):
     hy.lattice_advance(st, ref)
     e = hy.pred.errors(ref, sn.store[1, :4].contiguous())
     assert np.all(e[:, :2] < 5e-2), e
+
+
+def test_gather_symmetry_augmentation():
+    """Each of the eight symmetries of the square lattice maps input and
+    target like the numpy transform of the fields (velocity components
+    mirrored and swapped with the coordinates)."""
+    g = np.random.default_rng(9)
+    H = W = 16
+    store = g.normal(size=(2, H, W, 4)).astype(np.float32)
+    st = torch.from_numpy(store).cuda()
+    B = 8
+    src = torch.zeros(B, dtype=torch.int32, device="cuda")
+    dst = torch.ones(B, dtype=torch.int32, device="cuda")
+    sym = torch.arange(8, dtype=torch.int32, device="cuda")
+    scale = torch.tensor([1.0, 2.0, 4.0, 4.0], dtype=torch.float32, device="cuda")
+    f32 = torch.empty((B, H, W, 4), dtype=torch.float32, device="cuda")
+    tgt = torch.empty_like(f32)
+    assert L.tel_sur_gather(S._p(st), S._p(src), S._p(dst), S._p(sym), S._p(scale), S._p(f32), None, S._p(tgt),
+                            B, H, W, s()) == 0
+    torch.cuda.synchronize()
+
+    def transform(a, code):
+        a = a.copy()
+        if code & 4:
+            a = a.transpose(1, 0, 2)[..., [0, 1, 3, 2]]
+        if code & 2:
+            a = a[::-1].copy()
+            a[..., 3] *= -1
+        if code & 1:
+            a = a[:, ::-1].copy()
+            a[..., 2] *= -1
+        return a
+
+    got_in, got_t = f32.cpu().numpy(), tgt.cpu().numpy()
+    for code in range(8):
+        a, z = transform(store[0], code), transform(store[1], code)
+        assert np.array_equal(got_in[code], a), code
+        assert np.allclose(got_t[code], (z - a) / np.array([1.0, 2.0, 4.0, 4.0]), rtol=1e-6, atol=1e-6), code
