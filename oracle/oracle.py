@@ -31,7 +31,16 @@ class Params(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "a", "b", "R", "T", "lambda1", "lambda2", "lambda3",
         "kappa1", "kappa2", "kappa3", "chi", "nu", "Gamma", "tau_g")] + [
-        ("force_form", C.c_int)]
+        ("force_form", C.c_int), ("eos", C.c_int), ("omega", C.c_double)]
+
+
+CS, VDW, PR = 0, 1, 2  # equations of state
+
+
+class Eos(C.Structure):
+    """Mirror of ``orc_eos``."""
+
+    _fields_ = [("kind", C.c_int)] + [(n, C.c_double) for n in ("a", "b", "R", "T", "omega")]
 
 
 def build(force: bool = False) -> str:
@@ -69,6 +78,18 @@ def lib():
         L.orc_critical_point.restype = C.c_int
         L.orc_temperature_for_ratio.argtypes = [d, d, d, d, C.POINTER(d)]
         L.orc_temperature_for_ratio.restype = C.c_int
+        for name in ("orc_eos_psi", "orc_eos_dpsi", "orc_eos_p"):
+            fn = getattr(L, name)
+            fn.argtypes = [C.POINTER(Eos), d]
+            fn.restype = d
+        L.orc_eos_coexistence.argtypes = [C.POINTER(Eos), dp]
+        L.orc_eos_coexistence.restype = C.c_int
+        L.orc_eos_critical_point.argtypes = [C.c_int, d, d, d, d, dp]
+        L.orc_eos_critical_point.restype = C.c_int
+        L.orc_eos_temperature_for_ratio.argtypes = [C.c_int, d, d, d, d, d, C.POINTER(d)]
+        L.orc_eos_temperature_for_ratio.restype = C.c_int
+        L.orc_pr_tc.argtypes = [d, d, d]
+        L.orc_pr_tc.restype = d
         L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(Params), ip]
         L.orc_create.restype = C.c_void_p
         L.orc_destroy.argtypes = [C.c_void_p]
@@ -153,6 +174,47 @@ def temperature_for_ratio(a, b, R, ratio):
     return T.value
 
 
+def _eos(kind, a, b, R, T, omega):
+    return Eos(int(kind), float(a), float(b), float(R), float(T), float(omega))
+
+
+def eos_psi(kind, a, b, R, T, rho, omega=0.0):
+    return lib().orc_eos_psi(C.byref(_eos(kind, a, b, R, T, omega)), rho)
+
+
+def eos_dpsi(kind, a, b, R, T, rho, omega=0.0):
+    return lib().orc_eos_dpsi(C.byref(_eos(kind, a, b, R, T, omega)), rho)
+
+
+def eos_p(kind, a, b, R, T, rho, omega=0.0):
+    return lib().orc_eos_p(C.byref(_eos(kind, a, b, R, T, omega)), rho)
+
+
+def eos_coexistence(kind, a, b, R, T, omega=0.0):
+    out = np.zeros(4)
+    if lib().orc_eos_coexistence(C.byref(_eos(kind, a, b, R, T, omega)), out) != 0:
+        raise ValueError("no coexistence at this temperature")
+    return tuple(float(v) for v in out)
+
+
+def eos_critical_point(kind, a, b, R, omega=0.0):
+    out = np.zeros(2)
+    if lib().orc_eos_critical_point(int(kind), a, b, R, omega, out) != 0:
+        raise ValueError("bad EOS constants")
+    return float(out[0]), float(out[1])
+
+
+def eos_temperature_for_ratio(kind, a, b, R, ratio, omega=0.0):
+    T = C.c_double()
+    if lib().orc_eos_temperature_for_ratio(int(kind), a, b, R, omega, ratio, C.byref(T)) != 0:
+        raise ValueError("ratio out of range")
+    return T.value
+
+
+def pr_tc(a, b, R):
+    return lib().orc_pr_tc(a, b, R)
+
+
 # ---------------------------------------------------------------- lattice model
 class Oracle:
     """One lattice (D2Q9 or D3Q27) with its parameters; state arrays are numpy
@@ -162,8 +224,9 @@ class Oracle:
         self.lattice = lattice
         self.nx, self.ny, self.nz = nx, ny, nz
         self.params = dict(params)
-        vals = {k: float(params[k]) for k, _ in Params._fields_ if k != "force_form"}
-        p = Params(force_form=int(params.get("force_form", 1)), **vals)
+        vals = {k: float(params[k]) for k, _ in Params._fields_ if k not in ("force_form", "eos", "omega")}
+        p = Params(force_form=int(params.get("force_form", 1)), eos=int(params.get("eos", CS)),
+                   omega=float(params.get("omega", 0.0)), **vals)
         bca = np.asarray(bc, dtype=np.int32)
         self._h = lib().orc_create(lattice, nx, ny, nz, C.byref(p), bca)
         if not self._h:

@@ -38,7 +38,7 @@ struct orc_ctx {
 
 /* Psi~(rho) = rho ( -a rho - 8RT(b rho - 6)/(b rho - 4)^2 + RT ln rho ), Eq. 4
    with C = 0. */
-double orc_psi_tilde(double a, double b, double R, double T, double rho)
+static double cs_psi(double a, double b, double R, double T, double rho)
 {
     double br = b * rho;
     return rho * (-a * rho - 8.0 * R * T * (br - 6.0) / ((br - 4.0) * (br - 4.0))
@@ -47,7 +47,7 @@ double orc_psi_tilde(double a, double b, double R, double T, double rho)
 
 /* d Psi~ / d rho, differentiated by hand from Eq. 4:
    -2 a rho - 8RT (24 - 2 b rho)/(b rho - 4)^3 + RT (ln rho + 1). */
-double orc_dpsi_tilde(double a, double b, double R, double T, double rho)
+static double cs_dpsi(double a, double b, double R, double T, double rho)
 {
     double br = b * rho;
     double d = br - 4.0;
@@ -55,24 +55,101 @@ double orc_dpsi_tilde(double a, double b, double R, double T, double rho)
            + R * T * (log(rho) + 1.0);
 }
 
+/* The other two equations of state the text names as alternatives (their
+   formulas are in the unavailable supplement; these are the textbook forms,
+   with Psi~ obtained, like Eq. 4, by integrating p_eos = rho Psi' - Psi, i.e.
+   Psi~/rho = int p_eos / rho^2 drho, integration constant zero):
+     van der Waals:  p = rho R T/(1 - b rho) - a rho^2
+                     Psi~ = rho R T ln(rho/(1 - b rho)) - a rho^2
+     Peng-Robinson:  p = rho R T/(1 - b rho) - a alpha rho^2/(1 + 2 b rho - b^2 rho^2)
+                     Psi~ = rho R T ln(rho/(1 - b rho))
+                            - a alpha/(2 sqrt2 b) rho ln((1 + (1+sqrt2) b rho)/(1 + (1-sqrt2) b rho))
+     alpha(T) = (1 + k (1 - sqrt(T/T_c)))^2, k = 0.37464 + 1.54226 w - 0.26992 w^2,
+     T_c = 0.07780 a/(0.45724 b R) (acentric factor w). */
+double orc_pr_tc(double a, double b, double R) { return 0.07780 * a / (0.45724 * b * R); }
+
+static double pr_alpha(const orc_eos *e)
+{
+    double k = 0.37464 + 1.54226 * e->omega - 0.26992 * e->omega * e->omega;
+    double q = 1.0 + k * (1.0 - sqrt(e->T / orc_pr_tc(e->a, e->b, e->R)));
+    return q * q;
+}
+
+double orc_eos_psi(const orc_eos *e, double rho)
+{
+    double a = e->a, b = e->b, RT = e->R * e->T;
+    switch (e->kind) {
+    case ORC_EOS_VDW:
+        return rho * RT * log(rho / (1.0 - b * rho)) - a * rho * rho;
+    case ORC_EOS_PR: {
+        double s2 = sqrt(2.0), aa = a * pr_alpha(e);
+        return rho * RT * log(rho / (1.0 - b * rho))
+               - aa / (2.0 * s2 * b) * rho * log((1.0 + (1.0 + s2) * b * rho) / (1.0 + (1.0 - s2) * b * rho));
+    }
+    default:
+        return cs_psi(a, b, e->R, e->T, rho);
+    }
+}
+
+/* d Psi~/d rho, by hand from the forms above:
+     vdW: RT ln(rho/(1 - b rho)) + RT/(1 - b rho) - 2 a rho
+     PR:  RT ln(rho/(1 - b rho)) + RT/(1 - b rho)
+          - a alpha/(2 sqrt2 b) ln((1 + (1+sqrt2) b rho)/(1 + (1-sqrt2) b rho))
+          - a alpha rho/(1 + 2 b rho - b^2 rho^2) */
+double orc_eos_dpsi(const orc_eos *e, double rho)
+{
+    double a = e->a, b = e->b, RT = e->R * e->T;
+    switch (e->kind) {
+    case ORC_EOS_VDW:
+        return RT * log(rho / (1.0 - b * rho)) + RT / (1.0 - b * rho) - 2.0 * a * rho;
+    case ORC_EOS_PR: {
+        double s2 = sqrt(2.0), aa = a * pr_alpha(e);
+        return RT * log(rho / (1.0 - b * rho)) + RT / (1.0 - b * rho)
+               - aa / (2.0 * s2 * b) * log((1.0 + (1.0 + s2) * b * rho) / (1.0 + (1.0 - s2) * b * rho))
+               - aa * rho / (1.0 + 2.0 * b * rho - b * b * rho * rho);
+    }
+    default:
+        return cs_dpsi(a, b, e->R, e->T, rho);
+    }
+}
+
 /* p_eos = rho dPsi/drho - Psi (text before Eq. 4); C cancels. */
+double orc_eos_p(const orc_eos *e, double rho)
+{
+    return rho * orc_eos_dpsi(e, rho) - orc_eos_psi(e, rho);
+}
+
+/* upper end of the density range: the packing limit 4/b (CS) or 1/b */
+static double rho_limit(const orc_eos *e) { return (e->kind == ORC_EOS_CS ? 4.0 : 1.0) / e->b; }
+
+double orc_psi_tilde(double a, double b, double R, double T, double rho)
+{
+    orc_eos e = {ORC_EOS_CS, a, b, R, T, 0.0};
+    return orc_eos_psi(&e, rho);
+}
+double orc_dpsi_tilde(double a, double b, double R, double T, double rho)
+{
+    orc_eos e = {ORC_EOS_CS, a, b, R, T, 0.0};
+    return orc_eos_dpsi(&e, rho);
+}
 double orc_p_eos(double a, double b, double R, double T, double rho)
 {
-    return rho * orc_dpsi_tilde(a, b, R, T, rho) - orc_psi_tilde(a, b, R, T, rho);
+    orc_eos e = {ORC_EOS_CS, a, b, R, T, 0.0};
+    return orc_eos_p(&e, rho);
 }
 
 /* Locate the van der Waals loop of p_eos: the local maximum rho_s1 and the
    following local minimum rho_s2.  Returns 0 if found, -1 otherwise. */
-static int spinodals(double a, double b, double R, double T, double *s1, double *s2)
+static int spinodals(const orc_eos *e, double *s1, double *s2)
 {
     const int M = 20000;
-    double lo = log(1e-7), hi = log(0.98 * 4.0 / b);
-    double prev_p = orc_p_eos(a, b, R, T, exp(lo));
+    double lo = log(1e-7), hi = log(0.98 * rho_limit(e));
+    double prev_p = orc_eos_p(e, exp(lo));
     int state = 0; /* 0 rising, 1 falling */
     int i_max = -1, i_min = -1;
     for (int i = 1; i <= M; i++) {
         double x = lo + (hi - lo) * i / M;
-        double pv = orc_p_eos(a, b, R, T, exp(x));
+        double pv = orc_eos_p(e, exp(x));
         if (state == 0 && pv < prev_p) { state = 1; i_max = i - 1; }
         else if (state == 1 && pv > prev_p) { i_min = i - 1; break; }
         prev_p = pv;
@@ -85,7 +162,7 @@ static int spinodals(double a, double b, double R, double T, double *s1, double 
         double g = 0.5 * (sqrt(5.0) - 1.0);
         for (int it = 0; it < 200; it++) {
             double x1 = xb - g * (xb - xa), x2 = xa + g * (xb - xa);
-            double p1 = orc_p_eos(a, b, R, T, exp(x1)), p2 = orc_p_eos(a, b, R, T, exp(x2));
+            double p1 = orc_eos_p(e, exp(x1)), p2 = orc_eos_p(e, exp(x2));
             int keep_left = which == 0 ? (p1 > p2) : (p1 < p2);
             if (keep_left) xb = x2; else xa = x1;
         }
@@ -95,13 +172,12 @@ static int spinodals(double a, double b, double R, double T, double *s1, double 
 }
 
 /* root of p_eos(rho) = target on [lo, hi] where p_eos is increasing */
-static double p_root(double a, double b, double R, double T, double target,
-                     double lo, double hi)
+static double p_root(const orc_eos *e, double target, double lo, double hi)
 {
     for (int it = 0; it < 400; it++) {
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        if (orc_p_eos(a, b, R, T, mid) < target) lo = mid; else hi = mid;
+        if (orc_eos_p(e, mid) < target) lo = mid; else hi = mid;
     }
     return 0.5 * (lo + hi);
 }
@@ -110,34 +186,41 @@ static double p_root(double a, double b, double R, double T, double target,
    pressure and equal dPsi/drho.  Choosing C = -mu_coex and
    Psi_0 = Psi_eos(rho_g) = Psi_eos(rho_l) = -p_coex meets the condition stated
    after Eq. 4.  Solved by bisection on the saturation pressure. */
-int orc_coexistence(double a, double b, double R, double T, double out[4])
+int orc_eos_coexistence(const orc_eos *e, double out[4])
 {
     double s1, s2;
-    if (!(a > 0 && b > 0 && R > 0 && T > 0)) return -1;
-    if (spinodals(a, b, R, T, &s1, &s2)) return -1;
-    double rmax = 0.98 * 4.0 / b;
-    double p_hi = orc_p_eos(a, b, R, T, s1);
-    double p_lo = orc_p_eos(a, b, R, T, s2);
+    if (!(e->a > 0 && e->b > 0 && e->R > 0 && e->T > 0)) return -1;
+    if (e->kind < 0 || e->kind > 2) return -1;
+    if (spinodals(e, &s1, &s2)) return -1;
+    double rmax = 0.98 * rho_limit(e);
+    double p_hi = orc_eos_p(e, s1);
+    double p_lo = orc_eos_p(e, s2);
     if (p_lo < 0.0) p_lo = 0.0;
-    if (orc_p_eos(a, b, R, T, rmax) <= p_hi) return -1;
+    if (orc_eos_p(e, rmax) <= p_hi) return -1;
     double rg = 0, rl = 0;
     for (int it = 0; it < 400; it++) {
         double ps = 0.5 * (p_lo + p_hi);
         if (ps <= p_lo || ps >= p_hi) break;
-        rg = p_root(a, b, R, T, ps, 1e-300, s1);
-        rl = p_root(a, b, R, T, ps, s2, rmax);
-        double dmu = orc_dpsi_tilde(a, b, R, T, rl) - orc_dpsi_tilde(a, b, R, T, rg);
+        rg = p_root(e, ps, 1e-300, s1);
+        rl = p_root(e, ps, s2, rmax);
+        double dmu = orc_eos_dpsi(e, rl) - orc_eos_dpsi(e, rg);
         /* dmu > 0: the saturation pressure is too low */
         if (dmu > 0.0) p_lo = ps; else p_hi = ps;
     }
     double ps = 0.5 * (p_lo + p_hi);
-    rg = p_root(a, b, R, T, ps, 1e-300, s1);
-    rl = p_root(a, b, R, T, ps, s2, rmax);
+    rg = p_root(e, ps, 1e-300, s1);
+    rl = p_root(e, ps, s2, rmax);
     out[0] = rg;
     out[1] = rl;
-    out[2] = 0.5 * (orc_dpsi_tilde(a, b, R, T, rg) + orc_dpsi_tilde(a, b, R, T, rl));
-    out[3] = 0.5 * (orc_p_eos(a, b, R, T, rg) + orc_p_eos(a, b, R, T, rl));
+    out[2] = 0.5 * (orc_eos_dpsi(e, rg) + orc_eos_dpsi(e, rl));
+    out[3] = 0.5 * (orc_eos_p(e, rg) + orc_eos_p(e, rl));
     return 0;
+}
+
+int orc_coexistence(double a, double b, double R, double T, double out[4])
+{
+    orc_eos e = {ORC_EOS_CS, a, b, R, T, 0.0};
+    return orc_eos_coexistence(&e, out);
 }
 
 /* Critical point of the CS isotherms.  Along the spinodal dp/drho = 0; with
@@ -177,6 +260,58 @@ int orc_temperature_for_ratio(double a, double b, double R, double ratio, double
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
         if (orc_coexistence(a, b, R, mid, co)) return -1;
+        if (co[1] / co[0] > ratio) lo = mid; else hi = mid;
+    }
+    *T = 0.5 * (lo + hi);
+    return 0;
+}
+
+/* Critical point of any of the three equations of state, found without its
+   closed form: T_c is the lowest temperature at which p_eos(rho) no longer
+   has a van der Waals loop (bisection on T), rho_c the density of the
+   loop's vanishing extrema.  (CS: the maximum of the spinodal curve above.) */
+int orc_eos_critical_point(int kind, double a, double b, double R, double omega, double out[2])
+{
+    if (kind == ORC_EOS_CS) return orc_critical_point(a, b, R, out);
+    if (!(a > 0 && b > 0 && R > 0) || kind < 0 || kind > 2) return -1;
+    double hi = 2.0 * a / (b * R), lo = hi, s1, s2;
+    orc_eos e = {kind, a, b, R, hi, omega};
+    if (!spinodals(&e, &s1, &s2)) return -1;
+    /* step down until a loop appears: the bracket [lo, hi] of T_c */
+    int found = 0;
+    for (int it = 0; it < 60 && !found; it++) {
+        hi = lo;
+        lo *= 0.8;
+        e.T = lo;
+        found = !spinodals(&e, &s1, &s2);
+    }
+    if (!found) return -1;
+    for (int it = 0; it < 80; it++) {
+        e.T = 0.5 * (lo + hi);
+        if (spinodals(&e, &s1, &s2)) hi = e.T; else lo = e.T;
+    }
+    e.T = lo;
+    if (spinodals(&e, &s1, &s2)) return -1;
+    out[0] = 0.5 * (lo + hi);
+    out[1] = 0.5 * (s1 + s2);
+    return 0;
+}
+
+int orc_eos_temperature_for_ratio(int kind, double a, double b, double R, double omega, double ratio, double *T)
+{
+    if (kind == ORC_EOS_CS) return orc_temperature_for_ratio(a, b, R, ratio, T);
+    double cp[2], co[4];
+    if (!(ratio > 1.0) || orc_eos_critical_point(kind, a, b, R, omega, cp)) return -1;
+    orc_eos e = {kind, a, b, R, 0.3 * cp[0], omega};
+    double lo = 0.3 * cp[0], hi = 0.995 * cp[0];
+    if (orc_eos_coexistence(&e, co) || co[1] / co[0] < ratio) return -1;
+    e.T = hi;
+    if (orc_eos_coexistence(&e, co) || co[1] / co[0] > ratio) return -1;
+    for (int it = 0; it < 200; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        e.T = mid;
+        if (orc_eos_coexistence(&e, co)) return -1;
         if (co[1] / co[0] > ratio) lo = mid; else hi = mid;
     }
     *T = 0.5 * (lo + hi);
@@ -248,7 +383,8 @@ orc_ctx *orc_create(int lattice, int nx, int ny, int nz, const orc_params *p,
                 o->opp[i] = j;
     }
     double co[4];
-    if (orc_coexistence(p->a, p->b, p->R, p->T, co)) { free(o); return NULL; }
+    orc_eos e = {p->eos, p->a, p->b, p->R, p->T, p->omega};
+    if (orc_eos_coexistence(&e, co)) { free(o); return NULL; }
     o->rho_g = co[0]; o->rho_l = co[1]; o->mu_coex = co[2]; o->p_coex = co[3];
     /* nu = c_s^2 (tau - 1/2) with c_s^2 = 1/3; KBC uses beta = 1/(2 tau) */
     o->tau = 3.0 * p->nu + 0.5;
@@ -283,7 +419,8 @@ void orc_derived(const orc_ctx *o, double out[6])
 static double psi_shifted(const orc_ctx *o, double rho)
 {
     const orc_params *p = &o->p;
-    return orc_psi_tilde(p->a, p->b, p->R, p->T, rho) - o->mu_coex * rho + o->p_coex;
+    orc_eos e = {p->eos, p->a, p->b, p->R, p->T, p->omega};
+    return orc_eos_psi(&e, rho) - o->mu_coex * rho + o->p_coex;
 }
 
 /* C_l1 and C_l2 from (rho, phi), text before Eq. 5 */
@@ -372,11 +509,12 @@ void orc_chem_pot(const orc_ctx *o, const double *rho, const double *phi,
     orc_laplacian(o, rho, lr);
     orc_laplacian(o, phi, lp);
     double Dl = o->rho_g - o->rho_l, chi = p->chi;
+    orc_eos e = {p->eos, p->a, p->b, p->R, p->T, p->omega};
     for (long n = 0; n < N; n++) {
         double c1 = conc_l1(o, rho[n], phi[n]), c2 = conc_l2(o, rho[n], phi[n]);
         double w1 = c1 * (1.0 - c1) * (1.0 - 2.0 * c1);
         double w2 = c2 * (1.0 - c2) * (1.0 - 2.0 * c2);
-        double dpsi = orc_dpsi_tilde(p->a, p->b, p->R, p->T, rho[n]) - o->mu_coex;
+        double dpsi = orc_eos_dpsi(&e, rho[n]) - o->mu_coex;
         mu_rho[n] = 0.5 * p->lambda1 * dpsi
                     - (p->lambda2 * w1 + p->lambda3 * w2) / (2.0 * Dl)
                     - (p->kappa1 + (p->kappa2 + p->kappa3) / (4.0 * Dl * Dl)) * lr[n]

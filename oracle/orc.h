@@ -36,7 +36,24 @@ typedef struct {
     double nu;                         /* kinematic viscosity, tau = 3 nu + 1/2 */
     double Gamma, tau_g;               /* mobility M = Gamma (tau_g - 1/2)    */
     int force_form;                    /* 0 potential form, 1 lattice-consistent */
+    int eos;                           /* ORC_EOS_CS (Eq. 4), ORC_EOS_VDW, ORC_EOS_PR */
+    double omega;                      /* Peng-Robinson acentric factor          */
 } orc_params;
+
+/* Equations of state: Carnahan-Starling (Eq. 4), and the van der Waals and
+   Peng-Robinson forms the text names as alternatives (textbook forms). */
+enum { ORC_EOS_CS = 0, ORC_EOS_VDW = 1, ORC_EOS_PR = 2 };
+typedef struct {
+    int kind;
+    double a, b, R, T, omega;
+} orc_eos;
+double orc_eos_psi(const orc_eos *e, double rho);
+double orc_eos_dpsi(const orc_eos *e, double rho);
+double orc_eos_p(const orc_eos *e, double rho);
+int orc_eos_coexistence(const orc_eos *e, double out[4]);
+int orc_eos_critical_point(int kind, double a, double b, double R, double omega, double out[2]);
+int orc_eos_temperature_for_ratio(int kind, double a, double b, double R, double omega, double ratio, double *T);
+double orc_pr_tc(double a, double b, double R);
 
 typedef struct orc_ctx orc_ctx;
 
