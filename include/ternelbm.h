@@ -84,7 +84,21 @@ typedef struct {
     int precision;                    /* tel_precision */
     int force_form;                   /* tel_force_form */
     int bc[3];                        /* tel_bc per axis (bc[2] ignored for D2Q9) */
+    int eos;                          /* tel_eos: TEL_EOS_CS (Eq. 4, default 0), TEL_EOS_VDW, TEL_EOS_PR */
+    double omega;                     /* Peng-Robinson acentric factor (TEL_EOS_PR only) */
 } tel_params;
+
+/* Equations of state.  TEL_EOS_CS is Eq. 4 (Carnahan-Starling).  The text
+ * names van der Waals and Peng-Robinson as alternatives (their formulas are
+ * in the unavailable supplement); these are the textbook forms, with the free
+ * energy obtained like Eq. 4 by integrating p_eos = rho Psi' - Psi:
+ *   TEL_EOS_VDW: p = rho R T/(1 - b rho) - a rho^2
+ *   TEL_EOS_PR:  p = rho R T/(1 - b rho) - a alpha(T) rho^2/(1 + 2 b rho - b^2 rho^2),
+ *                alpha = (1 + k (1 - sqrt(T/T_c)))^2,
+ *                k = 0.37464 + 1.54226 omega - 0.26992 omega^2,
+ *                T_c = 0.07780 a/(0.45724 b R).
+ * The common tangent (C, Psi_0) is constructed the same way for all three. */
+typedef enum { TEL_EOS_CS = 0, TEL_EOS_VDW = 1, TEL_EOS_PR = 2 } tel_eos;
 
 typedef struct tel_ctx tel_ctx;
 
@@ -154,6 +168,9 @@ int tel_info(const tel_ctx *ctx, double out[10]);
  * no liquid-gas coexistence. */
 int tel_coexistence(double a, double b, double R, double T, double out[4]);
 int tel_temperature_for_ratio(double a, double b, double R, double ratio, double *T);
+/* The same two for any tel_eos (omega: Peng-Robinson acentric factor). */
+int tel_coexistence_eos(int eos, double a, double b, double R, double T, double omega, double out[4]);
+int tel_temperature_for_ratio_eos(int eos, double a, double b, double R, double omega, double ratio, double *T);
 
 /* Batched D2Q9 lattices (many uneven, independent cases advanced in one
  * persistent launch).  ncases independent D2Q9 lattices of nx[c] x ny[c]

@@ -23,6 +23,7 @@ D2Q9, D3Q27 = 0, 1
 FP64, FP32_SHIFTED = 0, 1
 PERIODIC, BOUNCEBACK = 0, 1
 FORCE_POTENTIAL, FORCE_LATTICE = 0, 1
+EOS_CS, EOS_VDW, EOS_PR = 0, 1, 2
 
 TEL_OK, TEL_EINVAL, TEL_ENOMEM, TEL_ECUDA, TEL_EUNSTABLE, TEL_ESTATE = 0, -1, -2, -3, -4, -5
 _NAMES = {-1: "TEL_EINVAL", -2: "TEL_ENOMEM", -3: "TEL_ECUDA", -4: "TEL_EUNSTABLE", -5: "TEL_ESTATE"}
@@ -42,14 +43,16 @@ class Params(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "a", "b", "R", "T", "lambda1", "lambda2", "lambda3", "kappa1", "kappa2",
         "kappa3", "chi", "nu", "Gamma", "tau_g", "rho_ref")] + [
-        ("precision", C.c_int), ("force_form", C.c_int), ("bc", C.c_int * 3)]
+        ("precision", C.c_int), ("force_form", C.c_int), ("bc", C.c_int * 3), ("eos", C.c_int),
+        ("omega", C.c_double)]
 
 
 _lib = None
 SYMBOLS = ("tel_create", "tel_destroy", "tel_last_error", "tel_set_stream", "tel_init",
            "tel_init_device", "tel_step", "tel_sync", "tel_fields", "tel_fields_device",
            "tel_get_state", "tel_set_state", "tel_info", "tel_coexistence",
-           "tel_temperature_for_ratio", "tel_fields_noalloc", "tel_batch_create",
+           "tel_temperature_for_ratio", "tel_coexistence_eos", "tel_temperature_for_ratio_eos",
+           "tel_fields_noalloc", "tel_batch_create",
            "tel_batch_destroy", "tel_batch_last_error", "tel_batch_set_stream", "tel_batch_init", "tel_batch_step",
            "tel_batch_sync", "tel_batch_fields", "tel_batch_fields_device", "tel_batch_errors",
            "tel_batch_tune", "tel_batch_info")
@@ -85,6 +88,8 @@ def lib(build: bool = True):
     L.tel_info.argtypes = [vp, dp]
     L.tel_coexistence.argtypes = [d, d, d, d, dp]
     L.tel_temperature_for_ratio.argtypes = [d, d, d, d, dp]
+    L.tel_coexistence_eos.argtypes = [i, d, d, d, d, d, dp]
+    L.tel_temperature_for_ratio_eos.argtypes = [i, d, d, d, d, d, dp]
     L.tel_fields_noalloc.argtypes = [i, i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
     L.tel_batch_create.argtypes = [i, vp, vp, vp, C.POINTER(vp)]
     L.tel_batch_destroy.argtypes = [vp]
@@ -111,17 +116,19 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
-def coexistence(a, b, R, T):
+def coexistence(a, b, R, T, eos=0, omega=0.0):
+    """(rho_g, rho_l, mu_coex, p_coex) of the common tangent; eos: EOS_CS
+    (Eq. 4), EOS_VDW or EOS_PR (omega: acentric factor)."""
     out = (C.c_double * 4)()
-    rc = lib().tel_coexistence(a, b, R, T, out)
+    rc = lib().tel_coexistence_eos(int(eos), a, b, R, T, float(omega), out)
     if rc:
         raise TelError(rc, f"no liquid-gas coexistence at T={T}")
     return tuple(out)
 
 
-def temperature_for_ratio(a, b, R, ratio):
+def temperature_for_ratio(a, b, R, ratio, eos=0, omega=0.0):
     T = C.c_double()
-    rc = lib().tel_temperature_for_ratio(a, b, R, ratio, C.byref(T))
+    rc = lib().tel_temperature_for_ratio_eos(int(eos), a, b, R, float(omega), ratio, C.byref(T))
     if rc:
         raise TelError(rc, f"no temperature with density ratio {ratio}")
     return T.value
@@ -141,6 +148,8 @@ def _params_struct(p):
     bcs = tuple(p.get("bc", (0, 0, 0)))
     for k in range(3):
         s.bc[k] = int(bcs[k])
+    s.eos = int(p.get("eos", EOS_CS))
+    s.omega = float(p.get("omega", 0.0))
     return s
 
 
@@ -280,16 +289,7 @@ class Lattice:
             p["precision"] = precision
         if force_form is not None:
             p["force_form"] = force_form
-        s = Params()
-        for k in ("a", "b", "R", "T", "lambda1", "lambda2", "lambda3", "kappa1", "kappa2",
-                  "kappa3", "chi", "nu", "Gamma", "tau_g"):
-            setattr(s, k, float(p[k]))
-        s.rho_ref = float(p.get("rho_ref", 0.0))
-        s.precision = int(p.get("precision", FP64))
-        s.force_form = int(p.get("force_form", FORCE_LATTICE))
-        bcs = tuple(p.get("bc", (0, 0, 0)))
-        for k in range(3):
-            s.bc[k] = int(bcs[k])
+        s = _params_struct(p)
         self._L = lib()
         h = C.c_void_p()
         rc = self._L.tel_create(int(lattice), int(nx), int(ny), int(nz), C.byref(s), C.byref(h))

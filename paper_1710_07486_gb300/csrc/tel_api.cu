@@ -59,29 +59,64 @@ static int fail(tel_ctx *c, int code, const char *fmt, ...)
 // the spinodals, where dp/drho = 0), then Newton polishing of the 2x2 system.
 // ---------------------------------------------------------------------------
 namespace {
+// The equation of state's pressure p, dPsi~/drho (m) and d2Psi~/drho2 (dm,
+// with dp/drho = rho dm).  CS is Eq. 4; VDW and PR are the textbook forms
+// (see tel_eos).
 struct CS {
-    double a, b, R, T;
+    int kind;
+    double a, b, R, T, omega;
+    double aal, A, c1, c2;  // PR: a alpha(T), a alpha/(2 sqrt2 b), (1 +- sqrt2) b
+    CS(double a_, double b_, double R_, double T_, int kind_ = TEL_EOS_CS, double omega_ = 0.0)
+        : kind(kind_), a(a_), b(b_), R(R_), T(T_), omega(omega_)
+    {
+        const double s2 = std::sqrt(2.0);
+        double alpha = 1.0;
+        if (kind == TEL_EOS_PR) {
+            const double k = 0.37464 + 1.54226 * omega - 0.26992 * omega * omega;
+            const double q = 1.0 + k * (1.0 - std::sqrt(T / (0.07780 * a / (0.45724 * b * R))));
+            alpha = q * q;
+        }
+        aal = a * alpha;
+        A = aal / (2.0 * s2 * b);
+        c1 = (1.0 + s2) * b;
+        c2 = (1.0 - s2) * b;
+    }
+    double limit() const { return (kind == TEL_EOS_CS ? 4.0 : 1.0) / b; }
     double p(double r) const
     {
+        if (kind == TEL_EOS_VDW) return r * R * T / (1.0 - b * r) - a * r * r;
+        if (kind == TEL_EOS_PR) return r * R * T / (1.0 - b * r) - aal * r * r / (1.0 + 2.0 * b * r - b * b * r * r);
         const double e = 0.25 * b * r;
         return r * R * T * (1 + e + e * e - e * e * e) / ((1 - e) * (1 - e) * (1 - e)) - a * r * r;
     }
     double m(double r) const  // dPsi~/drho
     {
+        if (kind != TEL_EOS_CS) {
+            double v = R * T * (std::log(r / (1.0 - b * r)) + 1.0 / (1.0 - b * r));
+            if (kind == TEL_EOS_VDW) return v - 2.0 * a * r;
+            return v - A * std::log((1.0 + c1 * r) / (1.0 + c2 * r)) - aal * r / (1.0 + 2.0 * b * r - b * b * r * r);
+        }
         const double d = b * r - 4.0;
         return -2.0 * a * r - 8.0 * R * T * (24.0 - 2.0 * b * r) / (d * d * d) + R * T * (std::log(r) + 1.0);
     }
-    double dm(double r) const  // d2Psi~/drho2 (dp/drho = rho dm)
+    double dm(double r) const  // d2Psi~/drho2
     {
+        if (kind != TEL_EOS_CS) {
+            const double q = 1.0 - b * r;
+            double v = R * T * (1.0 / r + b / q + b / (q * q));
+            if (kind == TEL_EOS_VDW) return v - 2.0 * a;
+            const double D = 1.0 + 2.0 * b * r - b * b * r * r;
+            return v - 2.0 * aal / D + aal * r * (2.0 * b - 2.0 * b * b * r) / (D * D);
+        }
         const double d = b * r - 4.0;
         return -2.0 * a - 32.0 * R * T * b * (b * r - 16.0) / (d * d * d * d) + R * T / r;
     }
 };
 
-// spinodals: the two roots of dm = 0 on (0, 4/b); returns false above T_c
+// spinodals: the two roots of dm = 0 below the density limit; false above T_c
 bool spinodals(const CS &s, double &s1, double &s2)
 {
-    const double hi = 0.999 * 4.0 / s.b;
+    const double hi = 0.999 * s.limit();
     const int M = 4000;
     double prev = s.dm(1e-6 / s.b), x_prev = 1e-6 / s.b;
     int found = 0;
@@ -122,7 +157,7 @@ bool coexist(const CS &s, double out[4])
     double s1, s2;
     if (!(s.a > 0 && s.b > 0 && s.R > 0 && s.T > 0)) return false;
     if (!spinodals(s, s1, s2)) return false;
-    const double rmax = 0.999 * 4.0 / s.b;
+    const double rmax = 0.999 * s.limit();
     // chemical potentials spanned by both branches
     double mlo = s.m(s2), mhi = s.m(s1);
     if (!(mhi > mlo)) return false;
@@ -158,25 +193,33 @@ bool coexist(const CS &s, double out[4])
 }
 }  // namespace
 
-extern "C" int tel_coexistence(double a, double b, double R, double T, double out[4])
+extern "C" int tel_coexistence_eos(int eos, double a, double b, double R, double T, double omega, double out[4])
 {
-    if (!out) return TEL_EINVAL;
-    CS s{a, b, R, T};
+    if (!out || eos < TEL_EOS_CS || eos > TEL_EOS_PR) return TEL_EINVAL;
+    if (!(a > 0 && b > 0 && R > 0 && T > 0)) return TEL_EINVAL;
+    CS s(a, b, R, T, eos, omega);
     return coexist(s, out) ? TEL_OK : TEL_EINVAL;
 }
 
-extern "C" int tel_temperature_for_ratio(double a, double b, double R, double ratio, double *T)
+extern "C" int tel_coexistence(double a, double b, double R, double T, double out[4])
 {
-    if (!T || !(ratio > 1.0) || !(a > 0 && b > 0 && R > 0)) return TEL_EINVAL;
+    return tel_coexistence_eos(TEL_EOS_CS, a, b, R, T, 0.0, out);
+}
+
+extern "C" int tel_temperature_for_ratio_eos(int eos, double a, double b, double R, double omega, double ratio,
+                                             double *T)
+{
+    if (!T || !(ratio > 1.0) || !(a > 0 && b > 0 && R > 0) || eos < TEL_EOS_CS || eos > TEL_EOS_PR)
+        return TEL_EINVAL;
     // bracket: a low temperature with a larger ratio, and one near T_c
     double lo = 0.02 * a / (b * R), hi = lo, out[4];
     {
-        CS s{a, b, R, lo};
+        CS s(a, b, R, lo, eos, omega);
         if (!coexist(s, out) || out[1] / out[0] < ratio) return TEL_EINVAL;
     }
     // walk up until coexistence disappears or the ratio falls below target
     for (double t = lo; t < 1.0 * a / (b * R); t *= 1.01) {
-        CS s{a, b, R, t};
+        CS s(a, b, R, t, eos, omega);
         if (!coexist(s, out) || out[1] / out[0] < ratio) { hi = t; break; }
         lo = t;
     }
@@ -184,11 +227,16 @@ extern "C" int tel_temperature_for_ratio(double a, double b, double R, double ra
     for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        CS s{a, b, R, mid};
+        CS s(a, b, R, mid, eos, omega);
         if (coexist(s, out) && out[1] / out[0] > ratio) lo = mid; else hi = mid;
     }
     *T = 0.5 * (lo + hi);
     return TEL_OK;
+}
+
+extern "C" int tel_temperature_for_ratio(double a, double b, double R, double ratio, double *T)
+{
+    return tel_temperature_for_ratio_eos(TEL_EOS_CS, a, b, R, 0.0, ratio, T);
 }
 
 // ---------------------------------------------------------------------------
@@ -204,6 +252,7 @@ static void fill_coef(const tel::DevParams &d, tel::Coef<T> &k)
     k.Kr = (T)d.Kr; k.Kp = (T)d.Kp; k.Kx = (T)d.Kx;
     k.rho_switch = (T)d.rho_switch; k.rho_ref = (T)d.rho_ref;
     k.beta = (T)d.beta; k.Gamma3 = (T)(3.0 * d.Gamma); k.inv_tau_g = (T)d.inv_tau_g;
+    k.aal = (T)d.aal; k.prA = (T)d.prA; k.c1 = (T)d.c1; k.c2 = (T)d.c2;
 }
 
 static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
@@ -220,6 +269,7 @@ static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
     if (!(p->kappa1 >= 0 && p->kappa2 >= 0 && p->kappa3 >= 0)) return fail(nullptr, TEL_EINVAL, "kappa must be >= 0");
     if (!(p->lambda1 >= 0 && p->lambda2 >= 0 && p->lambda3 >= 0)) return fail(nullptr, TEL_EINVAL, "lambda must be >= 0");
     if (p->precision != TEL_FP64 && p->precision != TEL_FP32_SHIFTED) return fail(nullptr, TEL_EINVAL, "bad precision");
+    if (p->eos != TEL_EOS_CS && p->eos != TEL_EOS_VDW && p->eos != TEL_EOS_PR) return fail(nullptr, TEL_EINVAL, "bad eos");
     if (p->force_form != TEL_FORCE_POTENTIAL && p->force_form != TEL_FORCE_LATTICE) return fail(nullptr, TEL_EINVAL, "bad force_form");
     for (int a = 0; a < 3; ++a)
         if (p->bc[a] != TEL_PERIODIC && p->bc[a] != TEL_BOUNCEBACK) return fail(nullptr, TEL_EINVAL, "bad bc[%d]", a);
@@ -251,7 +301,12 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
         if (v >= 1) d.chunk = v;
     }
     d.force_form = p.force_form;
+    d.eos = p.eos;
     d.a = p.a; d.b = p.b; d.RT = p.R * p.T;
+    {
+        const CS s(p.a, p.b, p.R, p.T, p.eos, p.omega);
+        d.aal = s.aal; d.prA = s.A; d.c1 = s.c1; d.c2 = s.c2;
+    }
     d.rho_g = co[0]; d.rho_l = co[1]; d.mu_coex = co[2]; d.p_coex = co[3];
     const double Dl = co[0] - co[1];
     d.lam1h = 0.5 * p.lambda1; d.lam2 = p.lambda2; d.lam3 = p.lambda3;
@@ -289,7 +344,7 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     int rc = validate(lattice, nx, ny, nz, params);
     if (rc) return rc;
     double co[4];
-    if (tel_coexistence(params->a, params->b, params->R, params->T, co) != TEL_OK)
+    if (tel_coexistence_eos(params->eos, params->a, params->b, params->R, params->T, params->omega, co) != TEL_OK)
         return fail(nullptr, TEL_EINVAL, "no liquid-gas coexistence at T=%g (T must be below the critical temperature)",
                     params->T);
     tel_ctx *c = new (std::nothrow) tel_ctx();
@@ -575,7 +630,7 @@ extern "C" int tel_fields_noalloc(int lattice, int nx, int ny, int nz, const tel
                             N, TEL_NOALLOC_MAX_NODES);
     if (!f_state || !g_state) return noalloc_fail(TEL_EINVAL, "tel_fields_noalloc: NULL state buffer");
     double co[4];
-    if (tel_coexistence(params->a, params->b, params->R, params->T, co) != TEL_OK)
+    if (tel_coexistence_eos(params->eos, params->a, params->b, params->R, params->T, params->omega, co) != TEL_OK)
         return noalloc_fail(TEL_EINVAL, "no liquid-gas coexistence at T=%g", params->T);
     tel_params pp = *params;
     if (lattice == TEL_D2Q9) pp.bc[2] = TEL_PERIODIC;
@@ -774,7 +829,8 @@ extern "C" int tel_batch_create(int ncases, const int *nx, const int *ny, const 
         b->ny[c] = ny[c];
         b->off[c] = o;
         double co[4];
-        if (tel_coexistence(params[c].a, params[c].b, params[c].R, params[c].T, co) != TEL_OK) {
+        if (tel_coexistence_eos(params[c].eos, params[c].a, params[c].b, params[c].R, params[c].T, params[c].omega,
+                                co) != TEL_OK) {
             delete[] hA[0]; delete[] hA[1]; tel_batch_destroy(b);
             return bfail(nullptr, TEL_EINVAL, "case %d: no liquid-gas coexistence at T=%g", c, params[c].T);
         }

@@ -29,6 +29,10 @@ namespace tel {
 
 enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_FIELDS = 2 };
 
+// Equations of state (values of tel_eos): Carnahan-Starling (Eq. 4), and the
+// textbook van der Waals and Peng-Robinson forms named as alternatives.
+enum Eos : int { EOS_CS = 0, EOS_VDW = 1, EOS_PR = 2 };
+
 // Error bits raised by the device (see TEL_EUNSTABLE).
 enum : unsigned { ERR_RHO = 1u, ERR_VEL = 2u, ERR_NAN = 4u };
 
@@ -41,6 +45,7 @@ struct Coef {
     T Kr, Kp, Kx;
     T rho_switch, rho_ref;
     T beta, Gamma3, inv_tau_g;         // Gamma3 = 3 Gamma
+    T aal, prA, c1, c2;                // PR: a alpha(T), a alpha/(2 sqrt2 b), (1 +- sqrt2) b
 };
 
 struct DevParams {
@@ -49,8 +54,11 @@ struct DevParams {
     long long N;             // nodes
     int chunk;               // planes per CTA along the marching axis
     int force_form;          // 0 potential, 1 lattice-consistent
-    // Carnahan-Starling free energy, Eq. 4, shifted by the common tangent
+    int eos;                 // Eos
+    // equation-of-state free energy (Eq. 4 or an alternative), shifted by the
+    // common tangent
     double a, b, RT, mu_coex, p_coex;
+    double aal, prA, c1, c2;          // Peng-Robinson constants at T (see Coef)
     double lam1h, lam2, lam3;         // lambda1/2, lambda2, lambda3
     double rho_g, rho_l;
     double inv_Dl;                    // 1/(rho_g - rho_l)
@@ -168,6 +176,19 @@ template <typename T>
 __device__ __forceinline__ T mu_eos(const DevParams &P, T rho)
 {
     const Coef<T> &K = coef<T>(P);
+    if (P.eos != EOS_CS) {
+        // dPsi~/drho = RT (ln(rho/(1 - b rho)) + 1/(1 - b rho)) - 2 a rho            (vdW)
+        //            ... - a alpha/(2 sqrt2 b) ln((1 + c1 rho)/(1 + c2 rho))
+        //                - a alpha rho/(1 + 2 b rho - b^2 rho^2)                     (PR)
+        const T q = (T)1 - K.b * rho;
+        T dpsi = K.RT * (log_<T>(rho / q) + (T)1 / q);
+        if (P.eos == EOS_VDW)
+            dpsi += K.a2 * rho;
+        else
+            dpsi -= K.prA * log_<T>(((T)1 + K.c1 * rho) / ((T)1 + K.c2 * rho))
+                    + K.aal * rho / ((T)1 + (T)2 * K.b * rho - K.b * K.b * rho * rho);
+        return K.lam1h * (dpsi - K.mu_coex);
+    }
     const T br = K.b * rho;
     const T d = br - (T)4;
     const T dpsi = K.a2 * rho - K.RT8 * ((T)24 - (T)2 * br) / (d * d * d) + K.RT * (log_<T>(rho) + (T)1)
@@ -217,9 +238,18 @@ __device__ __forceinline__ float mu_eos_gas(const DevParams &P, float rho)
 // Bulk free energy f_B of Eq. 2 (Psi_eos - Psi_0 with the common tangent).
 __device__ __forceinline__ double f_bulk(const DevParams &P, double rho, double phi)
 {
-    const double br = P.b * rho, d = br - 4.0;
-    const double psi = rho * (-P.a * rho - 8.0 * P.RT * (br - 6.0) / (d * d) + P.RT * log(rho))
-                       - P.mu_coex * rho + P.p_coex;
+    double psi;
+    if (P.eos == EOS_CS) {
+        const double br = P.b * rho, d = br - 4.0;
+        psi = rho * (-P.a * rho - 8.0 * P.RT * (br - 6.0) / (d * d) + P.RT * log(rho));
+    } else {
+        psi = rho * P.RT * log(rho / (1.0 - P.b * rho));
+        if (P.eos == EOS_VDW)
+            psi -= P.a * rho * rho;
+        else
+            psi -= P.prA * rho * log((1.0 + P.c1 * rho) / (1.0 + P.c2 * rho));
+    }
+    psi += -P.mu_coex * rho + P.p_coex;
     const double s = (rho - P.rho_l) * P.inv_Dl, pc = phi * P.inv_chi;
     const double c1 = 0.5 * (1.0 + pc - s), c2 = 0.5 * (1.0 - pc - s);
     return P.lam1h * psi + 0.5 * P.lam2 * c1 * c1 * (1 - c1) * (1 - c1)
@@ -432,8 +462,8 @@ struct Fused {
                     const CT lp = (CT)6 * lap.y;
                     CT mr, mp;
                     mu_wells<CT>(P, r0, p0, mr, mp);
-                    if (StoreTraits<ST>::shifted && r0 < coef<CT>(P).rho_switch)
-                        mr = (CT)mu_eos_gas(P, (float)r0) + mr;  // FP64 gas side
+                    if (StoreTraits<ST>::shifted && r0 < coef<CT>(P).rho_switch)  // FP64 gas side
+                        mr = (P.eos == EOS_CS ? (CT)mu_eos_gas(P, (float)r0) : (CT)mu_eos<double>(P, (double)r0)) + mr;
                     else
                         mr = mu_eos<CT>(P, r0) + mr;
                     mu_s[sB * NB + s] = V::pair(mr - coef<CT>(P).Kr * lr - coef<CT>(P).Kx * lp,

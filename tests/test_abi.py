@@ -94,3 +94,20 @@ def test_batch_create_validates_on_the_host():
         tel.Batch([(16, 16), (16, 16)], [p])
     L = tel.lib()
     assert L.tel_batch_create(0, None, None, None, C.byref(C.c_void_p())) == tel.TEL_EINVAL
+
+
+@pytest.mark.parametrize("eos,a,b,omega", [(1, 9.0 / 49.0, 2.0 / 21.0, 0.0), (2, 2.0 / 49.0, 2.0 / 21.0, 0.344)])
+@pytest.mark.parametrize("ratio", [10.0, 100.0, 1000.0])
+def test_library_coexistence_matches_oracle_other_eos(orc, eos, a, b, omega, ratio):
+    """The library's host solver (bisection on mu + Newton) against the
+    oracle's (bisection on the saturation pressure) for the van der Waals and
+    Peng-Robinson equations of state."""
+    T = tel.temperature_for_ratio(a, b, RGAS, ratio, eos=eos, omega=omega)
+    To = orc.eos_temperature_for_ratio(eos, a, b, RGAS, ratio, omega)
+    assert T == pytest.approx(To, rel=1e-10)
+    got = tel.coexistence(a, b, RGAS, To, eos=eos, omega=omega)
+    ref = orc.eos_coexistence(eos, a, b, RGAS, To, omega)
+    assert got[0] == pytest.approx(ref[0], rel=1e-11)
+    assert got[1] == pytest.approx(ref[1], rel=1e-11)
+    assert got[2] == pytest.approx(ref[2], rel=1e-10, abs=1e-13)
+    assert got[3] == pytest.approx(ref[3], rel=1e-9)
