@@ -35,6 +35,13 @@ extern "C" {
 int tel_sur_conv3x3(const void *x, const void *w, const float *bias, void *y, int B, int H, int W, int cin,
                     int cout, int relu, void *stream);
 
+/* The same convolution on the 5th-generation tensor cores (tcgen05.mma,
+ * accumulator in tensor memory); err (device, may be NULL) is OR-ed with 1
+ * if a bounded wait for the tensor cores timed out, in which case y is not
+ * written. */
+int tel_sur_conv3x3_tc(const void *x, const void *w, const float *bias, void *y, int B, int H, int W, int cin,
+                       int cout, int relu, unsigned *err, void *stream);
+
 /* Weights for the input gradient: the input gradient of a conv is the conv
  * of its output gradient with w_t[s][i][o] = w[8-s][o][i].  Writes w_t
  * (bf16 [9][Cin][Cout]) from w (bf16 [9][Cout][Cin]). */

@@ -244,6 +244,223 @@ int conv_dispatch_k(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, lo
 }
 
 // ---------------------------------------------------------------------------
+// Forward conv on the 5th-generation tensor cores: tcgen05.mma (kind::f16,
+// BF16 operands, FP32 accumulator in tensor memory), one 128-pixel x COUT
+// tile per CTA of 4 warps.  Operand tiles are staged in shared memory by
+// cp.async in the canonical no-swizzle K-major layout: core matrices of 8
+// rows x 16 bytes, the K-adjacent core matrices 128 B apart (leading byte
+// offset), the 8-row groups BK*16 B apart (stride byte offset).  One thread
+// issues the MMAs of a stage and commits them to an mbarrier; the stage's
+// buffer is refilled only after that mbarrier completes.  Every wait is
+// bounded: on time-out the kernel records an error and skips its output.
+// ---------------------------------------------------------------------------
+constexpr int TC_THREADS = 128;
+constexpr long long TC_SPIN = 1LL << 26;  // bounded mbarrier wait (iterations)
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version (tcgen05)
+    // base offset 0, relative LBO, swizzle mode 0 (none)
+    return d;
+}
+
+// kind::f16 instruction descriptor: F32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// returns false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < TC_SPIN; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity));
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int COUT, int BK>
+struct TcCfg {
+    static constexpr int BM = 128;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = COUT * BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;  // power of two >= 32
+    // enough shared memory that at most 512 / TMEM_COLS CTAs are resident on
+    // an SM (228 KB each), so that their tensor-memory allocations never wait
+    static constexpr size_t SMEM_OPS = 1024 + 2 * (size_t)STAGE;
+    static constexpr size_t SMEM_TMEM = (size_t)233472 * TMEM_COLS / 512 + 1024;
+    static constexpr size_t SMEM = SMEM_OPS > SMEM_TMEM ? SMEM_OPS : SMEM_TMEM;
+    static constexpr uint32_t IDESC = umma_idesc_bf16(BM, COUT);
+};
+
+template <int COUT, int BK>
+__global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
+                                                                const float *__restrict__ bias, bf16 *__restrict__ y,
+                                                                int H, int W, int CIN, int relu, unsigned *err)
+{
+    typedef TcCfg<COUT, BK> C;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long m0 = (long long)blockIdx.x * C::BM;
+    const int kchunks = CIN / BK;
+    const int stages = TAPS * kchunks;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                     "r"(C::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = tmem_base;
+
+    // this thread's pixel (row m = tid of the tile) for the A loads
+    const long long p = m0 + tid;
+    const int pw = (int)(p % W), ph = (int)((p / W) % H), pb = (int)(p / ((long long)W * H));
+
+    auto load_stage = [&](int s, int buf) {
+        const int t = s / kchunks, kc = s % kchunks;
+        unsigned char *a = base + buf * C::STAGE;
+        unsigned char *b = a + C::A_BYTES;
+        int hs = ph + tap_dy(t), ws = pw + tap_dx(t);
+        hs = hs < 0 ? hs + H : (hs >= H ? hs - H : hs);
+        ws = ws < 0 ? ws + W : (ws >= W ? ws - W : ws);
+        const bf16 *src = x + ((((long long)pb * H + hs) * W + ws) * CIN + kc * BK);
+        // A: row m = tid, k-groups q = 0..BK/8-1
+#pragma unroll
+        for (int q = 0; q < BK / 8; ++q)
+            cp_async16(a + ((tid >> 3) * (BK / 8) + q) * 128 + (tid & 7) * 16, src + q * 8);
+        // B: COUT rows x BK/8 k-groups
+        for (int c = tid; c < COUT * (BK / 8); c += TC_THREADS) {
+            const int n = c / (BK / 8), q = c % (BK / 8);
+            cp_async16(b + ((n >> 3) * (BK / 8) + q) * 128 + (n & 7) * 16,
+                       w + (((long long)t * COUT + n) * CIN + kc * BK + q * 8));
+        }
+    };
+
+    bool ok = true;
+    load_stage(0, 0);
+    cp_commit();
+    for (int s = 0; s < stages; ++s) {
+        if (s >= 1) {
+            // MMA(s-1) done: its buffer is free (the decision is made uniform)
+            ok = __syncthreads_and(mbar_wait(&mbar[(s - 1) & 1], ((s - 1) >> 1) & 1) ? 1 : 0) != 0;
+            if (!ok) break;
+        }
+        if (s + 1 < stages) {
+            load_stage(s + 1, (s + 1) & 1);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);  // cp.async data visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t a0 = smem_u32(base + (s & 1) * C::STAGE);
+            const uint32_t b0 = a0 + C::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t da = umma_desc(a0 + kk * 256, 128, BK * 16);
+                const uint64_t db = umma_desc(b0 + kk * 256, 128, BK * 16);
+                const uint32_t acc = (s > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(C::IDESC), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&mbar[s & 1])));
+        }
+    }
+    if (ok) ok = __syncthreads_and(mbar_wait(&mbar[(stages - 1) & 1], ((stages - 1) >> 1) & 1) ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+    if (ok) {
+        // epilogue: row m = tid lives in TMEM lane tid (warp w owns lanes 32w..32w+31)
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int n0 = 0; n0 < COUT; n0 += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(lane_addr + n0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+            __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[n0 + 2 * j] : 0.f);
+                float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[n0 + 2 * j + 1] : 0.f);
+                if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                o[j] = __floats2bfloat162_rn(v0, v1);
+            }
+            *reinterpret_cast<uint4 *>(y + p * COUT + n0) = *reinterpret_cast<const uint4 *>(o);
+        }
+    } else if (tid == 0 && err) {
+        atomicOr(err, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::TMEM_COLS));
+}
+
+template <int COUT, int BK>
+int launch_conv_tc(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, long long P, int H, int W, int cin,
+                   int relu, unsigned *err, cudaStream_t s)
+{
+    typedef TcCfg<COUT, BK> C;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(conv3x3_tc_kernel<COUT, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::SMEM) != cudaSuccess)
+            return TEL_ECUDA;
+        attr = true;
+    }
+    conv3x3_tc_kernel<COUT, BK><<<(unsigned)(P / C::BM), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu, err);
+    return launched();
+}
+
+template <int COUT>
+int conv_tc_dispatch_k(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, long long P, int H, int W, int cin,
+                       int relu, unsigned *err, cudaStream_t s)
+{
+    switch (cin) {
+    case 16: return launch_conv_tc<COUT, 16>(x, w, bias, y, P, H, W, cin, relu, err, s);
+    case 32: return launch_conv_tc<COUT, 32>(x, w, bias, y, P, H, W, cin, relu, err, s);
+    default: return launch_conv_tc<COUT, 64>(x, w, bias, y, P, H, W, cin, relu, err, s);  // 64, 128
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient: per CTA one tap, a (Cout tile BMO) x (Cin tile BNI)
 // block, and a chunk of pixels; each of 4 warps takes 16 of the 64 pixels of
 // a stage (its own k16 slice), then the warps' partial sums are added in
@@ -920,4 +1137,19 @@ extern "C" int tel_sur_sums(const float *f32, double *sums, int B, int H, int W,
     if (cudaMemsetAsync(sums, 0, sizeof(double) * 2 * B, S(stream)) != cudaSuccess) return TEL_ECUDA;
     sums_kernel<<<dim3(blocks_per_sample(N, B), B), 256, 0, S(stream)>>>(f32, sums, N);
     return launched();
+}
+
+extern "C" int tel_sur_conv3x3_tc(const void *x, const void *w, const float *bias, void *y, int B, int H, int W,
+                                  int cin, int cout, int relu, unsigned *err, void *stream)
+{
+    const long long P = (long long)B * H * W;
+    if (!x || !w || !y || B < 1 || H < 1 || W < 1 || !chan_ok(cin) || !chan_ok(cout) || P % 128) return TEL_EINVAL;
+    const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
+    bf16 *yb = (bf16 *)y;
+    switch (cout) {
+    case 16: return conv_tc_dispatch_k<16>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    case 32: return conv_tc_dispatch_k<32>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    case 64: return conv_tc_dispatch_k<64>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    default: return conv_tc_dispatch_k<128>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    }
 }

@@ -26,7 +26,7 @@ from . import Batch, TelError, lib
 CIN, COUT, NF = 16, 16, 4
 U_REF = 0.1  # velocity normalisation (lattice units)
 
-SUR_SYMBOLS = ("tel_sur_conv3x3", "tel_sur_flip_weights", "tel_sur_relu_bwd", "tel_sur_conv3x3_wgrad",
+SUR_SYMBOLS = ("tel_sur_conv3x3", "tel_sur_conv3x3_tc", "tel_sur_flip_weights", "tel_sur_relu_bwd", "tel_sur_conv3x3_wgrad",
                "tel_sur_pool2", "tel_sur_pool2_bwd", "tel_sur_up2", "tel_sur_up2_bwd", "tel_sur_add",
                "tel_sur_pack", "tel_sur_unpack", "tel_sur_gather", "tel_sur_loss", "tel_sur_advance",
                "tel_sur_errors", "tel_sur_sums", "tel_sur_adam", "tel_sur_zero", "tel_sur_to_bf16")
@@ -38,6 +38,7 @@ def sur_lib():
         return L
     vp, i, ll, f = C.c_void_p, C.c_int, C.c_longlong, C.c_float
     L.tel_sur_conv3x3.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp]
+    L.tel_sur_conv3x3_tc.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp, vp]
     L.tel_sur_flip_weights.argtypes = [vp, vp, i, i, vp]
     L.tel_sur_relu_bwd.argtypes = [vp, vp, vp, ll, vp]
     L.tel_sur_conv3x3_wgrad.argtypes = [vp, vp, vp, vp, i, i, i, i, i, vp]
