@@ -295,35 +295,43 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
     return false;
 }
 
-template <int COUT, int BK>
+template <int COUT>
 struct TcCfg {
     static constexpr int BM = 128;
-    static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = COUT * BK * 2;
+    static constexpr int NS = COUT == 128 ? 3 : 4;  // pipeline stages (two CTAs per SM at COUT 128)
+    static constexpr int KS = 4;                 // k-steps of 16 per stage (K = 64)
+    static constexpr int A_BYTES = BM * KS * 32;
+    static constexpr int B_BYTES = COUT * KS * 32;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;  // power of two >= 32
     // enough shared memory that at most 512 / TMEM_COLS CTAs are resident on
     // an SM (228 KB each), so that their tensor-memory allocations never wait
-    static constexpr size_t SMEM_OPS = 1024 + 2 * (size_t)STAGE;
+    static constexpr size_t SMEM_OPS = 1024 + NS * (size_t)STAGE;
     static constexpr size_t SMEM_TMEM = (size_t)233472 * TMEM_COLS / 512 + 1024;
     static constexpr size_t SMEM = SMEM_OPS > SMEM_TMEM ? SMEM_OPS : SMEM_TMEM;
     static constexpr uint32_t IDESC = umma_idesc_bf16(BM, COUT);
 };
 
-template <int COUT, int BK>
+// K runs over (tap, 16-channel group) pairs: k-step j reads tap j / (CIN/16)
+// and channels 16 (j % (CIN/16)) .. +15.  A stage holds KS consecutive
+// k-steps (the last one possibly fewer); in shared memory k-step kk of a
+// stage occupies k-groups 2kk, 2kk+1 of the core-matrix layout.
+template <int COUT>
 __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
                                                                 const float *__restrict__ bias, bf16 *__restrict__ y,
                                                                 int H, int W, int CIN, int relu, unsigned *err)
 {
-    typedef TcCfg<COUT, BK> C;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    __shared__ uint64_t mbar[2];
+    typedef TcCfg<COUT> C;
+    constexpr int NS = C::NS, KS = C::KS, KG = 2 * KS;  // k-groups (16 B) per stage row
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);  // 1024-byte aligned
+    __shared__ uint64_t mbar[NS];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
     const long long m0 = (long long)blockIdx.x * C::BM;
-    const int kchunks = CIN / BK;
-    const int stages = TAPS * kchunks;
+    const int cg = CIN / 16;               // 16-channel groups per tap
+    const int ksteps = TAPS * cg;          // total k-steps
+    const int stages = (ksteps + KS - 1) / KS;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
@@ -331,8 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const bf16 *__re
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
     }
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int b = 0; b < NS; ++b) mbar_init(&mbar[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -340,56 +347,53 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const bf16 *__re
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     const uint32_t tmem = tmem_base;
 
-    // this thread's pixel (row m = tid of the tile) for the A loads
-    const long long p = m0 + tid;
+    const long long p = m0 + tid;  // this thread's pixel: row tid of the A tile
     const int pw = (int)(p % W), ph = (int)((p / W) % H), pb = (int)(p / ((long long)W * H));
 
-    auto load_stage = [&](int s, int buf) {
-        const int t = s / kchunks, kc = s % kchunks;
-        unsigned char *a = base + buf * C::STAGE;
+    auto load_stage = [&](int st) {
+        unsigned char *a = base + (st % NS) * C::STAGE;
         unsigned char *b = a + C::A_BYTES;
-        int hs = ph + tap_dy(t), ws = pw + tap_dx(t);
-        hs = hs < 0 ? hs + H : (hs >= H ? hs - H : hs);
-        ws = ws < 0 ? ws + W : (ws >= W ? ws - W : ws);
-        const bf16 *src = x + ((((long long)pb * H + hs) * W + ws) * CIN + kc * BK);
-        // A: row m = tid, k-groups q = 0..BK/8-1
+        const int j0 = st * KS;
+        const int nk = ksteps - j0 < KS ? ksteps - j0 : KS;
 #pragma unroll
-        for (int q = 0; q < BK / 8; ++q)
-            cp_async16(a + ((tid >> 3) * (BK / 8) + q) * 128 + (tid & 7) * 16, src + q * 8);
-        // B: COUT rows x BK/8 k-groups
-        for (int c = tid; c < COUT * (BK / 8); c += TC_THREADS) {
-            const int n = c / (BK / 8), q = c % (BK / 8);
-            cp_async16(b + ((n >> 3) * (BK / 8) + q) * 128 + (n & 7) * 16,
-                       w + (((long long)t * COUT + n) * CIN + kc * BK + q * 8));
+        for (int kk = 0; kk < KS; ++kk) {
+            if (kk < nk) {
+                const int j = j0 + kk, t = j / cg, c0 = (j % cg) * 16;
+                int hs = ph + tap_dy(t), ws = pw + tap_dx(t);
+                hs = hs < 0 ? hs + H : (hs >= H ? hs - H : hs);
+                ws = ws < 0 ? ws + W : (ws >= W ? ws - W : ws);
+                const bf16 *src = x + ((((long long)pb * H + hs) * W + ws) * CIN + c0);
+                unsigned char *dst = a + ((tid >> 3) * KG + 2 * kk) * 128 + (tid & 7) * 16;
+                cp_async16(dst, src);
+                cp_async16(dst + 128, src + 8);
+            }
+        }
+        for (int c = tid; c < COUT * 2 * nk; c += TC_THREADS) {
+            const int n = c / (2 * nk), q = c % (2 * nk);  // q: k-group within the stage
+            const int j = j0 + (q >> 1), t = j / cg, c0 = (j % cg) * 16 + (q & 1) * 8;
+            cp_async16(b + ((n >> 3) * KG + q) * 128 + (n & 7) * 16, w + (((long long)t * COUT + n) * CIN + c0));
         }
     };
 
     bool ok = true;
-    load_stage(0, 0);
-    cp_commit();
+    // prologue: stages 0 .. NS-2 in flight (one commit group each, possibly empty)
+#pragma unroll
+    for (int st = 0; st < NS - 1; ++st) {
+        if (st < stages) load_stage(st);
+        cp_commit();
+    }
     for (int s = 0; s < stages; ++s) {
-        if (s >= 1) {
-            // MMA(s-1) done: its buffer is free (the decision is made uniform)
-            ok = __syncthreads_and(mbar_wait(&mbar[(s - 1) & 1], ((s - 1) >> 1) & 1) ? 1 : 0) != 0;
-            if (!ok) break;
-        }
-        if (s + 1 < stages) {
-            load_stage(s + 1, (s + 1) & 1);
-            cp_commit();
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::);  // cp.async data visible to the tensor cores
+        cp_wait<NS - 2>();                                     // stage s has landed
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);  // visible to the tensor cores
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-            const uint32_t a0 = smem_u32(base + (s & 1) * C::STAGE);
+            const uint32_t a0 = smem_u32(base + (s % NS) * C::STAGE);
             const uint32_t b0 = a0 + C::A_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t da = umma_desc(a0 + kk * 256, 128, BK * 16);
-                const uint64_t db = umma_desc(b0 + kk * 256, 128, BK * 16);
+            const int nk = ksteps - s * KS < KS ? ksteps - s * KS : KS;
+            for (int kk = 0; kk < nk; ++kk) {
+                const uint64_t da = umma_desc(a0 + kk * 256, 128, KG * 128);
+                const uint64_t db = umma_desc(b0 + kk * 256, 128, KG * 128);
                 const uint32_t acc = (s > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -397,10 +401,20 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const bf16 *__re
                     "l"(da), "l"(db), "r"(C::IDESC), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                smem_u32(&mbar[s & 1])));
+                smem_u32(&mbar[s % NS])));
         }
+        // refill the buffer of stage s-1 with stage s+NS-1 once MMA(s-1) is done
+        const int nxt = s + NS - 1;
+        if (s >= 1 && nxt < stages) {
+            ok = __syncthreads_and(mbar_wait(&mbar[(s - 1) % NS], ((s - 1) / NS) & 1) ? 1 : 0) != 0;
+            if (!ok) break;
+        }
+        if (nxt < stages) load_stage(nxt);
+        cp_commit();
     }
-    if (ok) ok = __syncthreads_and(mbar_wait(&mbar[(stages - 1) & 1], ((stages - 1) >> 1) & 1) ? 1 : 0) != 0;
+    // MMA(stages-1) complete implies all earlier ones are (same issuing thread)
+    if (ok) ok = __syncthreads_and(mbar_wait(&mbar[(stages - 1) % NS], ((stages - 1) / NS) & 1) ? 1 : 0) != 0;
+    cp_wait<0>();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
 
     if (ok) {
@@ -433,31 +447,20 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const bf16 *__re
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::TMEM_COLS));
 }
 
-template <int COUT, int BK>
+template <int COUT>
 int launch_conv_tc(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, long long P, int H, int W, int cin,
                    int relu, unsigned *err, cudaStream_t s)
 {
-    typedef TcCfg<COUT, BK> C;
+    typedef TcCfg<COUT> C;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(conv3x3_tc_kernel<COUT, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(conv3x3_tc_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C::SMEM) != cudaSuccess)
             return TEL_ECUDA;
         attr = true;
     }
-    conv3x3_tc_kernel<COUT, BK><<<(unsigned)(P / C::BM), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu, err);
+    conv3x3_tc_kernel<COUT><<<(unsigned)(P / C::BM), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu, err);
     return launched();
-}
-
-template <int COUT>
-int conv_tc_dispatch_k(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, long long P, int H, int W, int cin,
-                       int relu, unsigned *err, cudaStream_t s)
-{
-    switch (cin) {
-    case 16: return launch_conv_tc<COUT, 16>(x, w, bias, y, P, H, W, cin, relu, err, s);
-    case 32: return launch_conv_tc<COUT, 32>(x, w, bias, y, P, H, W, cin, relu, err, s);
-    default: return launch_conv_tc<COUT, 64>(x, w, bias, y, P, H, W, cin, relu, err, s);  // 64, 128
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1147,9 +1150,9 @@ extern "C" int tel_sur_conv3x3_tc(const void *x, const void *w, const float *bia
     const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
     bf16 *yb = (bf16 *)y;
     switch (cout) {
-    case 16: return conv_tc_dispatch_k<16>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
-    case 32: return conv_tc_dispatch_k<32>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
-    case 64: return conv_tc_dispatch_k<64>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
-    default: return conv_tc_dispatch_k<128>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    case 16: return launch_conv_tc<16>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    case 32: return launch_conv_tc<32>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    case 64: return launch_conv_tc<64>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    default: return launch_conv_tc<128>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
     }
 }
