@@ -298,8 +298,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
 template <int COUT>
 struct TcCfg {
     static constexpr int BM = 128;
-    static constexpr int NS = COUT == 128 ? 3 : 4;  // pipeline stages (two CTAs per SM at COUT 128)
-    static constexpr int KS = 4;                 // k-steps of 16 per stage (K = 64)
+    static constexpr int NS = 5;                 // pipeline stages
+    static constexpr int KS = 2;                 // k-steps of 16 per stage (K = 32)
     static constexpr int A_BYTES = BM * KS * 32;
     static constexpr int B_BYTES = COUT * KS * 32;
     static constexpr int STAGE = A_BYTES + B_BYTES;
@@ -376,14 +376,17 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const bf16 *__re
     };
 
     bool ok = true;
-    // prologue: stages 0 .. NS-2 in flight (one commit group each, possibly empty)
+    // Loads run LEAD = NS-3 stages ahead, so the buffer refilled at stage s
+    // (that of stage s + LEAD + 1 - NS = s - 2) was consumed by MMA(s-2),
+    // issued two stages earlier: the tensor cores' latency overlaps a stage.
+    constexpr int LEAD = NS - 3;
 #pragma unroll
-    for (int st = 0; st < NS - 1; ++st) {
+    for (int st = 0; st <= LEAD; ++st) {
         if (st < stages) load_stage(st);
         cp_commit();
     }
     for (int s = 0; s < stages; ++s) {
-        cp_wait<NS - 2>();                                     // stage s has landed
+        cp_wait<LEAD>();                                       // stage s has landed
         asm volatile("fence.proxy.async.shared::cta;\n" ::);  // visible to the tensor cores
         __syncthreads();
         if (tid == 0) {
@@ -403,10 +406,10 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const bf16 *__re
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_u32(&mbar[s % NS])));
         }
-        // refill the buffer of stage s-1 with stage s+NS-1 once MMA(s-1) is done
-        const int nxt = s + NS - 1;
-        if (s >= 1 && nxt < stages) {
-            ok = __syncthreads_and(mbar_wait(&mbar[(s - 1) % NS], ((s - 1) / NS) & 1) ? 1 : 0) != 0;
+        // refill the buffer of stage s-2 with stage s+LEAD+1 once MMA(s-2) is done
+        const int nxt = s + LEAD + 1;
+        if (s >= 2 && nxt < stages) {
+            ok = __syncthreads_and(mbar_wait(&mbar[(s - 2) % NS], ((s - 2) / NS) & 1) ? 1 : 0) != 0;
             if (!ok) break;
         }
         if (nxt < stages) load_stage(nxt);
