@@ -414,3 +414,51 @@ def test_gather_symmetry_augmentation():
         a, z = transform(store[0], code), transform(store[1], code)
         assert np.array_equal(got_in[code], a), code
         assert np.allclose(got_t[code], (z - a) / np.array([1.0, 2.0, 4.0, 4.0]), rtol=1e-6, atol=1e-6), code
+
+
+def test_surrogate_advance_is_faster_than_the_lattice_steps_it_replaces():
+    """What the network buys: one advance (a CUDA-graph replay of the whole
+    forward pass and head) against the k = 25 lattice steps it stands for,
+    on the same eight 256^2 states and the same GPU.  Timing does not depend
+    on the weights; accuracy at this k is the business of the bench, which
+    trains first."""
+    import paper_1710_07486_gb300 as tel
+    from paper_1710_07486_gb300 import inputs
+    from tests.cases import A, B, RGAS, base
+    T = tel.temperature_for_ratio(A, B, RGAS, 10.0)
+    rg, rl = tel.coexistence(A, B, RGAS, T)[:2]
+    n, H, k = 8, 256, 25
+    params = [base(T, precision=tel.FP32_SHIFTED) for _ in range(n)]
+    b = tel.Batch([(H, H)] * n, params)
+    for c in range(n):
+        b.init(c, *inputs.off_centre_2d(H, rg, rl, 5.0, 0.05, 0.1 * c, 32.0, width=5.0))
+    stream = torch.cuda.Stream()
+    b.set_stream(stream)
+    b.step(3)
+    b.step(3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    b.step(10 * k)
+    e1.record(stream)
+    e1.synchronize()
+    ms_lbm = e0.elapsed_time(e1) / 10
+    b.sync()
+    net = S.Net((32, 64, 128), seed=0)
+    pr = S.Predictor(net, n, H, H, np.full(4, 0.01, np.float32))
+    f = torch.zeros((n, H, H, 4), dtype=torch.float32, device="cuda")
+    f[..., 0] = 1.0
+    nxt = torch.empty_like(f)
+    pr.load(f)
+    g = pr.capture(f, nxt)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
+    e0.record(cur)
+    for _ in range(10):
+        g.replay()
+    e1.record(cur)
+    e1.synchronize()
+    ms_sur = e0.elapsed_time(e1) / 10
+    assert ms_lbm / ms_sur > 2.0, (ms_lbm, ms_sur)
