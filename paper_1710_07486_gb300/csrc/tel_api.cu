@@ -322,9 +322,13 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
     d.XI = (p.kappa3 - p.kappa2) / (4.0 * p.chi * Dl);
     d.rho_switch = std::sqrt(co[0] * co[1]);
     d.inv_rho_g = 1.0 / co[0];
+    d.inv_rho_g_f = (float)d.inv_rho_g;
     {
         const double dg = p.b * co[0] - 4.0;
         d.h_g = (24.0 - 2.0 * p.b * co[0]) / (dg * dg * dg);
+        d.gRT = d.lam1h * d.RT;
+        d.gRT8 = d.lam1h * 8.0 * d.RT;
+        d.ga2 = d.lam1h * 2.0 * p.a;
     }
     const double tau = 3.0 * p.nu + 0.5;
     d.beta = 1.0 / (2.0 * tau);

@@ -69,6 +69,8 @@ struct DevParams {
     double rho_switch;                // FP32 mode: gas side is rho < rho_switch
     double inv_rho_g;                 // 1/rho_g
     double h_g;                       // (24 - 2 b rho_g)/(b rho_g - 4)^3
+    double gRT, gRT8, ga2;            // lambda1/2 times RT, 8 RT, 2a (gas-side chemical potential)
+    float inv_rho_g_f;                // 1/rho_g in FP32
     // collision
     double beta, inv_beta;            // beta = 1/(2 tau)
     double c_gb;                      // 2 beta - 1: beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh>
@@ -222,17 +224,18 @@ __device__ __forceinline__ void mu_wells(const DevParams &P, T rho, T phi, T &mr
 __device__ __forceinline__ float mu_eos_gas(const DevParams &P, float rho)
 {
     const double t = (double)rho;
-    const double dg = t - P.rho_g;
-    const float L = log1pf((float)(dg * P.inv_rho_g));
-    const double d = P.b * t - 4.0;
+    const double dg = t - P.rho_g;  // exact: the cancellation happens here, in FP64
+    // ln(rho/rho_g) = log1p(dg/rho_g), well conditioned: FP32 suffices
+    const float L = log1pf((float)dg * P.inv_rho_g_f);
+    const double d = fma(P.b, t, -4.0);
     const double d3 = d * d * d;
     // FP32 seed (relative error ~2^-23) and one Newton-Raphson step in FP64:
     // ~2^-46, far below the FP32 logarithm's share of the result
     double r = (double)__frcp_rn((float)d3);
-    r = r * (2.0 - d3 * r);
-    const double h = (24.0 - 2.0 * P.b * t) * r;
-    const double eos = P.RT * (double)L - 8.0 * P.RT * (h - P.h_g) - 2.0 * P.a * dg;
-    return (float)(P.lam1h * eos);
+    r = r * fma(-d3, r, 2.0);
+    const double h = fma(-2.0, d, 16.0) * r;  // (24 - 2 b rho)/(b rho - 4)^3
+    // (lambda1/2) [RT L - 8RT (h - h_g) - 2a dg], coefficients premultiplied
+    return (float)fma(P.gRT, (double)L, fma(-P.gRT8, h - P.h_g, -P.ga2 * dg));
 }
 
 // Bulk free energy f_B of Eq. 2 (Psi_eos - Psi_0 with the common tangent).

@@ -93,10 +93,17 @@ class Net:
     """Parameters (FP32 master, BF16 working copy, Adam moments) and the
     forward/backward sequence for one batch shape (B, H, W)."""
 
-    def __init__(self, widths=(32, 64, 128), seed=0):
+    def __init__(self, widths=(32, 64, 128), seed=0, conv="mma"):
+        """conv: "mma" (warp-level tensor-core kernel, the faster at these
+        sizes) or "tc" (tcgen05 kernel with the accumulator in tensor
+        memory) for the forward and input-gradient convolutions."""
         import torch
         self.torch = torch
         self.L = sur_lib()
+        if conv not in ("mma", "tc"):
+            raise ValueError("conv must be 'mma' or 'tc'")
+        self.conv = conv
+        self.tc_err = torch.zeros(1, dtype=torch.int32, device="cuda")
         self.ops = layers(*widths)
         self.convs = [op for op in self.ops if op[0] == "conv"]
         # flat layout: per conv W [9][cout][cin] then b [cout]
@@ -127,6 +134,13 @@ class Net:
     @property
     def params(self):
         return self.n
+
+    def conv3x3(self, x, w_off, w, bias, y, B, H, W, ci, co, relu, s):
+        """One convolution with the selected kernel (weights at w[w_off:])."""
+        if self.conv == "tc":
+            return self.L.tel_sur_conv3x3_tc(_p(x), _p(w, w_off), bias, _p(y), B, H, W, ci, co, relu,
+                                             _p(self.tc_err), s)
+        return self.L.tel_sur_conv3x3(_p(x), _p(w, w_off), bias, _p(y), B, H, W, ci, co, relu, s)
 
     def sync_bf16(self):
         _ok(self.L.tel_sur_to_bf16(_p(self.w32), _p(self.w16), self.n, _stream()), "to_bf16")
@@ -230,8 +244,8 @@ class _Plan:
             if kind == "conv":
                 _, k, ci, co, relu, h, w, _, y = r
                 r[7] = a
-                _ok(L.tel_sur_conv3x3(_p(a), _p(net.w16, net.woff[k]), _p(net.w32, net.boff[k]), _p(y),
-                                      B, h, w, ci, co, relu, s), "conv3x3")
+                _ok(net.conv3x3(a, net.woff[k], net.w16, _p(net.w32, net.boff[k]), y, B, h, w, ci, co, relu, s),
+                    "conv3x3")
                 a = y
             elif kind == "pool":
                 _, c, h, w, y = r
@@ -270,7 +284,7 @@ class _Plan:
                     _ok(L.tel_sur_flip_weights(_p(net.w16, net.woff[k]), _p(net.wt16, net.woff[k]), ci, co, s),
                         "flip")
                     dx = self.dx[id(r)]
-                    _ok(L.tel_sur_conv3x3(_p(dz), _p(net.wt16, net.woff[k]), None, _p(dx), B, h, w, co, ci, 0, s),
+                    _ok(net.conv3x3(dz, net.woff[k], net.wt16, None, dx, B, h, w, co, ci, 0, s),
                         "conv3x3 (input gradient)")
                     d = dx
             elif kind == "pool":
@@ -570,3 +584,75 @@ class Hybrid:
             f32.copy_(self.prop)
         self.log.append(path)
         return path
+
+
+def _main():
+    """Timing driver: python -m paper_1710_07486_gb300.surrogate
+    [--batch B] [--size H] [--advances N] [--conv mma|tc] [--layers].
+    Builds the 581k-parameter network with seeded weights (kernel time does
+    not depend on their values), makes N advances of B states of H x H and
+    prints one JSON line; --layers times every convolution shape of the
+    network with both kernels instead."""
+    import argparse
+    import json
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--advances", type=int, default=3)
+    ap.add_argument("--conv", default="mma", choices=["mma", "tc"])
+    ap.add_argument("--layers", action="store_true")
+    a = ap.parse_args()
+    B, H = a.batch, a.size
+    if a.layers:
+        L = sur_lib()
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        out = []
+        for ci, co, h in [(CIN, 32, H), (32, 32, H), (32, 64, H // 2), (64, 64, H // 2), (64, 128, H // 4),
+                          (128, 128, H // 4), (128, 64, H // 2), (64, 32, H), (32, COUT, H)]:
+            x = torch.randn((B, h, h, ci), device="cuda").to(torch.bfloat16)
+            w = (torch.randn((9, co, ci), device="cuda") * 0.05).to(torch.bfloat16)
+            b = torch.zeros(co, device="cuda")
+            y = torch.empty((B, h, h, co), dtype=torch.bfloat16, device="cuda")
+            rec = {"cin": ci, "cout": co, "hw": h}
+            for name in ("mma", "tc"):
+                def run():
+                    if name == "tc":
+                        return L.tel_sur_conv3x3_tc(_p(x), _p(w), _p(b), _p(y), B, h, h, ci, co, 1, _p(err), _stream())
+                    return L.tel_sur_conv3x3(_p(x), _p(w), _p(b), _p(y), B, h, h, ci, co, 1, _stream())
+                for _ in range(3):
+                    _ok(run(), name)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(20):
+                    run()
+                e1.record()
+                e1.synchronize()
+                us = 1e3 * e0.elapsed_time(e1) / 20
+                rec[name + "_us"] = round(us, 2)
+                rec[name + "_tflops"] = round(2.0 * 9 * ci * co * B * h * h / (us * 1e-6) / 1e12, 1)
+            rec["timeout"] = int(err.item())
+            out.append(rec)
+        print(json.dumps({"batch": B, "size": H, "layers": out}))
+        return
+    net = Net((32, 64, 128), seed=0, conv=a.conv)
+    pr = Predictor(net, B, H, H, np.full(4, 0.01, np.float32))
+    f = torch.zeros((B, H, H, NF), dtype=torch.float32, device="cuda")
+    f[..., 0] = 1.0
+    nxt = torch.empty_like(f)
+    pr.load(f)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.advances):
+        pr.advance(f, nxt, mass=False)
+    e1.record()
+    e1.synchronize()
+    print(json.dumps({"batch": B, "size": H, "conv": a.conv, "advances": a.advances,
+                      "ms_per_advance": round(e0.elapsed_time(e1) / max(a.advances, 1), 4),
+                      "timeout": int(net.tc_err.item())}))
+
+
+if __name__ == "__main__":
+    _main()

@@ -462,3 +462,32 @@ def test_surrogate_advance_is_faster_than_the_lattice_steps_it_replaces():
     e1.synchronize()
     ms_sur = e0.elapsed_time(e1) / 10
     assert ms_lbm / ms_sur > 2.0, (ms_lbm, ms_sur)
+
+
+def test_network_with_tcgen05_convolutions_matches_the_warp_level_kernel():
+    """The whole network forward and backward with the tensor-memory
+    convolutions gives the warp-level kernel's results: both accumulate the
+    same BF16 products in FP32, so outputs agree to BF16 rounding."""
+    widths = (16, 32, 64)
+    nets = [S.Net(widths, seed=4, conv=c) for c in ("mma", "tc")]
+    g = np.random.default_rng(13)
+    B, H, W = 2, 32, 32
+    x = bf16_values(g, (B, H, W, 16))
+    x[..., 4:] = 0.0
+    x16 = dev_bf16(x)
+    tg = torch.from_numpy(g.normal(size=(B, H, W, 4)).astype(np.float32)).cuda()
+    outs, grads = [], []
+    for net in nets:
+        out = net.forward(x16, B, H, W)
+        dout = torch.empty((B, H, W, 16), dtype=BF, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        work = torch.zeros(4 * B, dtype=torch.float32, device="cuda")
+        assert L.tel_sur_loss(S._p(out), S._p(tg), S._p(dout), S._p(loss), S._p(work), B, H, W, s()) == 0
+        net.zero_grad()
+        net.backward(dout, B, H, W)
+        torch.cuda.synchronize()
+        outs.append(host(out))
+        grads.append(net.g.cpu().numpy().astype(np.float64))
+    assert int(nets[1].tc_err.item()) == 0
+    assert close_bf16(outs[1], outs[0])
+    assert np.linalg.norm(grads[1] - grads[0]) <= 2e-2 * np.linalg.norm(grads[0])
