@@ -453,15 +453,14 @@ class Predictor:
         self.work = torch.zeros(4 * B, dtype=torch.float32, device=dev)
         self.mass = torch.zeros(2 * B, dtype=torch.float64, device=dev)
         self.err = torch.zeros(6 * B, dtype=torch.float64, device=dev)
+        self.ident = torch.from_numpy(np.arange(B, dtype=np.int32)).to(dev)
         self.torch = torch
 
     def load(self, f32):
         """Network input from normalised FP32 fields (via the gather kernel
         with the identity index list)."""
-        import torch
-        idx = torch.arange(self.B, dtype=torch.int32, device=f32.device)
-        _ok(self.L.tel_sur_gather(_p(f32), _p(idx), None, None, None, None, _p(self.x16), None, self.B, self.H,
-                                  self.W, _stream()), "gather")
+        _ok(self.L.tel_sur_gather(_p(f32), _p(self.ident), None, None, None, None, _p(self.x16), None, self.B,
+                                  self.H, self.W, _stream()), "gather")
 
     def advance(self, f32, f32_next, mass=True):
         """f32_next = surrogate(f32); self.x16 must hold f32's network input
