@@ -631,17 +631,32 @@ struct Fused {
         const CT itg = K.inv_tau_g;
         ST *gd = reinterpret_cast<ST *>(A.gdst);
         CT goth = 0;
+        // opposite velocities (i, Q-1-i) share w_i and the even part of g^eq;
+        // c.u changes sign: g^eq = even +- odd
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (StoreTraits<ST>::shifted && i == L::REST) continue;
-            const CT ge = (i == L::REST) ? phi - others : geq_of(i, Gm3, phi, up, uu);
-            const CT gi = pull(gs, nb, P.N, i);
-            const CT go = gi - (gi - ge) * itg;
-            if (StoreTraits<ST>::shifted) goth += (CT)(ST)go;
+        for (int i = 0; i < L::REST; ++i) {
+            const int io = Q - 1 - i;
+            CT cu = 0;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                if (L::c(i, a)) cu += (CT)L::c(i, a) * up[a];
+            const CT wi = (CT)L::w(i);
+            const CT even = wi * (Gm3 + phi * ((CT)4.5 * cu * cu - (CT)1.5 * uu));
+            const CT odd = wi * (CT)3 * phi * cu;
+            const CT gi = pull(gs, nb, P.N, i), gio = pull(gs, nb, P.N, io);
+            const CT go = gi - (gi - (even + odd)) * itg;
+            const CT goo = gio - (gio - (even - odd)) * itg;
+            if (StoreTraits<ST>::shifted) goth += (CT)(ST)go + (CT)(ST)goo;
             gd[(long long)i * P.N + n] = (ST)go;
+            gd[(long long)io * P.N + n] = (ST)goo;
         }
-        // FP32 storage: the rest population closes the node's phase-field sum
-        if (StoreTraits<ST>::shifted) gd[(long long)L::REST * P.N + n] = (ST)(phi - goth);
+        if (StoreTraits<ST>::shifted) {
+            // FP32 storage: the rest population closes the node's phase-field sum
+            gd[(long long)L::REST * P.N + n] = (ST)(phi - goth);
+        } else {
+            const CT gi = pull(gs, nb, P.N, L::REST);
+            gd[(long long)L::REST * P.N + n] = (ST)(gi - (gi - (phi - others)) * itg);
+        }
 
         CT uF[3] = {0, 0, 0};
 #pragma unroll
@@ -690,7 +705,7 @@ struct Fused {
             // terms only where ds != 0 (one or two non-zero components of c_i)
             const bool has_ds = L::nnz(i) == 1 || L::nnz(i) == 2;
             if (StoreTraits<ST>::shifted) {
-                const CT r = __frcp_rn((float)feq);
+                const CT r = __fdividef(1.f, (float)feq);  // weight 1/f^eq: ~2 ulp is ample
                 if (has_ds) two_sum_acc<CT>(sh, shc, ds * dh * r);
                 hh += dh * dh * r;
             } else {
@@ -718,8 +733,8 @@ struct Fused {
             const double rhod = (double)rho;
             if (hhd > 1e-30 * rhod * rhod) gbd = 1.0 - P.c_gb * (shd / hhd);
         }
-        if (!isfinite(gbd)) bad |= ERR_NAN;
         const CT bet = K.beta, gb = (CT)gbd;
+        if (!isfinite(gb)) bad |= ERR_NAN;  // tested after the conversion: no FP64-pipe compare
         ST *fd = reinterpret_cast<ST *>(A.fdst);
         // FP32 storage: the rest population closes the node's mass so that the
         // stored set sums to the pulled mass; rounding of the other outputs
