@@ -467,6 +467,172 @@ int launch_conv_tc(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, lon
 }
 
 // ---------------------------------------------------------------------------
+// tcgen05 convolution with a shared halo tile (rows of a multiple of 128
+// pixels).  A CTA owns 128 consecutive pixels of one image row.  Per chunk of
+// 16 input channels it stages, once, the 3 x 130-pixel halo around them
+// (periodic wrap) and the weights of all nine taps; the nine MMAs of the
+// chunk then read the halo through shifted descriptors: in the pixel-major
+// core-matrix layout (16 B per pixel and 8-channel group, pixels 16 B apart,
+// the two channel groups one halo plane apart) the A operand of tap (dy, dx)
+// is the same tile started (1+dy) rows and (1+dx) pixels further on.
+// ---------------------------------------------------------------------------
+constexpr int HALO_C = 130;                      // pixels per halo row
+constexpr int HALO_PLANE = 3 * HALO_C * 16;      // bytes per 8-channel group
+
+template <int COUT>
+struct TchCfg {
+    static constexpr int NS = 2;                 // chunk buffers
+    static constexpr int A_BYTES = 2 * HALO_PLANE;
+    static constexpr int B_BYTES = TAPS * 2 * COUT * 16;
+    static constexpr int STAGE = (A_BYTES + B_BYTES + 127) / 128 * 128;
+    static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
+    static constexpr size_t SMEM_OPS = 1024 + NS * (size_t)STAGE;
+    static constexpr size_t SMEM_TMEM = (size_t)233472 * TMEM_COLS / 512 + 1024;
+    static constexpr size_t SMEM = SMEM_OPS > SMEM_TMEM ? SMEM_OPS : SMEM_TMEM;
+    static constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
+};
+
+template <int COUT>
+__global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__restrict__ x,
+                                                                 const bf16 *__restrict__ w,
+                                                                 const float *__restrict__ bias,
+                                                                 bf16 *__restrict__ y, int H, int W, int CIN, int relu,
+                                                                 unsigned *err)
+{
+    typedef TchCfg<COUT> C;
+    constexpr int NS = C::NS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);  // 1024-byte aligned
+    __shared__ uint64_t mbar[NS];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int segs = W / 128;
+    const long long row = blockIdx.x / segs;  // image row index b*H + h
+    const int w0 = (int)(blockIdx.x % segs) * 128;
+    const int h = (int)(row % H);
+    const long long b = row / H;
+    const int stages = CIN / 16;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                     "r"(C::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        for (int q = 0; q < NS; ++q) mbar_init(&mbar[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = tmem_base;
+
+    auto load_stage = [&](int st) {
+        unsigned char *a = base + (st % NS) * C::STAGE;
+        unsigned char *bt = a + C::A_BYTES;
+        const int c0 = st * 16;
+        // halo: [kg][r][c], 16 B per (kg, r, c)
+        for (int e = tid; e < 2 * 3 * HALO_C; e += TC_THREADS) {
+            const int kg = e / (3 * HALO_C), rc = e % (3 * HALO_C), r = rc / HALO_C, c = rc % HALO_C;
+            int hs = h + r - 1, ws = w0 + c - 1;
+            hs = hs < 0 ? hs + H : (hs >= H ? hs - H : hs);
+            ws = ws < 0 ? ws + W : (ws >= W ? ws - W : ws);
+            cp_async16(a + e * 16, x + (((b * H + hs) * W + ws) * CIN + c0 + kg * 8));
+        }
+        // weights of the nine taps: [t][kg][n], 16 B each
+        for (int e = tid; e < TAPS * 2 * COUT; e += TC_THREADS) {
+            const int t = e / (2 * COUT), kg = (e / COUT) % 2, n = e % COUT;
+            cp_async16(bt + e * 16, w + (((long long)t * COUT + n) * CIN + c0 + kg * 8));
+        }
+    };
+
+    bool ok = true;
+    load_stage(0);
+    cp_commit();
+    for (int s = 0; s < stages; ++s) {
+        if (s + 1 < stages) {
+            if (s >= 1) {  // buffer of stage s+1 held stage s-1: wait for its MMAs
+                ok = __syncthreads_and(mbar_wait(&mbar[(s - 1) % NS], ((s - 1) / NS) & 1) ? 1 : 0) != 0;
+                if (!ok) break;
+            }
+            load_stage(s + 1);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t a0 = smem_u32(base + (s % NS) * C::STAGE);
+            const uint32_t b0 = a0 + C::A_BYTES;
+#pragma unroll
+            for (int t = 0; t < TAPS; ++t) {
+                const uint32_t sa = a0 + ((1 + tap_dy(t)) * HALO_C + (1 + tap_dx(t))) * 16;
+                const uint64_t da = umma_desc(sa, HALO_PLANE, 128);
+                const uint64_t db = umma_desc(b0 + t * 2 * COUT * 16, COUT * 16, 128);
+                const uint32_t acc = (s > 0 || t > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(C::IDESC), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&mbar[s % NS])));
+        }
+    }
+    if (ok) ok = __syncthreads_and(mbar_wait(&mbar[(stages - 1) % NS], ((stages - 1) / NS) & 1) ? 1 : 0) != 0;
+    cp_wait<0>();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+    if (ok) {
+        const long long p = row * W + w0 + tid;  // output pixel of TMEM lane tid
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int n0 = 0; n0 < COUT; n0 += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(lane_addr + n0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+            __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[n0 + 2 * j] : 0.f);
+                float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[n0 + 2 * j + 1] : 0.f);
+                if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                o[j] = __floats2bfloat162_rn(v0, v1);
+            }
+            *reinterpret_cast<uint4 *>(y + p * COUT + n0) = *reinterpret_cast<const uint4 *>(o);
+        }
+    } else if (tid == 0 && err) {
+        atomicOr(err, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::TMEM_COLS));
+}
+
+template <int COUT>
+int launch_conv_tch(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, long long P, int H, int W, int cin,
+                    int relu, unsigned *err, cudaStream_t s)
+{
+    typedef TchCfg<COUT> C;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(conv3x3_tch_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::SMEM) != cudaSuccess)
+            return TEL_ECUDA;
+        attr = true;
+    }
+    conv3x3_tch_kernel<COUT><<<(unsigned)(P / 128), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu, err);
+    return launched();
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient: per CTA one tap, a (Cout tile BMO) x (Cin tile BNI)
 // block, and a chunk of pixels; each of 4 warps takes 16 of the 64 pixels of
 // a stage (its own k16 slice), then the warps' partial sums are added in
@@ -1152,6 +1318,14 @@ extern "C" int tel_sur_conv3x3_tc(const void *x, const void *w, const float *bia
     if (!x || !w || !y || B < 1 || H < 1 || W < 1 || !chan_ok(cin) || !chan_ok(cout) || P % 128) return TEL_EINVAL;
     const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
     bf16 *yb = (bf16 *)y;
+    if (W % 128 == 0) {  // rows of whole 128-pixel segments: the shared halo tile
+        switch (cout) {
+        case 16: return launch_conv_tch<16>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        case 32: return launch_conv_tch<32>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        case 64: return launch_conv_tch<64>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        default: return launch_conv_tch<128>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        }
+    }
     switch (cout) {
     case 16: return launch_conv_tc<16>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
     case 32: return launch_conv_tc<32>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));

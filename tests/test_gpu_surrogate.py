@@ -77,11 +77,13 @@ def test_conv_forward_against_oracle(cin, cout):
 
 @pytest.mark.parametrize("cin", CH)
 @pytest.mark.parametrize("cout", CH)
-def test_conv_forward_tcgen05_against_oracle(cin, cout):
+@pytest.mark.parametrize("B,H,W", [(2, 8, 24), (2, 3, 128), (1, 2, 256)])
+def test_conv_forward_tcgen05_against_oracle(cin, cout, B, H, W):
     """The tensor-memory (tcgen05) convolution at the same bar, and its
-    time-out flag clear."""
-    g = np.random.default_rng(cin * 1000 + cout + 7)
-    B, H, W = 2, 8, 24
+    time-out flag clear: rows of 24 pixels take the per-tap gather kernel,
+    rows of 128 and 256 the shared-halo kernel (with the periodic wrap in
+    both directions; H = 2 and 3 wrap onto rows the halo already holds)."""
+    g = np.random.default_rng(cin * 1000 + cout + 7 + W)
     x = bf16_values(g, (B, H, W, cin))
     Wo = bf16_values(g, (9, cin, cout), 1.0 / np.sqrt(9 * cin))
     b = g.normal(size=cout).astype(np.float32).astype(np.float64)
