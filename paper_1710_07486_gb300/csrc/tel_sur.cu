@@ -477,37 +477,44 @@ int launch_conv_tc(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, lon
 // is the same tile started (1+dy) rows and (1+dx) pixels further on.
 // ---------------------------------------------------------------------------
 constexpr int HALO_C = 130;                      // pixels per halo row
-constexpr int HALO_PLANE = 3 * HALO_C * 16;      // bytes per 8-channel group
 
-template <int COUT>
+constexpr int pow2_at_least(int v, int p) { return p >= v ? p : pow2_at_least(v, 2 * p); }
+
+// R image rows per CTA (R accumulators of COUT columns side by side in
+// tensor memory): the halo holds R + 2 rows and the weights are staged once
+// for all R rows.
+template <int COUT, int R>
 struct TchCfg {
     static constexpr int NS = 2;                 // chunk buffers
+    static constexpr int HALO_PLANE = (R + 2) * HALO_C * 16;  // bytes per 8-channel group
     static constexpr int A_BYTES = 2 * HALO_PLANE;
     static constexpr int B_BYTES = TAPS * 2 * COUT * 16;
     static constexpr int STAGE = (A_BYTES + B_BYTES + 127) / 128 * 128;
-    static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
+    static constexpr int TMEM_COLS = pow2_at_least(R * COUT, 32);
     static constexpr size_t SMEM_OPS = 1024 + NS * (size_t)STAGE;
-    static constexpr size_t SMEM_TMEM = (size_t)233472 * TMEM_COLS / 512 + 1024;
+    // shared memory large enough that at most 512 / TMEM_COLS CTAs fit on an
+    // SM (228 KB, 1 KB reserved per CTA): their allocations never wait
+    static constexpr size_t SMEM_TMEM = (size_t)233472 / (512 / TMEM_COLS + 1) - 1023;
     static constexpr size_t SMEM = SMEM_OPS > SMEM_TMEM ? SMEM_OPS : SMEM_TMEM;
     static constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
 };
 
-template <int COUT>
+template <int COUT, int R>
 __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__restrict__ x,
                                                                  const bf16 *__restrict__ w,
                                                                  const float *__restrict__ bias,
                                                                  bf16 *__restrict__ y, int H, int W, int CIN, int relu,
                                                                  unsigned *err)
 {
-    typedef TchCfg<COUT> C;
-    constexpr int NS = C::NS;
+    typedef TchCfg<COUT, R> C;
+    constexpr int NS = C::NS, HP = C::HALO_PLANE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);  // 1024-byte aligned
     __shared__ uint64_t mbar[NS];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int segs = W / 128;
-    const long long row = blockIdx.x / segs;  // image row index b*H + h
+    const long long row = (long long)(blockIdx.x / segs) * R;  // first image row b*H + h of the CTA
     const int w0 = (int)(blockIdx.x % segs) * 128;
     const int h = (int)(row % H);
     const long long b = row / H;
@@ -532,8 +539,8 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__r
         unsigned char *bt = a + C::A_BYTES;
         const int c0 = st * 16;
         // halo: [kg][r][c], 16 B per (kg, r, c)
-        for (int e = tid; e < 2 * 3 * HALO_C; e += TC_THREADS) {
-            const int kg = e / (3 * HALO_C), rc = e % (3 * HALO_C), r = rc / HALO_C, c = rc % HALO_C;
+        for (int e = tid; e < 2 * (R + 2) * HALO_C; e += TC_THREADS) {
+            const int kg = e / ((R + 2) * HALO_C), rc = e % ((R + 2) * HALO_C), r = rc / HALO_C, c = rc % HALO_C;
             int hs = h + r - 1, ws = w0 + c - 1;
             hs = hs < 0 ? hs + H : (hs >= H ? hs - H : hs);
             ws = ws < 0 ? ws + W : (ws >= W ? ws - W : ws);
@@ -569,14 +576,17 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__r
             const uint32_t b0 = a0 + C::A_BYTES;
 #pragma unroll
             for (int t = 0; t < TAPS; ++t) {
-                const uint32_t sa = a0 + ((1 + tap_dy(t)) * HALO_C + (1 + tap_dx(t))) * 16;
-                const uint64_t da = umma_desc(sa, HALO_PLANE, 128);
                 const uint64_t db = umma_desc(b0 + t * 2 * COUT * 16, COUT * 16, 128);
                 const uint32_t acc = (s > 0 || t > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(C::IDESC), "r"(acc));
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) {
+                    const uint32_t sa = a0 + ((1 + rr + tap_dy(t)) * HALO_C + (1 + tap_dx(t))) * 16;
+                    const uint64_t da = umma_desc(sa, HP, 128);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + rr * COUT),
+                        "l"(da), "l"(db), "r"(C::IDESC), "r"(acc));
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_u32(&mbar[s % NS])));
@@ -587,15 +597,17 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__r
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
 
     if (ok) {
-        const long long p = row * W + w0 + tid;  // output pixel of TMEM lane tid
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int rr = 0; rr < R; ++rr) {
+        const long long p = (row + rr) * W + w0 + tid;  // output pixel of TMEM lane tid, row rr
 #pragma unroll
         for (int n0 = 0; n0 < COUT; n0 += 8) {
             uint32_t r[8];
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
                            "=r"(r[7])
-                         : "r"(lane_addr + n0));
+                         : "r"(lane_addr + rr * COUT + n0));
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
             __align__(16) __nv_bfloat162 o[4];
 #pragma unroll
@@ -607,6 +619,7 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__r
             }
             *reinterpret_cast<uint4 *>(y + p * COUT + n0) = *reinterpret_cast<const uint4 *>(o);
         }
+        }
     } else if (tid == 0 && err) {
         atomicOr(err, 1u);
     }
@@ -616,19 +629,20 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__r
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::TMEM_COLS));
 }
 
-template <int COUT>
+template <int COUT, int R>
 int launch_conv_tch(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, long long P, int H, int W, int cin,
                     int relu, unsigned *err, cudaStream_t s)
 {
-    typedef TchCfg<COUT> C;
+    typedef TchCfg<COUT, R> C;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(conv3x3_tch_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(conv3x3_tch_kernel<COUT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C::SMEM) != cudaSuccess)
             return TEL_ECUDA;
         attr = true;
     }
-    conv3x3_tch_kernel<COUT><<<(unsigned)(P / 128), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu, err);
+    conv3x3_tch_kernel<COUT, R><<<(unsigned)(P / (128 * R)), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu,
+                                                                                     err);
     return launched();
 }
 
@@ -1318,12 +1332,20 @@ extern "C" int tel_sur_conv3x3_tc(const void *x, const void *w, const float *bia
     if (!x || !w || !y || B < 1 || H < 1 || W < 1 || !chan_ok(cin) || !chan_ok(cout) || P % 128) return TEL_EINVAL;
     const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
     bf16 *yb = (bf16 *)y;
-    if (W % 128 == 0) {  // rows of whole 128-pixel segments: the shared halo tile
+    if (W % 128 == 0 && H % 4 == 0) {  // whole 128-pixel segments, four rows per CTA: shared halo tile
         switch (cout) {
-        case 16: return launch_conv_tch<16>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
-        case 32: return launch_conv_tch<32>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
-        case 64: return launch_conv_tch<64>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
-        default: return launch_conv_tch<128>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        case 16: return launch_conv_tch<16, 4>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        case 32: return launch_conv_tch<32, 4>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        case 64: return launch_conv_tch<64, 4>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        default: return launch_conv_tch<128, 4>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        }
+    }
+    if (W % 128 == 0) {  // whole 128-pixel segments, one row per CTA
+        switch (cout) {
+        case 16: return launch_conv_tch<16, 1>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        case 32: return launch_conv_tch<32, 1>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        case 64: return launch_conv_tch<64, 1>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+        default: return launch_conv_tch<128, 1>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
         }
     }
     switch (cout) {

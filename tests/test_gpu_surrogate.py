@@ -77,12 +77,14 @@ def test_conv_forward_against_oracle(cin, cout):
 
 @pytest.mark.parametrize("cin", CH)
 @pytest.mark.parametrize("cout", CH)
-@pytest.mark.parametrize("B,H,W", [(2, 8, 24), (2, 3, 128), (1, 2, 256)])
+@pytest.mark.parametrize("B,H,W", [(2, 8, 24), (2, 3, 128), (1, 2, 256), (1, 4, 128), (2, 8, 256)])
 def test_conv_forward_tcgen05_against_oracle(cin, cout, B, H, W):
     """The tensor-memory (tcgen05) convolution at the same bar, and its
     time-out flag clear: rows of 24 pixels take the per-tap gather kernel,
-    rows of 128 and 256 the shared-halo kernel (with the periodic wrap in
-    both directions; H = 2 and 3 wrap onto rows the halo already holds)."""
+    rows of 128 and 256 the shared-halo kernel, one row per CTA when H is
+    not a multiple of 4 and four rows per CTA when it is (with the periodic
+    wrap in both directions; H = 2, 3 and 4 wrap onto rows the halo already
+    holds)."""
     g = np.random.default_rng(cin * 1000 + cout + 7 + W)
     x = bf16_values(g, (B, H, W, cin))
     Wo = bf16_values(g, (9, cin, cout), 1.0 / np.sqrt(9 * cin))
