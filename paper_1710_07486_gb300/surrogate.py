@@ -93,15 +93,17 @@ class Net:
     """Parameters (FP32 master, BF16 working copy, Adam moments) and the
     forward/backward sequence for one batch shape (B, H, W)."""
 
-    def __init__(self, widths=(32, 64, 128), seed=0, conv="mma"):
-        """conv: "mma" (warp-level tensor-core kernel, the faster at these
-        sizes) or "tc" (tcgen05 kernel with the accumulator in tensor
-        memory) for the forward and input-gradient convolutions."""
+    def __init__(self, widths=(32, 64, 128), seed=0, conv="auto"):
+        """conv selects the kernel of the forward and input-gradient
+        convolutions: "tc" (tcgen05, accumulator in tensor memory), "mma"
+        (warp-level tensor-core kernel) or "auto" (default): tcgen05 on
+        grids whose rows are whole 128-pixel segments, where its shared halo
+        tile makes it the faster, the warp-level kernel elsewhere."""
         import torch
         self.torch = torch
         self.L = sur_lib()
-        if conv not in ("mma", "tc"):
-            raise ValueError("conv must be 'mma' or 'tc'")
+        if conv not in ("mma", "tc", "auto"):
+            raise ValueError("conv must be 'mma', 'tc' or 'auto'")
         self.conv = conv
         self.tc_err = torch.zeros(1, dtype=torch.int32, device="cuda")
         self.ops = layers(*widths)
@@ -137,7 +139,7 @@ class Net:
 
     def conv3x3(self, x, w_off, w, bias, y, B, H, W, ci, co, relu, s):
         """One convolution with the selected kernel (weights at w[w_off:])."""
-        if self.conv == "tc":
+        if self.conv == "tc" or (self.conv == "auto" and W % 128 == 0):
             return self.L.tel_sur_conv3x3_tc(_p(x), _p(w, w_off), bias, _p(y), B, H, W, ci, co, relu,
                                              _p(self.tc_err), s)
         return self.L.tel_sur_conv3x3(_p(x), _p(w, w_off), bias, _p(y), B, H, W, ci, co, relu, s)
@@ -599,7 +601,7 @@ def _main():
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--advances", type=int, default=3)
-    ap.add_argument("--conv", default="mma", choices=["mma", "tc"])
+    ap.add_argument("--conv", default="auto", choices=["mma", "tc", "auto"])
     ap.add_argument("--layers", action="store_true")
     a = ap.parse_args()
     B, H = a.batch, a.size

@@ -468,14 +468,16 @@ def test_surrogate_advance_is_faster_than_the_lattice_steps_it_replaces():
     assert ms_lbm / ms_sur > 2.0, (ms_lbm, ms_sur)
 
 
-def test_network_with_tcgen05_convolutions_matches_the_warp_level_kernel():
+@pytest.mark.parametrize("H", [32, 128])
+def test_network_with_tcgen05_convolutions_matches_the_warp_level_kernel(H):
     """The whole network forward and backward with the tensor-memory
-    convolutions gives the warp-level kernel's results: both accumulate the
-    same BF16 products in FP32, so outputs agree to BF16 rounding."""
+    convolutions (per-tap gather at 32^2; shared halo at the 128^2 level,
+    gather below) gives the warp-level kernel's results: both accumulate
+    the same BF16 products in FP32, so outputs agree to BF16 rounding."""
     widths = (16, 32, 64)
     nets = [S.Net(widths, seed=4, conv=c) for c in ("mma", "tc")]
     g = np.random.default_rng(13)
-    B, H, W = 2, 32, 32
+    B, W = 2, H
     x = bf16_values(g, (B, H, W, 16))
     x[..., 4:] = 0.0
     x16 = dev_bf16(x)
