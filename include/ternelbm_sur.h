@@ -42,6 +42,16 @@ int tel_sur_conv3x3(const void *x, const void *w, const float *bias, void *y, in
 int tel_sur_conv3x3_tc(const void *x, const void *w, const float *bias, void *y, int B, int H, int W, int cin,
                        int cout, int relu, unsigned *err, void *stream);
 
+/* Inference form of the tensor-memory convolution for rows of whole
+ * 128-pixel segments (W a multiple of 128, H of 4): with up_input != 0, x is
+ * the (H/2) x (W/2) grid read through 2x2 nearest upsampling, which saves
+ * materialising the upsampled tensor; skip (bf16
+ * [B][H][W][cout], may be NULL) is added to the output, rounded as a
+ * separate tel_sur_add of the rounded output would be.  Other shapes:
+ * TEL_EINVAL. */
+int tel_sur_conv3x3_tc_fused(const void *x, const void *w, const float *bias, void *y, int B, int H, int W, int cin,
+                             int cout, int relu, int up_input, const void *skip, unsigned *err, void *stream);
+
 /* Weights for the input gradient: the input gradient of a conv is the conv
  * of its output gradient with w_t[s][i][o] = w[8-s][o][i].  Writes w_t
  * (bf16 [9][Cin][Cout]) from w (bf16 [9][Cout][Cin]). */

@@ -499,12 +499,15 @@ struct TchCfg {
     static constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
 };
 
+// up: x is the coarse (H/2) x (W/2) grid, read through 2x2 nearest
+// upsampling; skip (may be NULL): added to the stored (rounded) output, as a
+// separate addition of two BF16 tensors would.
 template <int COUT, int R>
 __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__restrict__ x,
                                                                  const bf16 *__restrict__ w,
                                                                  const float *__restrict__ bias,
                                                                  bf16 *__restrict__ y, int H, int W, int CIN, int relu,
-                                                                 unsigned *err)
+                                                                 unsigned *err, int up, const bf16 *__restrict__ skip)
 {
     typedef TchCfg<COUT, R> C;
     constexpr int NS = C::NS, HP = C::HALO_PLANE;
@@ -544,7 +547,9 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__r
             int hs = h + r - 1, ws = w0 + c - 1;
             hs = hs < 0 ? hs + H : (hs >= H ? hs - H : hs);
             ws = ws < 0 ? ws + W : (ws >= W ? ws - W : ws);
-            cp_async16(a + e * 16, x + (((b * H + hs) * W + ws) * CIN + c0 + kg * 8));
+            const long long src = up ? ((b * (H >> 1) + (hs >> 1)) * (W >> 1) + (ws >> 1))
+                                     : ((b * H + hs) * W + ws);
+            cp_async16(a + e * 16, x + (src * CIN + c0 + kg * 8));
         }
         // weights of the nine taps: [t][kg][n], 16 B each
         for (int e = tid; e < TAPS * 2 * COUT; e += TC_THREADS) {
@@ -617,6 +622,15 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__r
                 if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
                 o[j] = __floats2bfloat162_rn(v0, v1);
             }
+            if (skip) {
+                const uint4 sv = *reinterpret_cast<const uint4 *>(skip + p * COUT + n0);
+                const __nv_bfloat162 *sk = reinterpret_cast<const __nv_bfloat162 *>(&sv);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 a2 = __bfloat1622float2(o[j]), s2 = __bfloat1622float2(sk[j]);
+                    o[j] = __floats2bfloat162_rn(a2.x + s2.x, a2.y + s2.y);
+                }
+            }
             *reinterpret_cast<uint4 *>(y + p * COUT + n0) = *reinterpret_cast<const uint4 *>(o);
         }
         }
@@ -631,7 +645,7 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tch_kernel(const bf16 *__r
 
 template <int COUT, int R>
 int launch_conv_tch(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, long long P, int H, int W, int cin,
-                    int relu, unsigned *err, cudaStream_t s)
+                    int relu, unsigned *err, cudaStream_t s, int up = 0, const bf16 *skip = nullptr)
 {
     typedef TchCfg<COUT, R> C;
     static bool attr = false;
@@ -642,7 +656,7 @@ int launch_conv_tch(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, lo
         attr = true;
     }
     conv3x3_tch_kernel<COUT, R><<<(unsigned)(P / (128 * R)), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu,
-                                                                                     err);
+                                                                                     err, up, skip);
     return launched();
 }
 
@@ -1353,5 +1367,22 @@ extern "C" int tel_sur_conv3x3_tc(const void *x, const void *w, const float *bia
     case 32: return launch_conv_tc<32>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
     case 64: return launch_conv_tc<64>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
     default: return launch_conv_tc<128>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream));
+    }
+}
+
+extern "C" int tel_sur_conv3x3_tc_fused(const void *x, const void *w, const float *bias, void *y, int B, int H, int W,
+                                        int cin, int cout, int relu, int up_input, const void *skip, unsigned *err,
+                                        void *stream)
+{
+    const long long P = (long long)B * H * W;
+    if (!x || !w || !y || B < 1 || H < 4 || W < 128 || !chan_ok(cin) || !chan_ok(cout)) return TEL_EINVAL;
+    if (W % 128 || H % 4) return TEL_EINVAL;  // the four-row halo kernel only (H, W even for the upsampled input)
+    const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w, *sb = (const bf16 *)skip;
+    bf16 *yb = (bf16 *)y;
+    switch (cout) {
+    case 16: return launch_conv_tch<16, 4>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream), up_input, sb);
+    case 32: return launch_conv_tch<32, 4>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream), up_input, sb);
+    case 64: return launch_conv_tch<64, 4>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream), up_input, sb);
+    default: return launch_conv_tch<128, 4>(xb, wb, bias, yb, P, H, W, cin, relu, err, S(stream), up_input, sb);
     }
 }

@@ -26,7 +26,7 @@ from . import Batch, TelError, lib
 CIN, COUT, NF = 16, 16, 4
 U_REF = 0.1  # velocity normalisation (lattice units)
 
-SUR_SYMBOLS = ("tel_sur_conv3x3", "tel_sur_conv3x3_tc", "tel_sur_flip_weights", "tel_sur_relu_bwd", "tel_sur_conv3x3_wgrad",
+SUR_SYMBOLS = ("tel_sur_conv3x3", "tel_sur_conv3x3_tc", "tel_sur_conv3x3_tc_fused", "tel_sur_flip_weights", "tel_sur_relu_bwd", "tel_sur_conv3x3_wgrad",
                "tel_sur_pool2", "tel_sur_pool2_bwd", "tel_sur_up2", "tel_sur_up2_bwd", "tel_sur_add",
                "tel_sur_pack", "tel_sur_unpack", "tel_sur_gather", "tel_sur_loss", "tel_sur_advance",
                "tel_sur_errors", "tel_sur_sums", "tel_sur_adam", "tel_sur_zero", "tel_sur_to_bf16")
@@ -39,6 +39,7 @@ def sur_lib():
     vp, i, ll, f = C.c_void_p, C.c_int, C.c_longlong, C.c_float
     L.tel_sur_conv3x3.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp]
     L.tel_sur_conv3x3_tc.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp, vp]
+    L.tel_sur_conv3x3_tc_fused.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, i, vp, vp, vp]
     L.tel_sur_flip_weights.argtypes = [vp, vp, i, i, vp]
     L.tel_sur_relu_bwd.argtypes = [vp, vp, vp, ll, vp]
     L.tel_sur_conv3x3_wgrad.argtypes = [vp, vp, vp, vp, i, i, i, i, i, vp]
@@ -265,6 +266,63 @@ class _Plan:
                 a = y
         return a
 
+    def infer(self, x16):
+        """Forward pass for inference (nothing kept for backward): on grids
+        the tensor-memory halo kernel serves, an upsampling is read by the
+        next convolution directly and a skip addition happens in that
+        convolution's epilogue; the result equals forward()'s bit for bit."""
+        net, L, B = self.net, self.net.L, self.B
+        s = _stream()
+        recs = self.recs
+
+        def fusable(h, w):
+            return net.conv != "mma" and w % 128 == 0 and h % 4 == 0
+
+        a = x16
+        saved = {}
+        pending_up = None
+        i = 0
+        while i < len(recs):
+            r = recs[i]
+            kind = r[0]
+            if kind == "conv":
+                _, k, ci, co, relu, h, w, _, y = r
+                nxt = recs[i + 1] if i + 1 < len(recs) else None
+                skip, out = None, y
+                if fusable(h, w) and nxt is not None and nxt[0] == "add":
+                    skip, out = saved[nxt[1]], nxt[5]
+                    i += 1
+                if pending_up is not None or skip is not None:
+                    src = pending_up if pending_up is not None else a
+                    _ok(L.tel_sur_conv3x3_tc_fused(_p(src), _p(net.w16, net.woff[k]), _p(net.w32, net.boff[k]),
+                                                   _p(out), B, h, w, ci, co, relu, 1 if pending_up is not None else 0,
+                                                   _p(skip), _p(net.tc_err), s), "conv3x3 (fused)")
+                    pending_up = None
+                else:
+                    _ok(net.conv3x3(a, net.woff[k], net.w16, _p(net.w32, net.boff[k]), y, B, h, w, ci, co, relu, s),
+                        "conv3x3")
+                a = out
+            elif kind == "pool":
+                _, c, h, w, y = r
+                _ok(L.tel_sur_pool2(_p(a), _p(y), B, h, w, c, s), "pool2")
+                a = y
+            elif kind == "up":
+                _, c, h, w, y = r
+                nxt = recs[i + 1]
+                if nxt[0] == "conv" and fusable(nxt[5], nxt[6]):
+                    pending_up = a  # read through upsampling by the next convolution
+                else:
+                    _ok(L.tel_sur_up2(_p(a), _p(y), B, h, w, c, s), "up2")
+                    a = y
+            elif kind == "save":
+                saved[r[1]] = a
+            elif kind == "add":
+                _, slot, c, h, w, y = r
+                _ok(L.tel_sur_add(_p(a), _p(saved[slot]), _p(y), B * h * w * c, s), "add")
+                a = y
+            i += 1
+        return a
+
     def backward(self, dout):
         net, L, B = self.net, self.net.L, self.B
         s = _stream()
@@ -467,7 +525,7 @@ class Predictor:
     def advance(self, f32, f32_next, mass=True):
         """f32_next = surrogate(f32); self.x16 must hold f32's network input
         (load() or the previous advance).  Also writes the next input."""
-        out = self.net.forward(self.x16, self.B, self.H, self.W)
+        out = self.net.plan(self.B, self.H, self.W).infer(self.x16)
         if mass:
             _ok(self.L.tel_sur_zero(_p(self.mass), 4 * self.B, _stream()), "zero")  # 2B doubles = 4B floats
         _ok(self.L.tel_sur_advance(_p(f32), _p(out), _p(self.scale), _p(f32_next), _p(self.x16),

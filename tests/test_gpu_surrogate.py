@@ -497,3 +497,27 @@ def test_network_with_tcgen05_convolutions_matches_the_warp_level_kernel(H):
     assert int(nets[1].tc_err.item()) == 0
     assert close_bf16(outs[1], outs[0])
     assert np.linalg.norm(grads[1] - grads[0]) <= 2e-2 * np.linalg.norm(grads[0])
+
+
+def test_inference_with_fused_upsampling_and_skip_equals_the_training_forward():
+    """The inference pass (upsampling read by the next convolution, skip
+    addition in its epilogue, on the 256^2 and 128^2 levels) gives the
+    training forward's output bit for bit, and the fused entry point rejects
+    grids its kernel does not serve."""
+    net = S.Net((32, 64, 128), seed=9)
+    g = np.random.default_rng(21)
+    B, H, W = 2, 256, 256
+    x = bf16_values(g, (B, H, W, 16))
+    x[..., 4:] = 0.0
+    x16 = dev_bf16(x)
+    plan = net.plan(B, H, W)
+    ref = host(plan.forward(x16)).copy()
+    got = host(plan.infer(x16))
+    torch.cuda.synchronize()
+    assert int(net.tc_err.item()) == 0
+    assert np.array_equal(got, ref)
+    t = torch.empty(1, device="cuda")
+    assert L.tel_sur_conv3x3_tc_fused(S._p(t), S._p(t), None, S._p(t), 1, 6, 128, 16, 16, 0, 0, None, None,
+                                      s()) == -1  # H not a multiple of 4
+    assert L.tel_sur_conv3x3_tc_fused(S._p(t), S._p(t), None, S._p(t), 1, 8, 64, 16, 16, 0, 0, None, None,
+                                      s()) == -1  # rows narrower than 128
