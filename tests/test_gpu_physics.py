@@ -76,3 +76,122 @@ def test_laplace_law_gpu():
     assert q[0] > q[1] > q[2], q
     assert np.all((q > 0.95) & (q < 1.15)), q
     assert abs(q[-1] - 1.0) < 0.05, q
+
+
+# ---------------------------------------------------------------------------
+# Neumann triangle: a liquid-1 lens on a flat liquid-2/gas interface
+# ---------------------------------------------------------------------------
+def lens_params(T):
+    """Three-phase parameters for which the lens relaxes to rest: density
+    ratio 5, kappa1 = 0.02, kappa2 = kappa3 = 0.5, lambda2 = lambda3 =
+    0.3 kappa, nu = 0.3 (the paper's kappa/lambda ratio runs away here)."""
+    return base(T, kappa1=0.02, kappa2=0.5, kappa3=0.5, lambda2=0.15, lambda3=0.15, nu=0.3, Gamma=1.0,
+                force_form=1)
+
+
+def flat_tensions(p, steps):
+    """sigma_1g, sigma_2g, sigma_12 of relaxed flat binary slabs: the
+    integral of 2 f_I across an interface (two interfaces per periodic box)."""
+    rg, rl = tel.coexistence(A, B, RGAS, p["T"])[:2]
+    chi, Dl = p["chi"], rg - rl
+    Ai = 0.5 * p["kappa1"] + (p["kappa2"] + p["kappa3"]) / (8 * Dl * Dl)
+    Bi = (p["kappa2"] + p["kappa3"]) / (8 * chi * chi)
+    Xi = (p["kappa3"] - p["kappa2"]) / (4 * chi * Dl)
+    x = np.arange(256)
+    s = 0.5 * (np.tanh((x - 64) / 3.0) - np.tanh((x - 192) / 3.0))
+    out = {}
+    for kind in ("1g", "2g", "12"):
+        if kind == "1g":
+            rho, phi = rg + (rl - rg) * s, chi * s
+        elif kind == "2g":
+            rho, phi = rg + (rl - rg) * s, -chi * s
+        else:
+            rho, phi = np.full(256, rl), chi * (2 * s - 1)
+        lat = tel.Lattice(tel.D2Q9, 256, 4, 1, p)
+        lat.init(np.tile(rho, 4), np.tile(phi, 4), np.zeros(2048))
+        lat.step(steps)
+        f = lat.fields()
+        r, ph = f["rho"][:256], f["phi"][:256]
+        gr = (np.roll(r, -1) - np.roll(r, 1)) / 2
+        gp = (np.roll(ph, -1) - np.roll(ph, 1)) / 2
+        out[kind] = 0.5 * np.sum(2 * (Ai * gr ** 2 + Bi * gp ** 2 + Xi * gr * gp))
+    return out
+
+
+def fit_circle(x, y):
+    M = np.c_[2 * x, 2 * y, np.ones_like(x)]
+    (xc, yc, c), *_ = np.linalg.lstsq(M, x * x + y * y, rcond=None)
+    return xc, yc, np.sqrt(c + xc * xc + yc * yc)
+
+
+def lens_angles(fields, p, nx, ny):
+    """Angles of the lens's upper and lower caps with the flat liquid-2/gas
+    interface at the triple point, from circles fitted to the C1 = 1/2
+    contour (the middle 60% of the lens) and the far-field level of C2 = 1/2."""
+    rg, rl = tel.coexistence(A, B, RGAS, p["T"])[:2]
+    R = fields["rho"].reshape(ny, nx)
+    PH = fields["phi"].reshape(ny, nx)
+    Dl = rg - rl
+    C1 = 0.5 * (1 + PH / p["chi"] - (R - rl) / Dl)
+    C2 = 0.5 * (1 - PH / p["chi"] - (R - rl) / Dl)
+    cols = []
+    for xi in range(nx):
+        col = C1[:, xi]
+        inside = np.where(col > 0.5)[0]
+        if len(inside) < 3:
+            continue
+        j0, j1 = inside.min(), inside.max()
+        yb = j0 - 1 + (0.5 - col[j0 - 1]) / (col[j0] - col[j0 - 1])
+        yt = j1 + (col[j1] - 0.5) / (col[j1] - col[j1 + 1])
+        cols.append((xi, yb, yt))
+    cols = np.array(cols)
+    xs = cols[:, 0]
+    xl, xr = xs.min(), xs.max()
+    sel = (xs > xl + 0.2 * (xr - xl)) & (xs < xr - 0.2 * (xr - xl))
+    top, bot = fit_circle(cols[sel, 0], cols[sel, 2]), fit_circle(cols[sel, 0], cols[sel, 1])
+    cg = C2[:, :8].mean(axis=1)
+    j1 = np.where(cg > 0.5)[0].max()
+    yf = j1 + (cg[j1] - 0.5) / (cg[j1] - cg[j1 + 1])
+
+    def angle(circ, upper):
+        xc, yc, r = circ
+        dx = np.sqrt(max(r * r - (yf - yc) ** 2, 0.0))
+        t = np.array([-(yf - yc), dx]) / r
+        if (upper and t[1] < 0) or ((not upper) and t[1] > 0):
+            t = -t
+        return np.degrees(np.arctan2(abs(t[1]), -t[0]))
+
+    return angle(top, True), angle(bot, False)
+
+
+def neumann_angles(s1g, s2g, s12):
+    """Force balance at the triple point, sigma_2g e_x + sigma_1g (-cos a,
+    sin a) + sigma_12 (-cos b, -sin b) = 0, solved for the caps' angles."""
+    S = np.arccos((s2g ** 2 - s1g ** 2 - s12 ** 2) / (2 * s1g * s12))
+    a = np.arctan2(s12 * np.sin(S), s1g + s12 * np.cos(S))
+    return np.degrees(a), np.degrees(S - a)
+
+
+def test_neumann_angles_of_a_liquid_lens_gpu():
+    """A liquid-1 drop placed on the flat interface between liquid 2 and the
+    gas relaxes into a lens whose two caps meet the flat interface at the
+    angles the three measured interfacial tensions fix (Neumann triangle):
+    within 3 degrees (the paper's agreement), with the flow at rest."""
+    T = tel.temperature_for_ratio(A, B, RGAS, 5.0)
+    p = lens_params(T)
+    sig = flat_tensions(p, 10000)
+    nx, ny = 256, 192
+    lat = tel.Lattice(tel.D2Q9, nx, ny, 1, p)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    slab = 0.5 * (np.tanh((Y - 0.25 * ny) / 1.5) - np.tanh((Y - 0.75 * ny) / 1.5))
+    drop = 0.5 * (1 + np.tanh((36.0 - np.hypot(X - nx / 2, Y - 0.75 * ny)) / 1.5))
+    c2 = slab * (1 - drop)
+    rho = lat.rho_g + (lat.rho_l - lat.rho_g) * np.clip(drop + c2, 0, 1)
+    phi = p["chi"] * (drop - c2)
+    lat.init(rho.ravel(), phi.ravel(), np.zeros(2 * nx * ny))
+    lat.step(20000)
+    f = lat.fields()
+    assert np.abs(f["u"]).max() < 5e-3
+    geo = lens_angles(f, p, nx, ny)
+    ref = neumann_angles(sig["1g"], sig["2g"], sig["12"])
+    assert abs(geo[0] - ref[0]) < 3.0 and abs(geo[1] - ref[1]) < 3.0, (geo, ref, sig)
