@@ -405,6 +405,27 @@ def profiled_traffic():
         return None
 
 
+def max_over_ranks(x, world):
+    """The largest of the ranks' values (the job's time is its slowest
+    rank's); a no-op on one rank.  The tensor lives where the process
+    group's backend wants it: on the GPU for NCCL, on the host for gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank, steps, world, seconds):
+    """Whole-job throughput of independent replicas: every rank advances its
+    own lattice, so the job updates world * nodes * steps nodes in the
+    slowest rank's time."""
+    return nodes_per_rank * steps * world / seconds / 1e6
+
+
 def run_gpu(args):
     import torch
     import paper_1710_07486_gb300 as tel
@@ -459,12 +480,9 @@ def run_gpu(args):
         lat.sync()
     except tel.TelError as ex:
         status = f"unstable: {ex}"
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     N = lat.N
-    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+    mlups = job_mlups(N, args.steps, world, ms * 1e-3)
     per_launch_s = ms * 1e-3 / args.steps
     bpu = BYTES_PER_UPDATE[(1, 1)]
     achieved = bpu * N / per_launch_s / 1e9
@@ -492,11 +510,8 @@ def run_gpu(args):
     rc |= L.tel_fields(lat._h, C.c_void_p(o_rho.data_ptr()), C.c_void_p(o_phi.data_ptr()),
                        C.c_void_p(o_u.data_ptr()), None)
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_mlups = N * args.steps * world / e2e_s / 1e6
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_mlups = job_mlups(N, args.steps, world, e2e_s)
     h2d = (2 + 3) * N * 8 / args.steps
     d2h = ((2 + 3) * N * 8 + 4 * args.steps) / args.steps
 

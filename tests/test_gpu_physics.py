@@ -195,3 +195,30 @@ def test_neumann_angles_of_a_liquid_lens_gpu():
     geo = lens_angles(f, p, nx, ny)
     ref = neumann_angles(sig["1g"], sig["2g"], sig["12"])
     assert abs(geo[0] - ref[0]) < 3.0 and abs(geo[1] - ref[1]) < 3.0, (geo, ref, sig)
+
+
+def test_lens_state_parity_with_the_oracle_gpu(orc):
+    """The lens configuration of the Neumann test, 200 steps in FP64, on the
+    GPU and in the oracle: fields within 1e-10 (the full 20000-step
+    relaxation takes the oracle about 20 minutes, so the angles themselves
+    are measured on the GPU)."""
+    T = tel.temperature_for_ratio(A, B, RGAS, 5.0)
+    p = lens_params(T)
+    nx, ny = 256, 192
+    g = tel.Lattice(tel.D2Q9, nx, ny, 1, p)
+    o = orc.Oracle(0, nx, ny, 1, p)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    slab = 0.5 * (np.tanh((Y - 0.25 * ny) / 1.5) - np.tanh((Y - 0.75 * ny) / 1.5))
+    drop = 0.5 * (1 + np.tanh((36.0 - np.hypot(X - nx / 2, Y - 0.75 * ny)) / 1.5))
+    c2 = slab * (1 - drop)
+    rho = (o.rho_g + (o.rho_l - o.rho_g) * np.clip(drop + c2, 0, 1)).ravel()
+    phi = (p["chi"] * (drop - c2)).ravel()
+    u = np.zeros(2 * nx * ny)
+    g.init(rho, phi, u)
+    fo, go = o.init(rho, phi, u)
+    g.step(200)
+    assert o.step(fo, go, 200) == 0
+    a, b = g.fields(), o.fields(fo, go)
+    assert np.max(np.abs(a["rho"] - b["rho"]) / b["rho"]) < 1e-10
+    assert np.max(np.abs(a["phi"] - b["phi"])) / p["chi"] < 1e-10
+    assert np.max(np.abs(a["u"] - b["u"])) < 1e-10 * max(np.abs(b["u"]).max(), 1e-3)
