@@ -226,7 +226,7 @@ def run_c5(args):
     test = good[good >= ntrain]
     sn.good = good[good < ntrain]
     net = S.Net((32, 64, 128), seed=args.seed)
-    tr = S.Trainer(net, sn, B=args.c5_batch, seed=args.seed)
+    tr = S.Trainer(net, sn, B=args.c5_batch, seed=args.seed, clip=args.c5_clip)
     t0 = time.time()
     hist = tr.train(args.c5_iters, lr=args.c5_lr, log_every=max(args.c5_iters // 8, 1))
     torch.cuda.synchronize()
@@ -311,6 +311,7 @@ def run_c5(args):
                                f"k={k} steps per advance", "train_trajectories": int(len(sn.good)),
                    "test_trajectories": int(Bt), "unstable_trajectories": int(sn.bad.sum()),
                    "snapshots": nsnap, "params": net.n, "train_iters": args.c5_iters, "batch": args.c5_batch,
+                   "lr": args.c5_lr, "clip": args.c5_clip,
                    "seed": args.seed},
         "errors": {"one_advance_mean": {"rho": round(float(mean_net[0]), 6), "phi": round(float(mean_net[1]), 6),
                                         "u": round(float(mean_net[2]), 6)},
@@ -625,6 +626,7 @@ def main():
     ap.add_argument("--c5-iters", type=int, default=8000)
     ap.add_argument("--c5-batch", type=int, default=16)
     ap.add_argument("--c5-lr", type=float, default=1e-3)
+    ap.add_argument("--c5-clip", type=float, default=None, help="global gradient-norm clip (none by default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

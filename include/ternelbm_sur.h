@@ -133,6 +133,14 @@ int tel_sur_sums(const float *f32, double *sums, int B, int H, int W, void *stre
 int tel_sur_adam(float *w32, void *w16, const float *g, float *m, float *v, long long n, float lr, float beta1,
                  float beta2, float eps, int t, float grad_scale, void *stream);
 
+/* Gradient-norm clipping without a host round trip: scale[0] (device FP32)
+ * = min(1, clip / ||g||_2) over n values (norm accumulated in FP64 in
+ * work[0], device); tel_sur_adam_scaled is tel_sur_adam with the gradient
+ * multiplied by scale[0] read on the device. */
+int tel_sur_clip_scale(const float *g, long long n, float clip, double *work, float *scale, void *stream);
+int tel_sur_adam_scaled(float *w32, void *w16, const float *g, float *m, float *v, long long n, float lr, float beta1,
+                        float beta2, float eps, int t, const float *scale, void *stream);
+
 /* Zero n FP32 values (cudaMemsetAsync). */
 int tel_sur_zero(float *p, long long n, void *stream);
 

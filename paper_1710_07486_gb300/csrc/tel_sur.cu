@@ -1114,8 +1114,9 @@ __global__ void sums_kernel(const float *__restrict__ f32, double *sums, long lo
 }
 
 __global__ void adam_kernel(float *w32, bf16 *w16, const float *__restrict__ g, float *m, float *v, long long n, float lr,
-                            float b1, float b2, float eps, float c1, float c2, float gs)
+                            float b1, float b2, float eps, float c1, float c2, float gs, const float *gs_dev)
 {
+    if (gs_dev) gs *= *gs_dev;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const float gi = g[e] * gs;
         const float mi = b1 * m[e] + (1.f - b1) * gi;
@@ -1126,6 +1127,20 @@ __global__ void adam_kernel(float *w32, bf16 *w16, const float *__restrict__ g, 
         w32[e] = wi;
         if (w16) w16[e] = __float2bfloat16(wi);
     }
+}
+
+__global__ void sumsq_kernel(const float *__restrict__ g, long long n, double *out)
+{
+    double a = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        a += (double)g[e] * (double)g[e];
+    block_sum_atomic(a, out);
+}
+
+__global__ void clip_scale_kernel(const double *sumsq, float clip, float *scale)
+{
+    const double nrm = sqrt(*sumsq);
+    *scale = nrm > (double)clip ? (float)((double)clip / nrm) : 1.f;
 }
 
 __global__ void to_bf16_kernel(const float *__restrict__ w32, bf16 *w16, long long n)
@@ -1312,7 +1327,29 @@ extern "C" int tel_sur_adam(float *w32, void *w16, const float *g, float *m, flo
     if (n == 0) return TEL_OK;
     const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
     adam_kernel<<<blocks_for(n), 256, 0, S(stream)>>>(w32, (bf16 *)w16, g, m, v, n, lr, beta1, beta2, eps, c1, c2,
-                                                      grad_scale);
+                                                      grad_scale, nullptr);
+    return launched();
+}
+
+extern "C" int tel_sur_clip_scale(const float *g, long long n, float clip, double *work, float *scale, void *stream)
+{
+    if (!g || !work || !scale || n < 1 || !(clip > 0.f)) return TEL_EINVAL;
+    if (cudaMemsetAsync(work, 0, sizeof(double), S(stream)) != cudaSuccess) return TEL_ECUDA;
+    sumsq_kernel<<<blocks_for(n), 256, 0, S(stream)>>>(g, n, work);
+    int rc = launched();
+    if (rc) return rc;
+    clip_scale_kernel<<<1, 1, 0, S(stream)>>>(work, clip, scale);
+    return launched();
+}
+
+extern "C" int tel_sur_adam_scaled(float *w32, void *w16, const float *g, float *m, float *v, long long n, float lr,
+                                   float beta1, float beta2, float eps, int t, const float *scale, void *stream)
+{
+    if (!w32 || !g || !m || !v || !scale || n < 0 || t < 1) return TEL_EINVAL;
+    if (n == 0) return TEL_OK;
+    const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
+    adam_kernel<<<blocks_for(n), 256, 0, S(stream)>>>(w32, (bf16 *)w16, g, m, v, n, lr, beta1, beta2, eps, c1, c2, 1.f,
+                                                      scale);
     return launched();
 }
 

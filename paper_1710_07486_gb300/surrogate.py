@@ -29,7 +29,8 @@ U_REF = 0.1  # velocity normalisation (lattice units)
 SUR_SYMBOLS = ("tel_sur_conv3x3", "tel_sur_conv3x3_tc", "tel_sur_conv3x3_tc_fused", "tel_sur_flip_weights", "tel_sur_relu_bwd", "tel_sur_conv3x3_wgrad",
                "tel_sur_pool2", "tel_sur_pool2_bwd", "tel_sur_up2", "tel_sur_up2_bwd", "tel_sur_add",
                "tel_sur_pack", "tel_sur_unpack", "tel_sur_gather", "tel_sur_loss", "tel_sur_advance",
-               "tel_sur_errors", "tel_sur_sums", "tel_sur_adam", "tel_sur_zero", "tel_sur_to_bf16")
+               "tel_sur_errors", "tel_sur_sums", "tel_sur_adam", "tel_sur_clip_scale", "tel_sur_adam_scaled",
+               "tel_sur_zero", "tel_sur_to_bf16")
 
 
 def sur_lib():
@@ -54,6 +55,8 @@ def sur_lib():
     L.tel_sur_errors.argtypes = [vp, vp, vp, i, i, i, vp]
     L.tel_sur_sums.argtypes = [vp, vp, i, i, i, vp]
     L.tel_sur_adam.argtypes = [vp, vp, vp, vp, vp, ll, f, f, f, f, i, f, vp]
+    L.tel_sur_clip_scale.argtypes = [vp, ll, f, vp, vp, vp]
+    L.tel_sur_adam_scaled.argtypes = [vp, vp, vp, vp, vp, ll, f, f, f, f, i, vp, vp]
     L.tel_sur_zero.argtypes = [vp, ll, vp]
     L.tel_sur_to_bf16.argtypes = [vp, vp, ll, vp]
     for n in SUR_SYMBOLS:
@@ -181,8 +184,20 @@ class Net:
     def zero_grad(self):
         _ok(self.L.tel_sur_zero(_p(self.g), self.n, _stream()), "zero")
 
-    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8, grad_scale=1.0):
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8, grad_scale=1.0, clip=None):
+        """One Adam step; with clip, the gradient is first scaled to a global
+        norm of at most clip (computed and applied on the device)."""
         self.t += 1
+        if clip is not None:
+            if not hasattr(self, "_clip_work"):
+                self._clip_work = self.torch.zeros(1, dtype=self.torch.float64, device="cuda")
+                self._clip_scale = self.torch.ones(1, dtype=self.torch.float32, device="cuda")
+            _ok(self.L.tel_sur_clip_scale(_p(self.g), self.n, float(clip), _p(self._clip_work), _p(self._clip_scale),
+                                          _stream()), "clip_scale")
+            _ok(self.L.tel_sur_adam_scaled(_p(self.w32), _p(self.w16), _p(self.g), _p(self.m), _p(self.v), self.n,
+                                           float(lr), float(b1), float(b2), float(eps), self.t, _p(self._clip_scale),
+                                           _stream()), "adam")
+            return
         _ok(self.L.tel_sur_adam(_p(self.w32), _p(self.w16), _p(self.g), _p(self.m), _p(self.v), self.n,
                                 float(lr), float(b1), float(b2), float(eps), self.t, float(grad_scale),
                                 _stream()), "adam")
@@ -448,7 +463,7 @@ def coex_rho_l(p):
 class Trainer:
     """Adam on the mean squared error of the projected k-step change."""
 
-    def __init__(self, net, snaps, B=8, seed=0, scale=None, augment=True):
+    def __init__(self, net, snaps, B=8, seed=0, scale=None, augment=True, clip=None):
         import torch
         self.net, self.snaps, self.B = net, snaps, B
         self.torch = torch
@@ -464,6 +479,7 @@ class Trainer:
         self.dout = torch.empty((B, H, W, COUT), dtype=torch.bfloat16, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.work = torch.zeros(4 * B, dtype=torch.float32, device=dev)
+        self.clip = clip
         self.idx = torch.empty((3, B), dtype=torch.int32, device=dev)
         self.augment = augment and H == W
         self.rng = np.random.default_rng(seed)
@@ -486,7 +502,7 @@ class Trainer:
         _ok(L.tel_sur_loss(_p(out), _p(self.tgt), _p(self.dout), _p(self.loss), _p(self.work), B, H, W, s), "loss")
         net.zero_grad()
         net.backward(self.dout, B, H, W)
-        net.adam(lr)
+        net.adam(lr, clip=self.clip)
         return self.loss
 
     def train(self, steps, lr=1e-3, lr_min=1e-5, log_every=0):

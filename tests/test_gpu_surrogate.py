@@ -521,3 +521,30 @@ def test_inference_with_fused_upsampling_and_skip_equals_the_training_forward():
                                       s()) == -1  # H not a multiple of 4
     assert L.tel_sur_conv3x3_tc_fused(S._p(t), S._p(t), None, S._p(t), 1, 8, 64, 16, 16, 0, 0, None, None,
                                       s()) == -1  # rows narrower than 128
+
+
+def test_gradient_clipping_scale_and_scaled_adam_against_oracle():
+    """scale = min(1, clip/||g||) computed on the device, then the Adam step
+    with the scaled gradient, against the oracle's Adam on the scaled
+    gradient (clipping active and inactive)."""
+    g = np.random.default_rng(17)
+    n = 3000
+    for clip in (0.5, 1e6):
+        w = g.normal(size=n)
+        gr = (g.normal(size=n) * 0.1).astype(np.float32)
+        wd = torch.from_numpy(w.astype(np.float32)).cuda()
+        md = torch.zeros(n, dtype=torch.float32, device="cuda")
+        vd = torch.zeros(n, dtype=torch.float32, device="cuda")
+        gd = torch.from_numpy(gr).cuda()
+        work = torch.zeros(1, dtype=torch.float64, device="cuda")
+        sc = torch.zeros(1, dtype=torch.float32, device="cuda")
+        assert L.tel_sur_clip_scale(S._p(gd), n, clip, S._p(work), S._p(sc), s()) == 0
+        assert L.tel_sur_adam_scaled(S._p(wd), None, S._p(gd), S._p(md), S._p(vd), n, 1e-2, 0.9, 0.999, 1e-8, 1,
+                                     S._p(sc), s()) == 0
+        torch.cuda.synchronize()
+        nrm = np.linalg.norm(gr.astype(np.float64))
+        want = min(1.0, clip / nrm)
+        assert sc.item() == pytest.approx(want, rel=1e-6)
+        wr, _, _ = so.adam(w.astype(np.float32).astype(np.float64), gr.astype(np.float64) * want, np.zeros(n),
+                           np.zeros(n), 1, 1e-2)
+        assert np.max(np.abs(wd.cpu().numpy() - wr)) <= 1e-5 * np.abs(wr).max()
