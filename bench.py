@@ -226,7 +226,7 @@ def run_c5(args):
     test = good[good >= ntrain]
     sn.good = good[good < ntrain]
     net = S.Net((32, 64, 128), seed=args.seed)
-    tr = S.Trainer(net, sn, B=args.c5_batch, seed=args.seed, clip=args.c5_clip)
+    tr = S.Trainer(net, sn, B=args.c5_batch, seed=args.seed, clip=args.c5_clip if args.c5_clip > 0 else None)
     t0 = time.time()
     hist = tr.train(args.c5_iters, lr=args.c5_lr, log_every=max(args.c5_iters // 8, 1))
     torch.cuda.synchronize()
@@ -327,7 +327,7 @@ def run_c5(args):
                    "data_s": round(t_data, 2), "train_s": round(t_train, 2),
                    "train_ms_per_iter": round(1e3 * t_train / max(args.c5_iters, 1), 3)},
         "loss": [[i, round(l, 6)] for i, l in hist],
-        "gpu_launches": None,
+        "gpu_launches": pr.launches * args.steps,
     }
     print(json.dumps(line), flush=True)
 
@@ -619,14 +619,14 @@ def main():
                          "c5: learned surrogate (train + evaluate)")
     ap.add_argument("--c4-cases", type=int, default=256)
     ap.add_argument("--c5-n", type=int, default=256)
-    ap.add_argument("--c5-k", type=int, default=25)
-    ap.add_argument("--c5-snaps", type=int, default=40)
-    ap.add_argument("--c5-train-traj", type=int, default=96)
+    ap.add_argument("--c5-k", type=int, default=50)
+    ap.add_argument("--c5-snaps", type=int, default=24)
+    ap.add_argument("--c5-train-traj", type=int, default=192)
     ap.add_argument("--c5-test-traj", type=int, default=16)
-    ap.add_argument("--c5-iters", type=int, default=8000)
-    ap.add_argument("--c5-batch", type=int, default=16)
-    ap.add_argument("--c5-lr", type=float, default=1e-3)
-    ap.add_argument("--c5-clip", type=float, default=None, help="global gradient-norm clip (none by default)")
+    ap.add_argument("--c5-iters", type=int, default=16000)
+    ap.add_argument("--c5-batch", type=int, default=32)
+    ap.add_argument("--c5-lr", type=float, default=5e-4)
+    ap.add_argument("--c5-clip", type=float, default=0.2, help="global gradient-norm clip (<= 0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

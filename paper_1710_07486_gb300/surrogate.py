@@ -296,6 +296,7 @@ class _Plan:
         a = x16
         saved = {}
         pending_up = None
+        self.launches = 0  # kernels issued by this pass (one per library call below)
         i = 0
         while i < len(recs):
             r = recs[i]
@@ -309,16 +310,19 @@ class _Plan:
                     i += 1
                 if pending_up is not None or skip is not None:
                     src = pending_up if pending_up is not None else a
+                    self.launches += 1
                     _ok(L.tel_sur_conv3x3_tc_fused(_p(src), _p(net.w16, net.woff[k]), _p(net.w32, net.boff[k]),
                                                    _p(out), B, h, w, ci, co, relu, 1 if pending_up is not None else 0,
                                                    _p(skip), _p(net.tc_err), s), "conv3x3 (fused)")
                     pending_up = None
                 else:
+                    self.launches += 1
                     _ok(net.conv3x3(a, net.woff[k], net.w16, _p(net.w32, net.boff[k]), y, B, h, w, ci, co, relu, s),
                         "conv3x3")
                 a = out
             elif kind == "pool":
                 _, c, h, w, y = r
+                self.launches += 1
                 _ok(L.tel_sur_pool2(_p(a), _p(y), B, h, w, c, s), "pool2")
                 a = y
             elif kind == "up":
@@ -327,12 +331,14 @@ class _Plan:
                 if nxt[0] == "conv" and fusable(nxt[5], nxt[6]):
                     pending_up = a  # read through upsampling by the next convolution
                 else:
+                    self.launches += 1
                     _ok(L.tel_sur_up2(_p(a), _p(y), B, h, w, c, s), "up2")
                     a = y
             elif kind == "save":
                 saved[r[1]] = a
             elif kind == "add":
                 _, slot, c, h, w, y = r
+                self.launches += 1
                 _ok(L.tel_sur_add(_p(a), _p(saved[slot]), _p(y), B * h * w * c, s), "add")
                 a = y
             i += 1
@@ -541,7 +547,9 @@ class Predictor:
     def advance(self, f32, f32_next, mass=True):
         """f32_next = surrogate(f32); self.x16 must hold f32's network input
         (load() or the previous advance).  Also writes the next input."""
-        out = self.net.plan(self.B, self.H, self.W).infer(self.x16)
+        plan = self.net.plan(self.B, self.H, self.W)
+        out = plan.infer(self.x16)
+        self.launches = plan.launches + 2  # the head's sums and the advance kernel
         if mass:
             _ok(self.L.tel_sur_zero(_p(self.mass), 4 * self.B, _stream()), "zero")  # 2B doubles = 4B floats
         _ok(self.L.tel_sur_advance(_p(f32), _p(out), _p(self.scale), _p(f32_next), _p(self.x16),
