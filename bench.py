@@ -84,6 +84,23 @@ def workload_c4(seed, ncases=256):
     return cases
 
 
+def c4_setup(cases):
+    """Shapes, parameters and initial fields of the batched cases."""
+    import paper_1710_07486_gb300 as tel
+    from paper_1710_07486_gb300 import inputs
+    shapes, plist, fields = [], [], []
+    for w in cases:
+        T = tel.temperature_for_ratio(A_, B_, R_, w["ratio"])
+        rho_g, rho_l = tel.coexistence(A_, B_, R_, T)[:2]
+        R = w["n"] / 8.0
+        p, V, _ = c3_params(w, T, rho_g, rho_l, R=R)
+        p["precision"] = tel.FP32_SHIFTED
+        shapes.append((w["n"], w["n"]))
+        plist.append(p)
+        fields.append(inputs.off_centre_2d(w["n"], rho_g, rho_l, p["chi"], V, w["B"], R, width=10.0))
+    return shapes, plist, fields
+
+
 def run_c4(args):
     """Batched D2Q9 cases: one persistent launch per step over all cases,
     against the same cases advanced one lattice after another."""
@@ -93,16 +110,7 @@ def run_c4(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     cases = workload_c4(args.seed, args.c4_cases)
-    shapes, plist, fields = [], [], []
-    for k, w in enumerate(cases):
-        T = tel.temperature_for_ratio(A_, B_, R_, w["ratio"])
-        rho_g, rho_l = tel.coexistence(A_, B_, R_, T)[:2]
-        R = w["n"] / 8.0
-        p, V, _ = c3_params(w, T, rho_g, rho_l, R=R)
-        p["precision"] = tel.FP32_SHIFTED
-        shapes.append((w["n"], w["n"]))
-        plist.append(p)
-        fields.append(inputs.off_centre_2d(w["n"], rho_g, rho_l, p["chi"], V, w["B"], R, width=10.0))
+    shapes, plist, fields = c4_setup(cases)
     N = sum(a * b for a, b in shapes)
     stream = torch.cuda.Stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

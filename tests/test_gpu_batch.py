@@ -145,3 +145,26 @@ def test_batch_errors():
     b.init(1, np.full(192, rl), np.zeros(192), np.zeros(384))
     b.step(2)
     b.sync()
+
+
+def test_batch_full_workload_against_single_lattices():
+    """The batched benchmark's full workload (256 cases, 2.5e7 nodes) after
+    the tuner and two more steps: the largest, the smallest and two random
+    cases against single lattices advanced by the same number of steps."""
+    import bench
+    cases = bench.workload_c4(1710, 256)
+    shapes, plist, fields = bench.c4_setup(cases)
+    b = tel.Batch(shapes, plist)
+    for c, (rho, phi, u) in enumerate(fields):
+        b.init(c, rho, phi, u)
+    done = b.tune(1)[2]
+    b.step(2)
+    b.sync()
+    sizes = [x * y for x, y in shapes]
+    pick = {int(np.argmax(sizes)), int(np.argmin(sizes)), 17, 200}
+    for c in sorted(pick):
+        s = tel.Lattice(tel.D2Q9, shapes[c][0], shapes[c][1], 1, plist[c])
+        s.init(*fields[c])
+        s.step(done + 2)
+        got, ref = b.fields(c), s.fields()
+        assert close_fp32(got, ref), (c, errs(got, ref))
