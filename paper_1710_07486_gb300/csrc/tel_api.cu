@@ -324,11 +324,16 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
     d.inv_rho_g = 1.0 / co[0];
     d.inv_rho_g_f = (float)d.inv_rho_g;
     {
-        const double dg = p.b * co[0] - 4.0;
-        d.h_g = (24.0 - 2.0 * p.b * co[0]) / (dg * dg * dg);
         d.gRT = d.lam1h * d.RT;
-        d.gRT8 = d.lam1h * 8.0 * d.RT;
-        d.ga2 = d.lam1h * 2.0 * p.a;
+        d.rg_hi = (float)co[0];
+        d.rg_lo = (float)(co[0] - (double)d.rg_hi);
+        d.b_f = (float)p.b;
+        const double q = 1.0 / (p.b * co[0] - 4.0);
+        d.q_g = (float)q;
+        d.q_g2 = (float)(q * q);
+        d.q_g_x2 = (float)(2.0 * q);
+        d.gRT8b_f = (float)(d.lam1h * 8.0 * d.RT * p.b);
+        d.ga2_f = (float)(d.lam1h * 2.0 * p.a);
     }
     const double tau = 3.0 * p.nu + 0.5;
     d.beta = 1.0 / (2.0 * tau);

@@ -68,9 +68,13 @@ struct DevParams {
     double AI, BI, XI;                // f_I = AI |grad rho|^2 + BI |grad phi|^2 + XI grad rho.grad phi
     double rho_switch;                // FP32 mode: gas side is rho < rho_switch
     double inv_rho_g;                 // 1/rho_g
-    double h_g;                       // (24 - 2 b rho_g)/(b rho_g - 4)^3
-    double gRT, gRT8, ga2;            // lambda1/2 times RT, 8 RT, 2a (gas-side chemical potential)
-    float inv_rho_g_f;                // 1/rho_g in FP32
+    double gRT;                       // lambda1/2 times RT (gas-side chemical potential)
+    // FP32 constants of the gas-side chemical potential (mu_eos_gas)
+    float inv_rho_g_f;                // 1/rho_g
+    float rg_hi, rg_lo;               // rho_g = rg_hi + rg_lo, two floats
+    float b_f;                        // b
+    float q_g, q_g2, q_g_x2;          // q = 1/(b rho_g - 4), q^2, 2q
+    float gRT8b_f, ga2_f;             // lambda1/2 times 8 RT b and 2a
     // collision
     double beta, inv_beta;            // beta = 1/(2 tau)
     double c_gb;                      // 2 beta - 1: beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh>
@@ -134,16 +138,6 @@ __device__ __forceinline__ int map_coord(int q, int n, int wall)
 template <typename T> __device__ __forceinline__ T sqrt_(T x);
 template <> __device__ __forceinline__ double sqrt_<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float sqrt_<float>(float x) { return sqrtf(x); }
-// s + c += v with Knuth's error-free two-sum (no reassociation, no FMA).
-template <typename T>
-__device__ __forceinline__ void two_sum_acc(T &s, T &c, T v)
-{
-    const T t = s + v;
-    const T bp = t - s;
-    c += (s - (t - bp)) + (v - bp);
-    s = t;
-}
-
 // Pairs and quads of the compute type.  In FP32, pair arithmetic uses the
 // packed FP32x2 instructions of sm_100+ (__ffma2_rn, __fadd2_rn).
 template <typename T> struct Vec;
@@ -164,6 +158,20 @@ template <> struct Vec<double> {
     __device__ static __forceinline__ v2 add(v2 a, v2 b) { return make_double2(a.x + b.x, a.y + b.y); }
     __device__ static __forceinline__ v4 quad(double a, double b, double c, double d) { v4 q; q.x = a; q.y = b; q.z = c; q.w = d; return q; }
 };
+
+// Packed FP32x2 arithmetic (sm_100+): one instruction for two lanes.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "sub.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
 template <typename T> __device__ __forceinline__ T log_(T x);
 template <> __device__ __forceinline__ double log_<double>(double x) { return log(x); }
@@ -213,29 +221,54 @@ __device__ __forceinline__ void mu_wells(const DevParams &P, T rho, T phi, T &mr
 }
 
 // FP32-storage mode, gas side (rho < rho_switch): the equation-of-state part
-// of mu_rho in FP64 from its difference to the gas coexistence point, where
+// of mu_rho from its difference to the gas coexistence point, where
 // mu_coex = dPsi~/drho(rho_g):
-//   dPsi~(rho) - dPsi~(rho_g) = RT ln(rho/rho_g) - 8RT (h(rho) - h(rho_g)) - 2a (rho - rho_g),
-//   h(rho) = (24 - 2 b rho)/(b rho - 4)^3.
-// ln(rho/rho_g) = log1p((rho - rho_g)/rho_g) is well conditioned in FP32; the
-// rational difference and the combination are FP64, with 1/(b rho - 4)^3 from
-// an FP32 reciprocal refined by two Newton-Raphson steps in FP64
-// (r <- r (2 - d r), relative error ~1e-16).
+//   dPsi~(rho) - dPsi~(rho_g) = RT ln(rho/rho_g) - 8RT (h(rho) - h(rho_g)) - 2a D,
+//   D = rho - rho_g,  h(rho) = (24 - 2 b rho)/(b rho - 4)^3 = 16 r^3 - 2 r^2,
+//   r = 1/(b rho - 4).
+// Every piece is proportional to D and is evaluated without cancellation:
+//  - D from rho_g split into two floats (near rho_g the first subtraction is
+//    exact by Sterbenz's lemma);
+//  - ln(rho/rho_g) = log1p(D/rho_g);
+//  - with q = 1/(b rho_g - 4), r - q = -b D r q and
+//    h(rho) - h(rho_g) = (r - q) [16 (r^2 + r q + q^2) - 2 (r + q)] = -b D B,
+//    B = 2 r q [8 (r^2 + r q + q^2) - (r + q)], a sum of terms of one sign
+//    (r, q < 0 for b rho < 4).
+// So the result is (lambda1/2) [RT ln(rho/rho_g) + D (8RT b B - 2a)], whose
+// two products are added in FP64.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// 1/x from the approximate reciprocal and one Newton-Raphson step, r (2 - x r):
+// within about one ulp.
+__device__ __forceinline__ float rcp_nr(float x)
+{
+    const float r = rcp_approx(x);
+    return fmaf(r, fmaf(-x, r, 1.f), r);
+}
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <typename T> __device__ __forceinline__ T inv_(T x);
+template <> __device__ __forceinline__ double inv_<double>(double x) { return 1.0 / x; }
+template <> __device__ __forceinline__ float inv_<float>(float x) { return rcp_nr(x); }
+
 __device__ __forceinline__ float mu_eos_gas(const DevParams &P, float rho)
 {
-    const double t = (double)rho;
-    const double dg = t - P.rho_g;  // exact: the cancellation happens here, in FP64
-    // ln(rho/rho_g) = log1p(dg/rho_g), well conditioned: FP32 suffices
-    const float L = log1pf((float)dg * P.inv_rho_g_f);
-    const double d = fma(P.b, t, -4.0);
-    const double d3 = d * d * d;
-    // FP32 seed (relative error ~2^-23) and one Newton-Raphson step in FP64:
-    // ~2^-46, far below the FP32 logarithm's share of the result
-    double r = (double)__frcp_rn((float)d3);
-    r = r * fma(-d3, r, 2.0);
-    const double h = fma(-2.0, d, 16.0) * r;  // (24 - 2 b rho)/(b rho - 4)^3
-    // (lambda1/2) [RT L - 8RT (h - h_g) - 2a dg], coefficients premultiplied
-    return (float)fma(P.gRT, (double)L, fma(-P.gRT8, h - P.h_g, -P.ga2 * dg));
+    const float D = (rho - P.rg_hi) - P.rg_lo;
+    const float L = log1pf(D * P.inv_rho_g_f);
+    const float r = rcp_nr(fmaf(P.b_f, rho, -4.f));
+    const float rq = r + P.q_g;
+    const float B = (P.q_g_x2 * r) * fmaf(8.f, fmaf(r, rq, P.q_g2), -rq);
+    const float c = fmaf(P.gRT8b_f, B, -P.ga2_f);
+    return (float)fma(P.gRT, (double)L, (double)D * (double)c);
 }
 
 // Bulk free energy f_B of Eq. 2 (Psi_eos - Psi_0 with the common tangent).
@@ -274,6 +307,19 @@ __device__ __forceinline__ void eq_factors(T u, T e[3])
     e[0] = (T)(1.0 / 6.0) * t * (S - (T)2 * u) / ((T)1 + u);
 }
 
+// FP32 form of eq_factors for the FP32-storage step: S from the approximate
+// square root; 1/(1 - u) = (1 + u)/(1 - u^2) and 1/(1 + u) = (1 - u)/(1 - u^2)
+// from one refined reciprocal.
+__device__ __forceinline__ void eq_factors_f(float u, float e[3])
+{
+    const float S = sqrt_approx(fmaf(3.f * u, u, 1.f));
+    const float t = 2.f - S;
+    const float r = rcp_nr(fmaf(-u, u, 1.f)) * ((1.f / 6.f) * t);
+    e[1] = (2.f / 3.f) * t;
+    e[2] = (S + 2.f * u) * (1.f + u) * r;
+    e[0] = (S - 2.f * u) * (1.f - u) * r;
+}
+
 template <typename ST> struct StoreTraits;
 template <> struct StoreTraits<double> { typedef double CT; static constexpr bool shifted = false; };
 template <> struct StoreTraits<float> { typedef float CT; static constexpr bool shifted = true; };
@@ -305,8 +351,11 @@ struct Fused {
     static constexpr int OFF_RP = 0;                         // pairs [RS][NA]
     static constexpr int OFF_MU = OFF_RP + 2 * RS * NA;      // pairs [MS][NB]
     static constexpr int OFF_G = OFF_MU + 2 * MS * NB;       // quads [MS][NB]
-    static constexpr int OFF_F = OFF_G + 4 * MS * NB;        // per-thread population stash [Q][NT]
-    static constexpr int SMEM_ELEMS = OFF_F + (MODE == MODE_STEP ? Q * NT : 0);
+    static constexpr int OFF_F = OFF_G + 4 * MS * NB;        // per-thread population stash
+    // FP64 storage: [Q][NT] pulled populations.  FP32 storage: [REST][NT]
+    // pairs of pulled populations (the rest population stays in a register).
+    static constexpr int STASH = StoreTraits<ST>::shifted ? 2 * L::REST * NT : Q * NT;
+    static constexpr int SMEM_ELEMS = OFF_F + (MODE == MODE_STEP ? STASH : 0);
     static constexpr size_t SMEM_BYTES = sizeof(CT) * SMEM_ELEMS;
 
     __device__ static __forceinline__ int idx2(int ox, int oy) { return (ox + 2) + R2X * (oy + OY2); }
@@ -472,7 +521,7 @@ struct Fused {
                     mu_s[sB * NB + s] = V::pair(mr - coef<CT>(P).Kr * lr - coef<CT>(P).Kx * lp,
                                                 mp - coef<CT>(P).Kp * lp - coef<CT>(P).Kx * lr);
                     if (P.force_form == 1)  // grad rho and c_s^4/(4 rho) (lattice-consistent force)
-                        g_s[sB * NB + s] = V::quad((CT)3 * gx, (CT)3 * gy, (CT)3 * gz, (CT)(1.0 / 36.0) / r0);
+                        g_s[sB * NB + s] = V::quad((CT)3 * gx, (CT)3 * gy, (CT)3 * gz, (CT)(1.0 / 36.0) * inv_<CT>(r0));
                 }
             }
             __syncthreads();
@@ -481,15 +530,16 @@ struct Fused {
                 const int tx = tid % TX, ty = tid / TX;
                 const int x = x0 + tx, y = y0 + ty;
                 if (x < PX && (D == 2 || y < PY))
-                    node(P, A, fs, gs, rp_s, mu_s, g_s, sm + OFF_F + tid, x, y, mC, tx, ty);
+                    node(P, A, fs, gs, rp_s, mu_s, g_s, sm + OFF_F, x, y, mC, tx, ty);
             }
         }
     }
 
     __device__ static void node(const DevParams &P, const LaunchArgs &A, const ST *fs, const ST *gs,
-                                const V2 *rp_s, const V2 *mu_s, const V4 *g_s, CT *fq, int x, int y, int m,
+                                const V2 *rp_s, const V2 *mu_s, const V4 *g_s, CT *stash, int x, int y, int m,
                                 int tx, int ty)
     {
+        CT *fq = stash + (tx + TX * ty);  // this thread's column of the population stash
         const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
         const long long n = (long long)x + (long long)PX * ((long long)y + (long long)PY * m);
         const int ox = tx, oy = (D == 3 ? ty : 0);
@@ -579,20 +629,23 @@ struct Fused {
             init_node(P, A, n, x, y, m, rho, phi, mu_phi, F);
             return;
         }
+        if constexpr (StoreTraits<ST>::shifted && MODE == MODE_STEP) {
+            collide_pairs(P, A, fs, gs, reinterpret_cast<float2 *>(stash) + (tx + TX * ty), n, x, y, m, rho, phi,
+                          mu_phi, F);
+            return;
+        }
 
         // ---- pull f: momentum and second moments.  The pulled populations
         // are kept in this thread's column of shared memory (fq[i * NT]) for
         // the two later passes instead of 27 registers.
         Nbr nb;
         make_nbr(P, PX, PY, PM, x, y, m, nb);
-        CT fsum = 0;  // same summation order as phase A: equals rho - rho_ref
         CT j[3] = {0, 0, 0};
         CT Pi[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const CT fi = pull(fs, nb, P.N, i);
             if (MODE == MODE_STEP) fq[i * NT] = fi;
-            fsum += fi;
             if (L::cx(i)) { j[0] += (CT)L::cx(i) * fi; Pi[0] += fi; }
             if (L::cy(i)) { j[1] += (CT)L::cy(i) * fi; Pi[1] += fi; }
             if (D == 3 && L::cz(i)) { j[2] += (CT)L::cz(i) * fi; Pi[2] += fi; }
@@ -617,143 +670,329 @@ struct Fused {
             return;
         }
 
-        // ---- phase field first (its pulls reuse the offsets just computed):
-        // BGK towards g^eq(phi, mu_phi, u_phys)
-        CT up[3] = {0, 0, 0};
-        CT uu = 0;
+        if constexpr (!StoreTraits<ST>::shifted) {
+            // ---- FP64 storage, step mode.  Phase field first (its pulls reuse
+            // the offsets just computed): BGK towards g^eq(phi, mu_phi, u_phys)
+            CT up[3] = {0, 0, 0};
+            CT uu = 0;
 #pragma unroll
-        for (int a = 0; a < D; ++a) { up[a] = (j[a] + (CT)0.5 * F[a]) / rho; uu += up[a] * up[a]; }
-        const CT Gm3 = K.Gamma3 * mu_phi;
-        // sum of g^eq over the moving velocities, by lattice isotropy
-        // (sum_{i != 0} w_i = 1 - w_0, sum w_i (c_i.u)^2 = u.u/3)
-        const CT w0 = (CT)L::w(L::REST);
-        const CT others = ((CT)1 - w0) * Gm3 + (CT)1.5 * w0 * phi * uu;
-        const CT itg = K.inv_tau_g;
-        ST *gd = reinterpret_cast<ST *>(A.gdst);
-        CT goth = 0;
-        // opposite velocities (i, Q-1-i) share w_i and the even part of g^eq;
-        // c.u changes sign: g^eq = even +- odd
+            for (int a = 0; a < D; ++a) { up[a] = (j[a] + (CT)0.5 * F[a]) / rho; uu += up[a] * up[a]; }
+            const CT Gm3 = K.Gamma3 * mu_phi;
+            // sum of g^eq over the moving velocities, by lattice isotropy
+            // (sum_{i != 0} w_i = 1 - w_0, sum w_i (c_i.u)^2 = u.u/3)
+            const CT w0 = (CT)L::w(L::REST);
+            const CT others = ((CT)1 - w0) * Gm3 + (CT)1.5 * w0 * phi * uu;
+            const CT itg = K.inv_tau_g;
+            ST *gd = reinterpret_cast<ST *>(A.gdst);
+            // opposite velocities (i, Q-1-i) share w_i and the even part of g^eq;
+            // c.u changes sign: g^eq = even +- odd
 #pragma unroll
-        for (int i = 0; i < L::REST; ++i) {
-            const int io = Q - 1 - i;
-            CT cu = 0;
+            for (int i = 0; i < L::REST; ++i) {
+                const int io = Q - 1 - i;
+                CT cu = 0;
 #pragma unroll
-            for (int a = 0; a < D; ++a)
-                if (L::c(i, a)) cu += (CT)L::c(i, a) * up[a];
-            const CT wi = (CT)L::w(i);
-            const CT even = wi * (Gm3 + phi * ((CT)4.5 * cu * cu - (CT)1.5 * uu));
-            const CT odd = wi * (CT)3 * phi * cu;
-            const CT gi = pull(gs, nb, P.N, i), gio = pull(gs, nb, P.N, io);
-            const CT go = gi - (gi - (even + odd)) * itg;
-            const CT goo = gio - (gio - (even - odd)) * itg;
-            if (StoreTraits<ST>::shifted) goth += (CT)(ST)go + (CT)(ST)goo;
-            gd[(long long)i * P.N + n] = (ST)go;
-            gd[(long long)io * P.N + n] = (ST)goo;
-        }
-        if (StoreTraits<ST>::shifted) {
-            // FP32 storage: the rest population closes the node's phase-field sum
-            gd[(long long)L::REST * P.N + n] = (ST)(phi - goth);
-        } else {
-            const CT gi = pull(gs, nb, P.N, L::REST);
-            gd[(long long)L::REST * P.N + n] = (ST)(gi - (gi - (phi - others)) * itg);
-        }
+                for (int a = 0; a < D; ++a)
+                    if (L::c(i, a)) cu += (CT)L::c(i, a) * up[a];
+                const CT wi = (CT)L::w(i);
+                const CT even = wi * (Gm3 + phi * ((CT)4.5 * cu * cu - (CT)1.5 * uu));
+                const CT odd = wi * (CT)3 * phi * cu;
+                const CT gi = pull(gs, nb, P.N, i), gio = pull(gs, nb, P.N, io);
+                gd[(long long)i * P.N + n] = gi - (gi - (even + odd)) * itg;
+                gd[(long long)io * P.N + n] = gio - (gio - (even - odd)) * itg;
+            }
+            {
+                const CT gi = pull(gs, nb, P.N, L::REST);
+                gd[(long long)L::REST * P.N + n] = gi - (gi - (phi - others)) * itg;
+            }
 
-        CT uF[3] = {0, 0, 0};
+            CT uF[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                uF[a] = u[a] + F[a] / rho;
+                if (!(fabs(u[a]) < (CT)1) || !(fabs(uF[a]) < (CT)1)) bad |= ERR_VEL;
+            }
+            // equilibrium factors at u and at u + F/rho
+            CT e[3][3], eF[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a < D) { eq_factors<CT>(u[a], e[a]); eq_factors<CT>(uF[a], eF[a]); }
+                else { e[a][0] = 0; e[a][1] = 1; e[a][2] = 0; eF[a][0] = 0; eF[a][1] = 1; eF[a][2] = 0; }
+            }
+            // second moments of f^eq from the factor moments M0 = sum e, M1 = sum c e, M2 = sum c^2 e
+            CT M0[3], M1[3], M2[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                M0[a] = e[a][0] + e[a][1] + e[a][2];
+                M1[a] = e[a][2] - e[a][0];
+                M2[a] = e[a][2] + e[a][0];
+            }
+            CT dPi[6];
+            dPi[0] = Pi[0] - rho * M2[0] * M0[1] * M0[2];
+            dPi[1] = Pi[1] - rho * M0[0] * M2[1] * M0[2];
+            dPi[2] = (D == 3) ? Pi[2] - rho * M0[0] * M0[1] * M2[2] : (CT)0;
+            dPi[3] = Pi[3] - rho * M1[0] * M1[1] * M0[2];
+            dPi[4] = (D == 3) ? Pi[4] - rho * M1[0] * M0[1] * M1[2] : (CT)0;
+            dPi[5] = (D == 3) ? Pi[5] - rho * M0[0] * M1[1] * M1[2] : (CT)0;
+            const CT tr = dPi[0] + dPi[1] + dPi[2];
+            const CT dev[3] = {dPi[0] - tr / (CT)D, dPi[1] - tr / (CT)D, dPi[2] - tr / (CT)D};
+
+            // entropic scalar products <ds|dh>, <dh|dh> (weights 1/f^eq)
+            CT sh = 0, hh = 0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const CT fi = fq[i * NT];
+                const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
+                const CT ds = ds_of(i, dev, dPi);
+                const CT dh = fi - feq - ds;
+                const CT r = (CT)1 / feq;
+                // <ds|dh> has terms only where ds != 0 (one or two non-zero components of c_i)
+                if (L::nnz(i) == 1 || L::nnz(i) == 2) sh += ds * dh * r;
+                hh += dh * dh * r;
+            }
+            // stabiliser gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>, applied
+            // as beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh> (gamma = 2, i.e.
+            // beta gamma = 2 beta, when <dh|dh> vanishes)
+            const CT gb = hh > (CT)1e-30 * rho * rho ? (CT)1 - (CT)P.c_gb * (sh / hh) : (CT)2 * K.beta;
+            const CT bet = K.beta;
+            if (!isfinite(gb)) bad |= ERR_NAN;
+            ST *fd = reinterpret_cast<ST *>(A.fdst);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const CT fi = fq[i * NT];
+                const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
+                const CT feqF = rho * eF[0][L::cx(i) + 1] * eF[1][L::cy(i) + 1] * eF[2][L::cz(i) + 1];
+                const CT ds = ds_of(i, dev, dPi);
+                const CT dh = fi - feq - ds;
+                fd[(long long)i * P.N + n] = fi - ((CT)2 * bet * ds + gb * dh) + (feqF - feq);
+            }
+            if (bad) atomicOr(P.err, bad);
+        }
+    }
+
+    // FP32 storage, step mode: the collision of one node over the pairs of
+    // opposite velocities (k, Q-1-k), k < REST, in packed FP32x2 arithmetic.
+    // The two members of a pair share w_i and Delta s_i; their equilibria are
+    // the same products of the one-dimensional factors with c reversed, their
+    // g equilibria differ in the sign of c.u, and they enter the odd moments
+    // through their difference and the even moments through their sum.
+    // The pulled pairs are kept in this thread's column of shared memory
+    // (stash2[k NT]) for the gamma and output passes.
+    __device__ static void collide_pairs(const DevParams &P, const LaunchArgs &A, const ST *fs, const ST *gs,
+                                         float2 *stash2, long long n, int x, int y, int m, float rho, float phi,
+                                         float mu_phi, const float F[3])
+    {
+        constexpr int NP = L::REST;
+        const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
+        const Coef<float> &K = P.cf;
+        const float shift = K.rho_ref;
+        Nbr nb;
+        make_nbr(P, PX, PY, PM, x, y, m, nb);
+        auto didx = [&](int i) -> long long {
+            if (FAST) return (long long)((unsigned)i * (unsigned)P.N + (unsigned)n);
+            return (long long)i * P.N + n;
+        };
+
+        // ---- pull f: mass, momentum and second moments
+        const float f0 = pull(fs, nb, P.N, L::REST);
+        float fsum = 0.f;
+        float j[3] = {0.f, 0.f, 0.f};
+        float Pi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx yy zz xy xz yz
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float fa = pull(fs, nb, P.N, k), fb = pull(fs, nb, P.N, Q - 1 - k);
+            stash2[k * NT] = make_float2(fa, fb);
+            const float sp = fa + fb, dp = fa - fb;
+            fsum += sp;
+            if (L::cx(k)) { j[0] += (float)L::cx(k) * dp; Pi[0] += sp; }
+            if (L::cy(k)) { j[1] += (float)L::cy(k) * dp; Pi[1] += sp; }
+            if (D == 3 && L::cz(k)) { j[2] += (float)L::cz(k) * dp; Pi[2] += sp; }
+            if (L::cx(k) * L::cy(k)) Pi[3] += (float)(L::cx(k) * L::cy(k)) * sp;
+            if (D == 3 && L::cx(k) * L::cz(k)) Pi[4] += (float)(L::cx(k) * L::cz(k)) * sp;
+            if (D == 3 && L::cy(k) * L::cz(k)) Pi[5] += (float)(L::cy(k) * L::cz(k)) * sp;
+        }
+        fsum += f0;  // rho - rho_ref as pulled
+        const float cs2 = 1.f / 3.f;
+        // the shift w_i rho_ref adds rho_ref c_s^2 to each diagonal second moment
+        Pi[0] = fmaf(shift, cs2, Pi[0]);
+        Pi[1] = fmaf(shift, cs2, Pi[1]);
+        if (D == 3) Pi[2] = fmaf(shift, cs2, Pi[2]);
+
+        unsigned bad = 0;
+        if (!(rho > 0.f)) bad |= ERR_RHO;
+        const float ir = rcp_nr(rho);
+        float u[3] = {0.f, 0.f, 0.f}, up[3] = {0.f, 0.f, 0.f}, uF[3] = {0.f, 0.f, 0.f};
+        float uu = 0.f;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            uF[a] = u[a] + F[a] / rho;
-            if (!(fabs(u[a]) < (CT)1) || !(fabs(uF[a]) < (CT)1)) bad |= ERR_VEL;
+            u[a] = j[a] * ir;
+            up[a] = fmaf(0.5f, F[a], j[a]) * ir;  // velocity with half the force (Eq. for the g equilibrium)
+            uF[a] = fmaf(F[a], ir, u[a]);         // u + F/rho (exact-difference forcing)
+            uu = fmaf(up[a], up[a], uu);
+            if (!(fabsf(u[a]) < 1.f) || !(fabsf(uF[a]) < 1.f)) bad |= ERR_VEL;
         }
-        // equilibrium factors at u and at u + F/rho
-        CT e[3][3], eF[3][3];
+
+        // ---- g: BGK towards g^eq_i = w_i [Gm3 - 1.5 phi u.u + cu (3 phi + 4.5 phi cu)],
+        // cu = c_i.u; the pair's second member has -cu.  The rest population
+        // closes the node's phase-field sum.
+        {
+            const float2 G0 = bc2(fmaf(-1.5f * phi, uu, K.Gamma3 * mu_phi));
+            const float2 P3 = bc2(3.f * phi), P45 = bc2(4.5f * phi), IT = bc2(K.inv_tau_g);
+            float2 U2[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) U2[a] = make_float2(up[a], -up[a]);
+            float2 goth = bc2(0.f);
+            float *gd = reinterpret_cast<float *>(A.gdst);
+            // pair (kp, k), kp = Q-1-k: the member kp has a positive last
+            // non-zero component of c, so c.u is U2 of that axis plus or minus
+            // the others
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const int kp = Q - 1 - k;
+                float2 cu = bc2(0.f);
+                bool first = true;
+#pragma unroll
+                for (int a = D - 1; a >= 0; --a) {
+                    const int ca = L::c(kp, a);
+                    if (!ca) continue;
+                    cu = first ? U2[a] : (ca > 0 ? add2(cu, U2[a]) : sub2(cu, U2[a]));
+                    first = false;
+                }
+                const float2 geq = mul2(bc2((float)L::w(k)), fma2(cu, fma2(P45, cu, P3), G0));
+                const float2 g2 = make_float2(pull(gs, nb, P.N, kp), pull(gs, nb, P.N, k));
+                const float2 go = fma2(IT, sub2(geq, g2), g2);
+                goth = add2(goth, go);
+                gd[didx(kp)] = go.x;
+                gd[didx(k)] = go.y;
+            }
+            gd[didx(L::REST)] = phi - (goth.x + goth.y);
+        }
+
+        // ---- equilibrium factors at u; second moments of f^eq
+        float e[3][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (a < D) { eq_factors<CT>(u[a], e[a]); eq_factors<CT>(uF[a], eF[a]); }
-            else { e[a][0] = 0; e[a][1] = 1; e[a][2] = 0; eF[a][0] = 0; eF[a][1] = 1; eF[a][2] = 0; }
+            if (a < D) eq_factors_f(u[a], e[a]);
+            else { e[a][0] = 0.f; e[a][1] = 1.f; e[a][2] = 0.f; }
         }
-        // second moments of f^eq from the factor moments M0 = sum e, M1 = sum c e, M2 = sum c^2 e
-        CT M0[3], M1[3], M2[3];
+        float M0[3], M1[3], M2[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             M0[a] = e[a][0] + e[a][1] + e[a][2];
             M1[a] = e[a][2] - e[a][0];
             M2[a] = e[a][2] + e[a][0];
         }
-        CT dPi[6];
+        float dPi[6];
         dPi[0] = Pi[0] - rho * M2[0] * M0[1] * M0[2];
         dPi[1] = Pi[1] - rho * M0[0] * M2[1] * M0[2];
-        dPi[2] = (D == 3) ? Pi[2] - rho * M0[0] * M0[1] * M2[2] : (CT)0;
+        dPi[2] = (D == 3) ? Pi[2] - rho * M0[0] * M0[1] * M2[2] : 0.f;
         dPi[3] = Pi[3] - rho * M1[0] * M1[1] * M0[2];
-        dPi[4] = (D == 3) ? Pi[4] - rho * M1[0] * M0[1] * M1[2] : (CT)0;
-        dPi[5] = (D == 3) ? Pi[5] - rho * M0[0] * M1[1] * M1[2] : (CT)0;
-        const CT tr = dPi[0] + dPi[1] + dPi[2];
-        const CT dev[3] = {dPi[0] - tr / (CT)D, dPi[1] - tr / (CT)D, dPi[2] - tr / (CT)D};
+        dPi[4] = (D == 3) ? Pi[4] - rho * M1[0] * M0[1] * M1[2] : 0.f;
+        dPi[5] = (D == 3) ? Pi[5] - rho * M0[0] * M1[1] * M1[2] : 0.f;
+        const float tr = (dPi[0] + dPi[1] + dPi[2]) * (1.f / (float)D);
+        // Delta s: 1/2 of the deviatoric normal stress on the velocities along
+        // one axis, +-1/4 of the shear stress on the velocities in one plane
+        float2 DS1[3], DS2[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            DS1[a] = bc2(0.5f * (dPi[a] - tr));
+            DS2[a] = bc2(0.25f * dPi[3 + a]);
+        }
+        // pair factors: X[c] = rho (e_x[c], e_x[-c]), Y[c], Z[c] likewise
+        float2 X[3], Y[3], Z[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            X[c] = make_float2(rho * e[0][c], rho * e[0][2 - c]);
+            Y[c] = make_float2(e[1][c], e[1][2 - c]);
+            Z[c] = make_float2(e[2][c], e[2][2 - c]);
+        }
+        auto feq2 = [&](int k, const float2 *Xa, const float2 *Ya, const float2 *Za) -> float2 {
+            const float2 v = mul2(Xa[L::cx(k) + 1], Ya[L::cy(k) + 1]);
+            return D == 3 ? mul2(v, Za[L::cz(k) + 1]) : v;
+        };
+        // Delta h = Delta - Delta s of pair k, Delta = f - f^eq
+        auto dh2 = [&](int k, float2 dl) -> float2 {
+            if (L::nnz(k) == 1) return sub2(dl, DS1[L::cx(k) ? 0 : (L::cy(k) ? 1 : 2)]);
+            if (L::nnz(k) == 2) {
+                const int pl = L::cz(k) == 0 ? 0 : (L::cy(k) == 0 ? 1 : 2);
+                const int sg = L::cz(k) == 0 ? L::cx(k) * L::cy(k) : (L::cy(k) == 0 ? L::cx(k) * L::cz(k)
+                                                                                  : L::cy(k) * L::cz(k));
+                return sg > 0 ? sub2(dl, DS2[pl]) : add2(dl, DS2[pl]);
+            }
+            return dl;
+        };
 
-        // entropic scalar products <ds|dh>, <dh|dh>.  FP64 storage: FP64
-        // sums.  FP32 storage: the FP32 terms are summed with Knuth's
-        // error-free two-sum (the sum of the terms exact to ~2^-48).
-        double shd = 0.0, hhd = 0.0;
-        CT sh = 0, hh = 0, shc = 0;
+        // ---- entropic scalar products <ds|dh> and <dh|dh> (weights 1/f^eq).
+        // Delta = f - f^eq replaces f in the stash: the output pass needs no
+        // f^eq(u) then.
+        float2 hh2 = bc2(0.f), shp = bc2(0.f), shn = bc2(0.f);  // <ds|dh>: terms of Delta s sign +, -
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const CT fi = fq[i * NT];
-            const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
-            const CT dl = StoreTraits<ST>::shifted ? fi - (feq - (CT)L::w(i) * shift) : fi - feq;
-            const CT ds = ds_of(i, dev, dPi);
-            const CT dh = dl - ds;
-            // <dh|dh> sums non-negative terms (no cancellation); <ds|dh> has
-            // terms only where ds != 0 (one or two non-zero components of c_i)
-            const bool has_ds = L::nnz(i) == 1 || L::nnz(i) == 2;
-            if (StoreTraits<ST>::shifted) {
-                const CT r = __fdividef(1.f, (float)feq);  // weight 1/f^eq: ~2 ulp is ample
-                if (has_ds) two_sum_acc<CT>(sh, shc, ds * dh * r);
-                hh += dh * dh * r;
-            } else {
-                const CT r = (CT)1 / feq;
-                if (has_ds) shd += (double)(ds * dh * r);
-                hhd += (double)(dh * dh * r);
+        for (int k = 0; k < NP; ++k) {
+            const float2 f2 = stash2[k * NT];
+            const float2 fe = feq2(k, X, Y, Z);
+            const float2 dl = sub2(f2, sub2(fe, bc2((float)L::w(k) * shift)));
+            stash2[k * NT] = dl;
+            const float2 dh = dh2(k, dl);
+            const float2 t = mul2(dh, make_float2(rcp_approx(fe.x), rcp_approx(fe.y)));  // weight 1/f^eq
+            hh2 = fma2(dh, t, hh2);
+            if (L::nnz(k) == 1) {
+                shp = fma2(DS1[L::cx(k) ? 0 : (L::cy(k) ? 1 : 2)], t, shp);
+            } else if (L::nnz(k) == 2) {
+                const int pl = L::cz(k) == 0 ? 0 : (L::cy(k) == 0 ? 1 : 2);
+                const int sg = L::cz(k) == 0 ? L::cx(k) * L::cy(k) : (L::cy(k) == 0 ? L::cx(k) * L::cz(k)
+                                                                                  : L::cy(k) * L::cz(k));
+                if (sg > 0) shp = fma2(DS2[pl], t, shp);
+                else shn = fma2(DS2[pl], t, shn);
             }
         }
-        // stabiliser gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh> in FP64,
-        // applied as beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh> (gamma = 2,
-        // i.e. beta gamma = 2 beta, when <dh|dh> vanishes).  FP32 storage:
-        // <ds|dh> is the compensated pair (sum + correction) added in FP64,
-        // 1/<dh|dh> an FP32 reciprocal refined by one Newton-Raphson step in
-        // FP64.
+        const float fe0 = rho * e[0][1] * e[1][1] * e[2][1];
+        const float dl0 = f0 - (fe0 - (float)L::w(L::REST) * shift);
+        const float hh = fmaf(dl0 * dl0, rcp_approx(fe0), hh2.x + hh2.y);
+        const float sh = (shp.x + shp.y) - (shn.x + shn.y);
+
+        // ---- stabiliser: beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh>, formed
+        // in FP64 from the FP32 ratio (gamma = 2, beta gamma = 2 beta, when
+        // <dh|dh> vanishes)
         double gbd = 2.0 * P.beta;
-        if (StoreTraits<ST>::shifted) {
-            if (hh > (CT)1e-30 * rho * rho) {
-                const double shs = (double)sh + (double)shc;
-                const double H = (double)hh;
-                double rH = (double)__frcp_rn((float)hh);
-                rH = rH * (2.0 - H * rH);
-                gbd = 1.0 - P.c_gb * (shs * rH);
-            }
-        } else {
-            const double rhod = (double)rho;
-            if (hhd > 1e-30 * rhod * rhod) gbd = 1.0 - P.c_gb * (shd / hhd);
-        }
-        const CT bet = K.beta, gb = (CT)gbd;
-        if (!isfinite(gb)) bad |= ERR_NAN;  // tested after the conversion: no FP64-pipe compare
-        ST *fd = reinterpret_cast<ST *>(A.fdst);
-        // FP32 storage: the rest population closes the node's mass so that the
-        // stored set sums to the pulled mass; rounding of the other outputs
-        // is then unbiased and the total mass does not drift.
-        CT oth = 0;
+        if (hh > 1e-30f * rho * rho) gbd = fma(-P.c_gb, (double)(sh * rcp_nr(hh)), 1.0);
+        const float gb = (float)gbd;
+        if (!isfinite(gb)) bad |= ERR_NAN;
+
+        // ---- output: f - beta (2 Delta s + gamma Delta h) + f^eq(u + F/rho) - f^eq(u)
+        //   = (1 - beta gamma) Delta + f^eq(u + F/rho) + (beta gamma - 2 beta) Delta s,
+        // stored shifted by -w_i rho_ref.  The rest population closes the
+        // node's mass to the pulled mass.
+        float eF[3][3];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const CT fi = fq[i * NT];
-            const CT feq = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
-            const CT feqF = rho * eF[0][L::cx(i) + 1] * eF[1][L::cy(i) + 1] * eF[2][L::cz(i) + 1];
-            const CT dl = StoreTraits<ST>::shifted ? fi - (feq - (CT)L::w(i) * shift) : fi - feq;
-            const CT ds = ds_of(i, dev, dPi);
-            const CT dh = dl - ds;
-            const CT out = fi - ((CT)2 * bet * ds + gb * dh) + (feqF - feq);
-            if (StoreTraits<ST>::shifted && i == L::REST) continue;
-            if (StoreTraits<ST>::shifted) oth += (CT)(ST)out;
-            fd[(long long)i * P.N + n] = (ST)out;
+        for (int a = 0; a < 3; ++a) {
+            if (a < D) eq_factors_f(uF[a], eF[a]);
+            else { eF[a][0] = 0.f; eF[a][1] = 1.f; eF[a][2] = 0.f; }
         }
-        if (StoreTraits<ST>::shifted) fd[(long long)L::REST * P.N + n] = (ST)(fsum - oth);
+        float2 XF[3], YF[3], ZF[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            XF[c] = make_float2(rho * eF[0][c], rho * eF[0][2 - c]);
+            YF[c] = make_float2(eF[1][c], eF[1][2 - c]);
+            ZF[c] = make_float2(eF[2][c], eF[2][2 - c]);
+        }
+        const float2 OMG = bc2(1.f - gb), PG = bc2(gb - 2.f * K.beta), NG = bc2(2.f * K.beta - gb);
+        float *fd = reinterpret_cast<float *>(A.fdst);
+        float2 oth = bc2(0.f);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float2 out = fma2(OMG, stash2[k * NT], sub2(feq2(k, XF, YF, ZF), bc2((float)L::w(k) * shift)));
+            if (L::nnz(k) == 1) {
+                out = fma2(PG, DS1[L::cx(k) ? 0 : (L::cy(k) ? 1 : 2)], out);
+            } else if (L::nnz(k) == 2) {
+                const int pl = L::cz(k) == 0 ? 0 : (L::cy(k) == 0 ? 1 : 2);
+                const int sg = L::cz(k) == 0 ? L::cx(k) * L::cy(k) : (L::cy(k) == 0 ? L::cx(k) * L::cz(k)
+                                                                                  : L::cy(k) * L::cz(k));
+                out = fma2(sg > 0 ? PG : NG, DS2[pl], out);
+            }
+            oth = add2(oth, out);
+            fd[didx(k)] = out.x;
+            fd[didx(Q - 1 - k)] = out.y;
+        }
+        fd[didx(L::REST)] = fsum - (oth.x + oth.y);
 
         if (bad) atomicOr(P.err, bad);
     }
