@@ -147,6 +147,7 @@ template <> struct Vec<float> {
     __device__ static __forceinline__ v2 pair(float a, float b) { return make_float2(a, b); }
     __device__ static __forceinline__ v2 fma(v2 a, v2 b, v2 c) { return __ffma2_rn(a, b, c); }
     __device__ static __forceinline__ v2 add(v2 a, v2 b) { return __fadd2_rn(a, b); }
+    __device__ static __forceinline__ v2 sub(v2 a, v2 b);
     __device__ static __forceinline__ v4 quad(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 };
 struct __align__(16) dquad { double x, y, z, w; };
@@ -156,6 +157,7 @@ template <> struct Vec<double> {
     __device__ static __forceinline__ v2 pair(double a, double b) { return make_double2(a, b); }
     __device__ static __forceinline__ v2 fma(v2 a, v2 b, v2 c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
     __device__ static __forceinline__ v2 add(v2 a, v2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+    __device__ static __forceinline__ v2 sub(v2 a, v2 b) { return make_double2(a.x - b.x, a.y - b.y); }
     __device__ static __forceinline__ v4 quad(double a, double b, double c, double d) { v4 q; q.x = a; q.y = b; q.z = c; q.w = d; return q; }
 };
 
@@ -172,6 +174,7 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
     return r;
 }
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 Vec<float>::sub(float2 a, float2 b) { return sub2(a, b); }
 
 template <typename T> __device__ __forceinline__ T log_(T x);
 template <> __device__ __forceinline__ double log_<double>(double x) { return log(x); }
@@ -329,7 +332,9 @@ template <> struct StoreTraits<float> { typedef float CT; static constexpr bool 
 // ---------------------------------------------------------------------------
 // FAST: no bounce-back axis and Q N < 2^31, so pulls need no wall test and
 // their indices fit 32 bits.
-template <int D, int TX, int TY, typename ST, int MODE, bool FAST>
+// VEC: phase A reads the populations as aligned four-node vectors along x
+// (D3Q27, FP32 storage, periodic, nx a multiple of 4, 32 x 8 tiles).
+template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false>
 struct Fused {
     typedef Lat<D> L;
     typedef typename StoreTraits<ST>::CT CT;
@@ -341,6 +346,12 @@ struct Fused {
     static constexpr int R2X = TX + 4, R2Y = (D == 3 ? TY + 4 : 1), NA = R2X * R2Y;
     static constexpr int R1X = TX + 2, R1Y = (D == 3 ? TY + 2 : 1), NB = R1X * R1Y;
     static constexpr int OY2 = (D == 3 ? 2 : 0), OY1 = (D == 3 ? 1 : 0);
+    // vector phase A: 8 warps, each with 3 rows of 10 chunks of 4 nodes
+    // (x0 - 4 .. x0 + TX + 3) in lanes 0-29; warps 0-3 sum f, warps 4-7 g,
+    // over the TY + 4 rows of tile + ring 2
+    static constexpr int NAV = 256;
+    static_assert(!VEC || (D == 3 && TX == 32 && TY == 8 && MODE == MODE_STEP && FAST &&
+                           StoreTraits<ST>::shifted), "vector phase A: D3Q27 32 x 8 FP32 periodic step");
 
     // shared memory layout (in CT units)
     // ring buffers over planes: RS slots of rho, phi (tile + ring 2), MS of
@@ -461,10 +472,16 @@ struct Fused {
             const int mC = mA - 3;
             const bool doA = mA <= m1 + 1;
             const bool doB = mB >= m0 - 1 && mB <= m1;
-            const int nA = doA ? NA : 0;
+            const int nA = doA ? (VEC ? NAV : NA) : 0;
             const int nW = nA + (doB ? NB : 0);
             const int mm = map_coord(mA, PM, bM);
             for (int w = tid; w < nW; w += NT) {
+                if constexpr (VEC) {
+                    if (w < nA) {
+                        phase_a_vec(P, fs, gs, rp_s + slot5(mA) * NA, w, x0, y0, mm, shift);
+                        continue;
+                    }
+                }
                 if (w < nA) {
                     // ---------------- phase A: moments of plane mA on tile + ring 2
                     const int r = w;
@@ -499,16 +516,20 @@ struct Fused {
                     const V2 ncp = V::pair(-r0, -p0);
                     V2 lap = V::pair((CT)0, (CT)0);
                     CT gx = 0, gy = 0, gz = 0;
+                    // over opposite neighbours (i, Q-1-i): the Laplacian takes
+                    // both differences to the centre, the gradient the
+                    // difference of the two
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        if (L::nnz(i) == 0) continue;
-                        const int k = slot5(mB + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i));
+                    for (int i = 0; i < L::REST; ++i) {
+                        const int io = Q - 1 - i;
+                        const V2 va = rp_s[slot5(mB + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
+                        const V2 vb = rp_s[slot5(mB + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))];
                         const CT wi = (CT)L::w(i);
-                        const V2 v = rp_s[k];
-                        lap = V::fma(V::pair(wi, wi), V::add(v, ncp), lap);
-                        if (L::cx(i)) gx += wi * (CT)L::cx(i) * v.x;
-                        if (L::cy(i)) gy += wi * (CT)L::cy(i) * v.x;
-                        if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * v.x;
+                        lap = V::fma(V::pair(wi, wi), V::add(V::add(va, ncp), V::add(vb, ncp)), lap);
+                        const CT d = va.x - vb.x;
+                        if (L::cx(i)) gx += wi * (CT)L::cx(i) * d;
+                        if (L::cy(i)) gy += wi * (CT)L::cy(i) * d;
+                        if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * d;
                     }
                     const CT lr = (CT)6 * lap.x;
                     const CT lp = (CT)6 * lap.y;
@@ -535,6 +556,66 @@ struct Fused {
         }
     }
 
+    // Phase A on four-node vectors along x.  Item w (all 32 lanes of warp
+    // w / 32 present) sums f (warps 0-3) or g (warps 4-7) over row
+    // oy = 3 (w / 32 % 4) + (w % 32) / 10 - 2 for the chunk
+    // x0 - 4 + 4c .. x0 - 1 + 4c, c = (w % 32) % 10; lanes 30, 31 idle.
+    // Population i pulled into node x is f_i(x - c_ix) of row y - c_iy and
+    // plane m - c_iz: with the populations of one sign of c_ix summed per
+    // vector, the shifted element comes from the same vector or, at its end,
+    // from the neighbouring lane's.  Only the nodes of tile + ring 2 are
+    // stored (the outermost node of chunks 0 and 9 takes a neighbour row's
+    // value and is not needed).
+    __device__ static void phase_a_vec(const DevParams &P, const ST *fs, const ST *gs, V2 *rp_plane, int w,
+                                       int x0, int y0, int m, CT shift)
+    {
+        const int lane = w & 31, rr = lane / 10, c = lane - 10 * rr;
+        const bool is_g = (w >> 5) >= 4;
+        const int oy = 3 * ((w >> 5) & 3) + rr - 2;
+        const bool act = lane < 30;
+        const int PX = P.nx, PY = P.ny, PM = P.nz;
+        // periodic wrap; with nx % 4 == 0 a chunk never straddles the seam
+        int X = (x0 - 4 + 4 * c) % PX;
+        if (X < 0) X += PX;
+        const int y = y0 + oy;
+        int ro[3], po[3];
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+            int yy = (y - d) % PY, mm = m - d;  // m is already in [0, PM)
+            if (yy < 0) yy += PY;
+            if (mm < 0) mm += PM; else if (mm >= PM) mm -= PM;
+            ro[d + 1] = yy * PX;
+            po[d + 1] = mm * PX * PY;
+        }
+        const ST *src = is_g ? gs : fs;
+        float2 h[3][2];  // [c_x + 1][low, high half of the vector]
+#pragma unroll
+        for (int a = 0; a < 3; ++a) h[a][0] = h[a][1] = bc2(0.f);
+        if (act) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const unsigned k = (unsigned)i * (unsigned)P.N + (unsigned)(ro[L::cy(i) + 1] + po[L::cz(i) + 1] + X);
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(src + k));
+                const int a = L::cx(i) + 1;
+                h[a][0] = add2(h[a][0], make_float2(v.x, v.y));
+                h[a][1] = add2(h[a][1], make_float2(v.z, v.w));
+            }
+        }
+        // c_x = +1 pulls from x - 1, c_x = -1 from x + 1
+        const float hl = __shfl_up_sync(0xffffffffu, h[2][1].y, 1);
+        const float hr = __shfl_down_sync(0xffffffffu, h[0][0].x, 1);
+        const float sum[4] = {h[1][0].x + hl + h[0][0].y, h[1][0].y + h[2][0].x + h[0][1].x,
+                              h[1][1].x + h[2][0].y + h[0][1].y, h[1][1].y + h[2][1].x + hr};
+        if (act) {
+            float *dst = reinterpret_cast<float *>(rp_plane) + (is_g ? 1 : 0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int ox = 4 * c - 4 + e;
+                if (ox >= -2 && ox < TX + 2) dst[2 * idx2(ox, oy)] = is_g ? sum[e] : shift + sum[e];
+            }
+        }
+    }
+
     __device__ static void node(const DevParams &P, const LaunchArgs &A, const ST *fs, const ST *gs,
                                 const V2 *rp_s, const V2 *mu_s, const V4 *g_s, CT *stash, int x, int y, int m,
                                 int tx, int ty)
@@ -555,10 +636,12 @@ struct Fused {
 #pragma unroll
         for (int a = 0; a < 3; ++a) { gmu[a] = V::pair((CT)0, (CT)0); grp[a] = V::pair((CT)0, (CT)0); }
         const bool need_grp = (MODE == MODE_FIELDS) || P.force_form == 0;
+        // over opposite neighbours (i, Q-1-i): w_i c_i (v(x + c_i) - v(x - c_i))
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (L::nnz(i) == 0) continue;
-            const V2 vm = mu_s[slot3(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i))];
+        for (int i = 0; i < L::REST; ++i) {
+            const int io = Q - 1 - i;
+            const V2 vm = V::sub(mu_s[slot3(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i))],
+                                 mu_s[slot3(m + L::pM(io)) * NB + idx1(ox + L::pX(io), oy + L::pY(io))]);
             const CT wi = (CT)L::w(i);
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -566,7 +649,8 @@ struct Fused {
                 if (ca) gmu[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vm, gmu[a]);
             }
             if (need_grp) {
-                const V2 vr = rp_s[slot5(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
+                const V2 vr = V::sub(rp_s[slot5(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))],
+                                     rp_s[slot5(m + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))]);
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     const int ca = L::c(i, a);
@@ -1106,10 +1190,10 @@ struct Fused {
 template <typename ST> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<float> { static constexpr int value = TEL_MIN_BLOCKS_FP32; };
 
-template <int D, int TX, int TY, typename ST, int MODE, bool FAST>
+template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false>
 __global__ void __launch_bounds__(TX * TY, MinBlocks<ST>::value) fused_kernel(const DevParams P, const LaunchArgs A)
 {
-    Fused<D, TX, TY, ST, MODE, FAST>::run(P, A);
+    Fused<D, TX, TY, ST, MODE, FAST, VEC>::run(P, A);
 }
 
 // Batched persistent D2Q9 step: each CTA walks a work list of (case, tile,

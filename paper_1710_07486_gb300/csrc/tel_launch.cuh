@@ -5,13 +5,13 @@
 
 namespace tel {
 
-template <int D, int TX, int TY, typename ST, int MODE, bool FAST>
+template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false>
 static cudaError_t launch_one(const DevParams &P, const LaunchArgs &A, cudaStream_t s)
 {
-    typedef Fused<D, TX, TY, ST, MODE, FAST> K;
+    typedef Fused<D, TX, TY, ST, MODE, FAST, VEC> K;
     static bool configured = false;  // per-instantiation: opt in to > 48 KB of shared memory
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(fused_kernel<D, TX, TY, ST, MODE, FAST>,
+        cudaError_t e = cudaFuncSetAttribute(fused_kernel<D, TX, TY, ST, MODE, FAST, VEC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -25,7 +25,7 @@ static cudaError_t launch_one(const DevParams &P, const LaunchArgs &A, cudaStrea
     } else {
         grid.y = nch;
     }
-    fused_kernel<D, TX, TY, ST, MODE, FAST><<<grid, K::NT, K::SMEM_BYTES, s>>>(P, A);
+    fused_kernel<D, TX, TY, ST, MODE, FAST, VEC><<<grid, K::NT, K::SMEM_BYTES, s>>>(P, A);
     return cudaGetLastError();
 }
 
@@ -37,7 +37,12 @@ static cudaError_t launch_prec(int precision, int mode, const DevParams &P, cons
         if (mode == MODE_INIT) return launch_one<D, TX, TY, double, MODE_INIT, FAST>(P, A, s);
         return launch_one<D, TX, TY, double, MODE_FIELDS, FAST>(P, A, s);
     }
-    if (mode == MODE_STEP) return launch_one<D, TX, TY, float, MODE_STEP, FAST>(P, A, s);
+    if (mode == MODE_STEP) {
+        // aligned four-node vectors in phase A (D3Q27 32 x 8, periodic, nx % 4 == 0)
+        if constexpr (D == 3 && TX == 32 && TY == 8 && FAST)
+            if (P.nx % 4 == 0) return launch_one<D, TX, TY, float, MODE_STEP, FAST, true>(P, A, s);
+        return launch_one<D, TX, TY, float, MODE_STEP, FAST>(P, A, s);
+    }
     if (mode == MODE_INIT) return launch_one<D, TX, TY, float, MODE_INIT, FAST>(P, A, s);
     return launch_one<D, TX, TY, float, MODE_FIELDS, FAST>(P, A, s);
 }

@@ -124,6 +124,27 @@ def test_fp32_shifted_against_fp64_oracle(orc, T10, lattice, shape):
     assert abs(a["phi"].sum() - phi.sum()) / np.abs(phi).sum() < 1e-6
 
 
+@pytest.mark.parametrize("shape", [(36, 10, 21), (16, 16, 16), (37, 11, 19)])
+def test_one_step_fp32_state_parity_d3q27(orc, T10, shape):
+    """One FP32-shifted step against the oracle started from the same state.
+    nx % 4 == 0 reads phase A as aligned four-node vectors (here with partial
+    tiles in x and y and periodic seams inside a tile); nx % 4 != 0 takes the
+    scalar path.  Bar: one FP32 step against FP64, 2e-5 (f relative to the
+    node's largest f, g relative to chi)."""
+    p = asymmetric(T10, force_form=1)
+    g, o, rho, phi, u = setup_pair(orc, 1, shape, p, precision=tel.FP32_SHIFTED)
+    g.init(rho, phi, u)
+    g.step(2)
+    f0, g0 = g.get_state()
+    g.step(1)
+    f1, g1 = g.get_state()
+    o1 = orc.Oracle(1, shape[0], shape[1], shape[2], dict(p, rho_ref=0.0))
+    assert o1.step(f0, g0, 1) == 0
+    ef = np.max(np.abs(f0 - f1) / np.max(np.abs(f0), axis=0))
+    eg = np.max(np.abs(g0 - g1)) / p["chi"]
+    assert max(ef, eg) < 2e-5, (ef, eg)
+
+
 def test_step_batches_and_checkpoint_are_bitwise(orc, T10):
     p = base(T10)
     g, o, rho, phi, u = setup_pair(orc, 0, (40, 24), p)
