@@ -358,7 +358,10 @@ struct Fused {
     // mu and grad rho (tile + ring 1)
     // (rho, phi) and (mu_rho, mu_phi) are stored as pairs, (grad rho,
     // c_s^4/(4 rho)) as quads, so that a stencil neighbour is one load.
-    static constexpr int RS = 6, MS = 4;
+    // SPLIT (D3Q27): phases A and B in separate passes, pipeline depth 2,
+    // RS = 4, MS = 3; otherwise one merged A/B pass, depth 3, RS = 6, MS = 4.
+    static constexpr bool SPLIT = (D == 3);
+    static constexpr int RS = SPLIT ? 4 : 6, MS = SPLIT ? 3 : 4;
     static constexpr int OFF_RP = 0;                         // pairs [RS][NA]
     static constexpr int OFF_MU = OFF_RP + 2 * RS * NA;      // pairs [MS][NB]
     static constexpr int OFF_G = OFF_MU + 2 * MS * NB;       // quads [MS][NB]
@@ -371,8 +374,8 @@ struct Fused {
 
     __device__ static __forceinline__ int idx2(int ox, int oy) { return (ox + 2) + R2X * (oy + OY2); }
     __device__ static __forceinline__ int idx1(int ox, int oy) { return (ox + 1) + R1X * (oy + OY1); }
-    __device__ static __forceinline__ int slot5(int m) { int s = m % RS; return s < 0 ? s + RS : s; }
-    __device__ static __forceinline__ int slot3(int m) { int s = m % MS; return s < 0 ? s + MS : s; }
+    __device__ static __forceinline__ int slotR(int m) { int s = m % RS; return s < 0 ? s + RS : s; }
+    __device__ static __forceinline__ int slotM(int m) { int s = m % MS; return s < 0 ? s + MS : s; }
 
     // Sources of the populations pulled into node (x, y, m): per axis the
     // source coordinate x - c for c = -1, 0, 1 (periodic wrap) as an offset,
@@ -458,100 +461,116 @@ struct Fused {
         const ST *fs = reinterpret_cast<const ST *>(A.fsrc);
         const ST *gs = reinterpret_cast<const ST *>(A.gsrc);
 
-        // Software pipeline over planes, one barrier per plane.  Iteration it
-        // works on three planes: moments of mA (phase A) and chemical
-        // potentials of mB = mA - 2 (phase B, from moments completed in earlier
-        // iterations) in one load-balanced pass, then, after the barrier, the
-        // collision of mC = mA - 3 (phase C).  With RS = 6 moment slots and
-        // MS = 4 potential slots, the next iteration's A/B pass never writes a
-        // slot that phase C is still reading, so no second barrier is needed.
-        const int iters = (m1 - m0) + 5;
+        // Software pipeline over planes.  SPLIT: iteration it computes the
+        // moments of mA (phase A), then, after a barrier, the chemical
+        // potentials of mB = mA - 1 (phase B), then, after a barrier, the
+        // collision of mC = mA - 2 (phase C).  The next iteration's phase A
+        // may overlap this phase C: with RS = 4 the moment slot it writes is
+        // not one that phase C reads (one more barrier when phase C reads the
+        // neighbouring planes' moments, for grad rho and grad phi); phase B
+        // only starts once every thread has passed the next barrier, so MS = 3.
+        // Merged (D2Q9): phases A (plane mA) and B (mB = mA - 2) share one
+        // load-balanced pass, then, after the barrier, phase C collides
+        // mC = mA - 3; with RS = 6 and MS = 4 the next A/B pass never writes a
+        // slot that phase C is still reading.
+        const int tid_x = tid % TX, tid_y = tid / TX;
+        const bool need_grp = (MODE == MODE_FIELDS) || P.force_form == 0;
+        const int iters = (m1 - m0) + (SPLIT ? 4 : 5);
         for (int it = 0; it < iters; ++it) {
             const int mA = m0 - 2 + it;
-            const int mB = mA - 2;
-            const int mC = mA - 3;
+            const int mB = mA - (SPLIT ? 1 : 2);
+            const int mC = mA - (SPLIT ? 2 : 3);
             const bool doA = mA <= m1 + 1;
             const bool doB = mB >= m0 - 1 && mB <= m1;
             const int nA = doA ? (VEC ? NAV : NA) : 0;
-            const int nW = nA + (doB ? NB : 0);
             const int mm = map_coord(mA, PM, bM);
-            for (int w = tid; w < nW; w += NT) {
+            auto item_a = [&](int w) {
                 if constexpr (VEC) {
-                    if (w < nA) {
-                        phase_a_vec(P, fs, gs, rp_s + slot5(mA) * NA, w, x0, y0, mm, shift);
-                        continue;
-                    }
+                    phase_a_vec(P, fs, gs, rp_s + slotR(mA) * NA, w, x0, y0, mm, shift);
+                    return;
                 }
-                if (w < nA) {
-                    // ---------------- phase A: moments of plane mA on tile + ring 2
-                    const int r = w;
-                    const int ox = r % R2X - 2, oy = (D == 3 ? r / R2X - 2 : 0);
-                    const int xx = map_coord(x0 + ox, PX, bX);
-                    const int yy = (D == 3 ? map_coord(y0 + oy, PY, bY) : 0);
-                    CT rho, phi;
-                    if (MODE == MODE_INIT) {
-                        const long long n = (long long)xx + (long long)PX * ((long long)yy + (long long)PY * mm);
-                        rho = (CT)A.in_rho[n];
-                        phi = (CT)A.in_phi[n];
-                    } else {
-                        Nbr nb;
-                        make_nbr(P, PX, PY, PM, xx, yy, mm, nb);
-                        CT sr = 0, sp = 0;
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) sr += pull(fs, nb, P.N, i);
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) sp += pull(gs, nb, P.N, i);
-                        rho = StoreTraits<ST>::shifted ? shift + sr : sr;
-                        phi = sp;
-                    }
-                    rp_s[slot5(mA) * NA + r] = V::pair(rho, phi);
+                // ---------------- phase A: moments of plane mA on tile + ring 2
+                const int r = w;
+                const int ox = r % R2X - 2, oy = (D == 3 ? r / R2X - 2 : 0);
+                const int xx = map_coord(x0 + ox, PX, bX);
+                const int yy = (D == 3 ? map_coord(y0 + oy, PY, bY) : 0);
+                CT rho, phi;
+                if (MODE == MODE_INIT) {
+                    const long long n = (long long)xx + (long long)PX * ((long long)yy + (long long)PY * mm);
+                    rho = (CT)A.in_rho[n];
+                    phi = (CT)A.in_phi[n];
                 } else {
-                    // ---------------- phase B: chemical potentials of plane mB on tile + ring 1
-                    const int s = w - nA;
-                    const int sB = slot3(mB);
-                    const int ox = s % R1X - 1, oy = (D == 3 ? s / R1X - 1 : 0);
-                    const int c0 = idx2(ox, oy);
-                    const V2 cp = rp_s[slot5(mB) * NA + c0];
-                    const CT r0 = cp.x, p0 = cp.y;
-                    const V2 ncp = V::pair(-r0, -p0);
-                    V2 lap = V::pair((CT)0, (CT)0);
-                    CT gx = 0, gy = 0, gz = 0;
-                    // over opposite neighbours (i, Q-1-i): the Laplacian takes
-                    // both differences to the centre, the gradient the
-                    // difference of the two
+                    Nbr nb;
+                    make_nbr(P, PX, PY, PM, xx, yy, mm, nb);
+                    CT sr = 0, sp = 0;
 #pragma unroll
-                    for (int i = 0; i < L::REST; ++i) {
-                        const int io = Q - 1 - i;
-                        const V2 va = rp_s[slot5(mB + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
-                        const V2 vb = rp_s[slot5(mB + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))];
-                        const CT wi = (CT)L::w(i);
-                        lap = V::fma(V::pair(wi, wi), V::add(V::add(va, ncp), V::add(vb, ncp)), lap);
-                        const CT d = va.x - vb.x;
-                        if (L::cx(i)) gx += wi * (CT)L::cx(i) * d;
-                        if (L::cy(i)) gy += wi * (CT)L::cy(i) * d;
-                        if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * d;
-                    }
-                    const CT lr = (CT)6 * lap.x;
-                    const CT lp = (CT)6 * lap.y;
-                    CT mr, mp;
-                    mu_wells<CT>(P, r0, p0, mr, mp);
-                    if (StoreTraits<ST>::shifted && r0 < coef<CT>(P).rho_switch)  // FP64 gas side
-                        mr = (P.eos == EOS_CS ? (CT)mu_eos_gas(P, (float)r0) : (CT)mu_eos<double>(P, (double)r0)) + mr;
-                    else
-                        mr = mu_eos<CT>(P, r0) + mr;
-                    mu_s[sB * NB + s] = V::pair(mr - coef<CT>(P).Kr * lr - coef<CT>(P).Kx * lp,
-                                                mp - coef<CT>(P).Kp * lp - coef<CT>(P).Kx * lr);
-                    if (P.force_form == 1)  // grad rho and c_s^4/(4 rho) (lattice-consistent force)
-                        g_s[sB * NB + s] = V::quad((CT)3 * gx, (CT)3 * gy, (CT)3 * gz, (CT)(1.0 / 36.0) * inv_<CT>(r0));
+                    for (int i = 0; i < Q; ++i) sr += pull(fs, nb, P.N, i);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) sp += pull(gs, nb, P.N, i);
+                    rho = StoreTraits<ST>::shifted ? shift + sr : sr;
+                    phi = sp;
+                }
+                rp_s[slotR(mA) * NA + r] = V::pair(rho, phi);
+            };
+            auto item_b = [&](int s) {
+                // ---------------- phase B: chemical potentials of plane mB on tile + ring 1
+                const int sB = slotM(mB);
+                const int ox = s % R1X - 1, oy = (D == 3 ? s / R1X - 1 : 0);
+                const int c0 = idx2(ox, oy);
+                const V2 cp = rp_s[slotR(mB) * NA + c0];
+                const CT r0 = cp.x, p0 = cp.y;
+                const V2 ncp = V::pair(-r0, -p0);
+                V2 lap = V::pair((CT)0, (CT)0);
+                CT gx = 0, gy = 0, gz = 0;
+                // over opposite neighbours (i, Q-1-i): the Laplacian takes
+                // both differences to the centre, the gradient the
+                // difference of the two
+#pragma unroll
+                for (int i = 0; i < L::REST; ++i) {
+                    const int io = Q - 1 - i;
+                    const V2 va = rp_s[slotR(mB + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
+                    const V2 vb = rp_s[slotR(mB + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))];
+                    const CT wi = (CT)L::w(i);
+                    lap = V::fma(V::pair(wi, wi), V::add(V::add(va, ncp), V::add(vb, ncp)), lap);
+                    const CT d = va.x - vb.x;
+                    if (L::cx(i)) gx += wi * (CT)L::cx(i) * d;
+                    if (L::cy(i)) gy += wi * (CT)L::cy(i) * d;
+                    if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * d;
+                }
+                const CT lr = (CT)6 * lap.x;
+                const CT lp = (CT)6 * lap.y;
+                CT mr, mp;
+                mu_wells<CT>(P, r0, p0, mr, mp);
+                if (StoreTraits<ST>::shifted && r0 < coef<CT>(P).rho_switch)  // FP64 gas side
+                    mr = (P.eos == EOS_CS ? (CT)mu_eos_gas(P, (float)r0) : (CT)mu_eos<double>(P, (double)r0)) + mr;
+                else
+                    mr = mu_eos<CT>(P, r0) + mr;
+                mu_s[sB * NB + s] = V::pair(mr - coef<CT>(P).Kr * lr - coef<CT>(P).Kx * lp,
+                                            mp - coef<CT>(P).Kp * lp - coef<CT>(P).Kx * lr);
+                if (P.force_form == 1)  // grad rho and c_s^4/(4 rho) (lattice-consistent force)
+                    g_s[sB * NB + s] = V::quad((CT)3 * gx, (CT)3 * gy, (CT)3 * gz, (CT)(1.0 / 36.0) * inv_<CT>(r0));
+            };
+            if constexpr (SPLIT) {
+                for (int w = tid; w < nA; w += NT) item_a(w);
+                __syncthreads();
+                if (doB)
+                    for (int s = tid; s < NB; s += NT) item_b(s);
+            } else {
+                const int nW = nA + (doB ? NB : 0);
+                for (int w = tid; w < nW; w += NT) {
+                    if (w < nA) item_a(w);
+                    else item_b(w - nA);
                 }
             }
             __syncthreads();
             // ---------------- phase C: collide plane mC
             if (mC >= m0 && mC < m1) {
-                const int tx = tid % TX, ty = tid / TX;
-                const int x = x0 + tx, y = y0 + ty;
+                const int x = x0 + tid_x, y = y0 + tid_y;
                 if (x < PX && (D == 2 || y < PY))
-                    node(P, A, fs, gs, rp_s, mu_s, g_s, sm + OFF_F, x, y, mC, tx, ty);
+                    node(P, A, fs, gs, rp_s, mu_s, g_s, sm + OFF_F, x, y, mC, tid_x, tid_y);
+            }
+            if constexpr (SPLIT) {
+                if (need_grp) __syncthreads();
             }
         }
     }
@@ -624,7 +643,7 @@ struct Fused {
         const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
         const long long n = (long long)x + (long long)PX * ((long long)y + (long long)PY * m);
         const int ox = tx, oy = (D == 3 ? ty : 0);
-        const V2 rp0 = rp_s[slot5(m) * NA + idx2(ox, oy)];
+        const V2 rp0 = rp_s[slotR(m) * NA + idx2(ox, oy)];
         const CT rho = rp0.x, phi = rp0.y;
         const Coef<CT> &K = coef<CT>(P);
         const CT shift = K.rho_ref;
@@ -640,8 +659,8 @@ struct Fused {
 #pragma unroll
         for (int i = 0; i < L::REST; ++i) {
             const int io = Q - 1 - i;
-            const V2 vm = V::sub(mu_s[slot3(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i))],
-                                 mu_s[slot3(m + L::pM(io)) * NB + idx1(ox + L::pX(io), oy + L::pY(io))]);
+            const V2 vm = V::sub(mu_s[slotM(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i))],
+                                 mu_s[slotM(m + L::pM(io)) * NB + idx1(ox + L::pX(io), oy + L::pY(io))]);
             const CT wi = (CT)L::w(i);
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -649,8 +668,8 @@ struct Fused {
                 if (ca) gmu[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vm, gmu[a]);
             }
             if (need_grp) {
-                const V2 vr = V::sub(rp_s[slot5(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))],
-                                     rp_s[slot5(m + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))]);
+                const V2 vr = V::sub(rp_s[slotR(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))],
+                                     rp_s[slotR(m + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))]);
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     const int ca = L::c(i, a);
@@ -683,7 +702,7 @@ struct Fused {
             for (int i = 0; i < Q; ++i) {
                 if (L::nnz(i) == 0) continue;
                 const CT wi3 = (CT)(3.0 * L::w(i));
-                const int sp_ = slot3(m + L::pM(i));
+                const int sp_ = slotM(m + L::pM(i));
                 const int kp = idx1(ox + L::pX(i), oy + L::pY(i));
                 const V4 gq = g_s[sp_ * NB + kp];
                 const CT Gp[3] = {gq.x, gq.y, gq.z};
@@ -700,13 +719,13 @@ struct Fused {
 #pragma unroll
                 for (int a = 0; a < D; ++a) dT[a] += q * Gp[a];
             }
-            const V4 g0 = g_s[slot3(m) * NB + idx1(ox, oy)];
+            const V4 g0 = g_s[slotM(m) * NB + idx1(ox, oy)];
             const CT G0[3] = {g0.x, g0.y, g0.z};
 #pragma unroll
             for (int a = 0; a < D; ++a)
                 F[a] += cs2 * ((CT)1.5 * G0[a] - (CT)0.5 * AG[a]) + dT[a];
         }
-        const V2 mu0 = mu_s[slot3(m) * NB + idx1(ox, oy)];
+        const V2 mu0 = mu_s[slotM(m) * NB + idx1(ox, oy)];
         const CT mu_phi = mu0.y;
 
         if (MODE == MODE_INIT) {
