@@ -176,6 +176,16 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 Vec<float>::sub(float2 a, float2 b) { return sub2(a, b); }
 
+// Asynchronous 4-byte copies global -> shared (sm_80+): the thread goes on
+// while they are in flight and waits for its own before reading them.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <typename T> __device__ __forceinline__ T log_(T x);
 template <> __device__ __forceinline__ double log_<double>(double x) { return log(x); }
 template <> __device__ __forceinline__ float log_<float>(float x) { return logf(x); }
@@ -426,6 +436,16 @@ struct Fused {
         return (CT)__ldg(base + src_index(b, N, i));
     }
 
+    // address of population i pulled into the node described by b
+    __device__ static __forceinline__ const ST *pull_ptr(const ST *base, const Nbr &b, long long N, int i)
+    {
+        if (FAST) {
+            const int cX = L::pX(i) + 1, cY = L::pY(i) + 1, cM = L::pM(i) + 1;
+            return base + ((unsigned)i * (unsigned)N + (unsigned)(b.off[0][cX] + b.off[1][cY] + b.off[2][cM]));
+        }
+        return base + src_index(b, N, i);
+    }
+
     // global index of population i pulled into the node described by b
     __device__ static __forceinline__ long long src_index(const Nbr &b, long long N, int i)
     {
@@ -648,6 +668,24 @@ struct Fused {
         const Coef<CT> &K = coef<CT>(P);
         const CT shift = K.rho_ref;
 
+        // FP32 storage, step mode: start the copies of the node's f pulls into
+        // its column of the stash now, so that they are in flight during the
+        // stencils below (pairs (f_k, f_{Q-1-k}); the rest population into a
+        // register).
+        Nbr nbc;
+        CT f_rest = 0;
+        if constexpr (StoreTraits<ST>::shifted && MODE == MODE_STEP) {
+            make_nbr(P, PX, PY, PM, x, y, m, nbc);
+            CT *col = stash + 2 * (tx + TX * ty);
+#pragma unroll
+            for (int k = 0; k < L::REST; ++k) {
+                cp_async4(col + 2 * k * NT, pull_ptr(fs, nbc, P.N, k));
+                cp_async4(col + 2 * k * NT + 1, pull_ptr(fs, nbc, P.N, Q - 1 - k));
+            }
+            cp_async_commit();
+            f_rest = pull(fs, nbc, P.N, L::REST);
+        }
+
         // gradients at the node: grad (mu_rho, mu_phi) from the ring-1 pairs,
         // grad (rho, phi) from the ring-2 pairs (the latter only for the
         // potential-form force and the field output), as packed pairs
@@ -733,7 +771,7 @@ struct Fused {
             return;
         }
         if constexpr (StoreTraits<ST>::shifted && MODE == MODE_STEP) {
-            collide_pairs(P, A, fs, gs, reinterpret_cast<float2 *>(stash) + (tx + TX * ty), n, x, y, m, rho, phi,
+            collide_pairs(P, A, gs, nbc, f_rest, reinterpret_cast<float2 *>(stash) + (tx + TX * ty), n, rho, phi,
                           mu_phi, F);
             return;
         }
@@ -878,32 +916,33 @@ struct Fused {
     // the same products of the one-dimensional factors with c reversed, their
     // g equilibria differ in the sign of c.u, and they enter the odd moments
     // through their difference and the even moments through their sum.
-    // The pulled pairs are kept in this thread's column of shared memory
-    // (stash2[k NT]) for the gamma and output passes.
-    __device__ static void collide_pairs(const DevParams &P, const LaunchArgs &A, const ST *fs, const ST *gs,
-                                         float2 *stash2, long long n, int x, int y, int m, float rho, float phi,
-                                         float mu_phi, const float F[3])
+    // The f pulls arrive in this thread's column of the stash (copies started
+    // by node()) and stay there for the gamma and output passes; the g pulls
+    // are all issued before the f moments are formed.
+    __device__ static void collide_pairs(const DevParams &P, const LaunchArgs &A, const ST *gs, const Nbr &nb,
+                                         float f0, float2 *stash2, long long n, float rho, float phi, float mu_phi,
+                                         const float F[3])
     {
         constexpr int NP = L::REST;
-        const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
         const Coef<float> &K = P.cf;
         const float shift = K.rho_ref;
-        Nbr nb;
-        make_nbr(P, PX, PY, PM, x, y, m, nb);
+        float2 gp[NP];  // (g_{Q-1-k}, g_k)
+#pragma unroll
+        for (int k = 0; k < NP; ++k) gp[k] = make_float2(pull(gs, nb, P.N, Q - 1 - k), pull(gs, nb, P.N, k));
+        cp_async_wait_all();
         auto didx = [&](int i) -> long long {
             if (FAST) return (long long)((unsigned)i * (unsigned)P.N + (unsigned)n);
             return (long long)i * P.N + n;
         };
 
         // ---- pull f: mass, momentum and second moments
-        const float f0 = pull(fs, nb, P.N, L::REST);
         float fsum = 0.f;
         float j[3] = {0.f, 0.f, 0.f};
         float Pi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx yy zz xy xz yz
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            const float fa = pull(fs, nb, P.N, k), fb = pull(fs, nb, P.N, Q - 1 - k);
-            stash2[k * NT] = make_float2(fa, fb);
+            const float2 fp = stash2[k * NT];
+            const float fa = fp.x, fb = fp.y;
             const float sp = fa + fb, dp = fa - fb;
             fsum += sp;
             if (L::cx(k)) { j[0] += (float)L::cx(k) * dp; Pi[0] += sp; }
@@ -961,7 +1000,7 @@ struct Fused {
                     first = false;
                 }
                 const float2 geq = mul2(bc2((float)L::w(k)), fma2(cu, fma2(P45, cu, P3), G0));
-                const float2 g2 = make_float2(pull(gs, nb, P.N, kp), pull(gs, nb, P.N, k));
+                const float2 g2 = gp[k];
                 const float2 go = fma2(IT, sub2(geq, g2), g2);
                 goth = add2(goth, go);
                 gd[didx(kp)] = go.x;
