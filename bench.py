@@ -316,7 +316,8 @@ def run_c5(args):
         "ms_per_step": round(ms_sur, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 (FP32 accumulation)", "data": "synthetic (snapshots of seeded LBM collisions; no dataset)",
         "config": {"workload": f"D2Q9 {H}^2 periodic collisions, density ratio U[100,1000], FP32-shifted LBM, "
-                               f"k={k} steps per advance", "train_trajectories": int(len(sn.good)),
+                               f"k={k} steps per advance", "generated_trajectories": int(ntrain + ntest),
+                   "train_trajectories": int(len(sn.good)),
                    "test_trajectories": int(Bt), "unstable_trajectories": int(sn.bad.sum()),
                    "snapshots": nsnap, "params": net.n, "train_iters": args.c5_iters, "batch": args.c5_batch,
                    "lr": args.c5_lr, "clip": args.c5_clip,
@@ -629,9 +630,10 @@ def main():
     ap.add_argument("--c5-n", type=int, default=256)
     ap.add_argument("--c5-k", type=int, default=50)
     ap.add_argument("--c5-snaps", type=int, default=24)
-    ap.add_argument("--c5-train-traj", type=int, default=192)
-    ap.add_argument("--c5-test-traj", type=int, default=16)
-    ap.add_argument("--c5-iters", type=int, default=16000)
+    ap.add_argument("--c5-train-traj", type=int, default=2000,
+                    help="trajectories generated for training (those with an unstable node are dropped)")
+    ap.add_argument("--c5-test-traj", type=int, default=32, help="trajectories generated for the held-out set")
+    ap.add_argument("--c5-iters", type=int, default=32000)
     ap.add_argument("--c5-batch", type=int, default=32)
     ap.add_argument("--c5-lr", type=float, default=5e-4)
     ap.add_argument("--c5-clip", type=float, default=0.2, help="global gradient-norm clip (<= 0: none)")
