@@ -4,7 +4,8 @@
  * on top of the method: a small convolutional encoder-decoder that advances
  * the density, composition and velocity fields of a D2Q9 lattice k steps at
  * a time, trained on snapshots of the lattice update itself, with the plain
- * update as fallback and judge of its error.  Each entry point is one kernel
+ * update as its fallback and as the reference its error is measured
+ * against.  Each entry point is one kernel
  * (or a short fixed sequence) issued on `stream` (a cudaStream_t, NULL = the
  * legacy default stream); all pointers are DEVICE pointers owned by the
  * caller, nothing is allocated or retained.  Return 0 on success,
