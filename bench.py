@@ -582,7 +582,24 @@ def cpu_baseline(args, steps=None, n=None):
     note = "" if done == steps else f" (oracle flagged the state unstable after {done} steps)"
     return {"value": round(n ** 3 * max(done, 1) / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"D3Q27 {n}^3 periodic box, same collision scaled (R={R * n / 256.0:g}, interface width 10), "
-                      f"{done} steps, FP64, single thread, {dt:.1f} s{note}"}
+                      f"{done} steps, FP64, single thread, {dt:.1f} s{note}",
+            "host": host_cpu()}
+
+
+def host_cpu():
+    """The host's CPU model and logical core count (the oracle uses one)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu": model, "logical_cores": os.cpu_count(), "machine": platform.machine()}
 
 
 def run_reference(args):
@@ -606,7 +623,8 @@ def run_reference(args):
                                    f"(bounded sample: {args.ref_n}^3 box, 1 step per timed step)",
                        "parallelism": "cpu, 1 thread"},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"D3Q27 {args.ref_n}^3 periodic box, one step per timed step"},
+                             "sample": f"D3Q27 {args.ref_n}^3 periodic box, one step per timed step",
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
