@@ -117,8 +117,10 @@ int tel_create(int lattice, int nx, int ny, int nz, const tel_params *params,
 /* Release all device memory and the library-created stream. NULL is a no-op. */
 void tel_destroy(tel_ctx *ctx);
 
-/* Message for the last failing call on ctx (or the last tel_create failure
- * when ctx is NULL).  Valid until the next call on the same context. */
+/* Message for the last failing call on ctx; when ctx is NULL, the message of
+ * the last failing context-free call (tel_create, tel_batch_create,
+ * tel_fields_noalloc) made by the calling thread (each thread keeps its own).  Valid until the next
+ * failing call of the same kind (same context, or same thread). */
 const char *tel_last_error(const tel_ctx *ctx);
 
 /* Run subsequent work on a caller stream (a cudaStream_t, e.g. PyTorch's
@@ -224,13 +226,19 @@ int tel_batch_info(const tel_batch *b, double out[6]);
  * <= 0), and receives rho, phi, u, p (any may be NULL) in host buffers, as
  * tel_fields returns them.  No device or pinned memory is allocated: the
  * library stages the fields through a fixed device array of at most
- * TEL_NOALLOC_MAX_NODES nodes (about 12.6 MB, reserved on every GPU that loads
- * the library, until exit).  Larger lattices are rejected with TEL_EINVAL.
- * The first call on a device looks up that array's device address, so make
- * it before any stream capture.  Calls share the array: calls that overlap on
- * the GPU race with each other.  The work runs on cuda_stream (NULL: the
- * legacy default stream) and the call synchronises it.  Errors as for
- * tel_fields; the message is available from tel_last_error(NULL). */
+ * TEL_NOALLOC_MAX_NODES nodes (about 12.6 MB).  Larger lattices are rejected
+ * with TEL_EINVAL.
+ * When the array's device memory is taken: under CUDA's lazy module loading
+ * (the default) the array is loaded on a device by the FIRST call on that
+ * device, and stays until the process exits.  So make one call on each device
+ * at start-up, before handing the device's memory to your own pool (else that
+ * first call can fail with TEL_ECUDA, out of memory), and before any stream
+ * capture.  With eager loading (CUDA_MODULE_LOADING=EAGER) every GPU holds it
+ * from the moment the library is loaded.
+ * Calls share the array: calls that overlap on the GPU race with each other.
+ * The work runs on cuda_stream (NULL: the legacy default stream) and the call
+ * synchronises it.  Errors as for tel_fields; the message is available from
+ * tel_last_error(NULL) on the calling thread. */
 #define TEL_NOALLOC_MAX_NODES 262144
 int tel_fields_noalloc(int lattice, int nx, int ny, int nz, const tel_params *params,
                        const void *f_state, const void *g_state, double *rho, double *phi,

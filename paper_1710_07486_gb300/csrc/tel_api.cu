@@ -9,7 +9,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <new>
 
 #include "ternelbm.h"
@@ -31,7 +30,11 @@ struct tel_ctx {
     char msg[512];
 };
 
-static char g_create_msg[512] = "";
+// Message of the last failing context-free call (tel_create, the
+// thermodynamics helpers, tel_batch_create, tel_fields_noalloc) on the calling
+// thread: thread-local, so concurrent failures on different threads do not
+// overwrite each other's text.
+static thread_local char g_create_msg[512] = "";
 
 static int fail(tel_ctx *c, int code, const char *fmt, ...)
 {
@@ -596,32 +599,34 @@ extern "C" int tel_set_state(tel_ctx *c, const double *f, const double *g)
 // cudaMalloc is not available to them.  tel_fields_noalloc serves them: the
 // state lives in the caller's own device buffers, the results go to the
 // caller's host buffers, and the only device memory used besides those is a
-// fixed array of this file, reserved when the library is loaded.
+// fixed array of this file.
 //
 // tel_noalloc_scratch holds (3 + D) field arrays of up to
-// TEL_NOALLOC_MAX_NODES nodes followed by the error word; every GPU that
-// loads the library keeps it until the process exits.  In host code its name
-// is only a host-side stand-in: the device address is obtained once per
-// device with cudaGetSymbolAddress (the first call on each device, with that
-// device current) and passed to the kernel.  All calls share the array: the
-// error word is cleared on every call, and calls that overlap on the GPU
-// race with each other.
+// TEL_NOALLOC_MAX_NODES nodes followed by the error word.  This translation
+// unit has no kernels, so its module holds only this array; under CUDA's lazy
+// module loading the module, and with it the array's device memory, is
+// loaded on a device by the first call there (the first address lookup) and
+// then kept until the process exits.  In host code the array's name is only a
+// host-side stand-in: its device address is looked up with
+// cudaGetSymbolAddress on every call, with the caller's device current, and
+// passed to the kernel (so no address is kept across a device reset, which
+// reloads the module, possibly elsewhere).  All calls share the array: the
+// error word is cleared on every call, and calls that overlap on the GPU race
+// with each other.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) double tel_noalloc_scratch[6 * TEL_NOALLOC_MAX_NODES + 32];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[kMaxDevices] = {nullptr};
-char g_noalloc_msg[512] = "";
-
+// failure of tel_fields_noalloc: the message goes to the calling thread's
+// context-free error text (tel_last_error(NULL))
 int noalloc_fail(int code, const char *fmt, ...)
 {
+    char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(g_noalloc_msg, sizeof(g_noalloc_msg), fmt, ap);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
-    std::snprintf(g_create_msg, sizeof(g_create_msg), "%s", g_noalloc_msg);
+    std::snprintf(g_create_msg, sizeof(g_create_msg), "%s", buf);
     return code;
 }
 }  // namespace
@@ -644,22 +649,15 @@ extern "C" int tel_fields_noalloc(int lattice, int nx, int ny, int nz, const tel
     tel_params pp = *params;
     if (lattice == TEL_D2Q9) pp.bc[2] = TEL_PERIODIC;
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(TEL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(TEL_EINVAL, "device %d out of range", dev);
-    double *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, tel_noalloc_scratch);
-            if (e != cudaSuccess)
-                return noalloc_fail(TEL_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            g_noalloc_ptr[dev] = static_cast<double *>(ptr);
-        }
-        scratch = g_noalloc_ptr[dev];
+    // device address of the fixed array on the current device (the first
+    // lookup on a device loads the array there)
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, tel_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(TEL_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     }
+    double *scratch = static_cast<double *>(ptr);
     tel::DevParams d{};
     fill_devparams(lattice, nx, ny, nz, pp, co, d);
     unsigned *err = reinterpret_cast<unsigned *>(scratch + 6 * (size_t)TEL_NOALLOC_MAX_NODES);

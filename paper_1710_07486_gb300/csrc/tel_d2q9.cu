@@ -15,13 +15,12 @@ static cudaError_t launch_batch_one(const DevParams *Ps, const LaunchArgs *As, c
                                     int grid, cudaStream_t s)
 {
     typedef Fused<2, TX, 1, ST, MODE_STEP, FAST> K;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(batch_kernel<TX, ST, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)K::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;
+    cudaError_t e = once.run([] {
+        return cudaFuncSetAttribute(batch_kernel<TX, ST, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)K::SMEM_BYTES);
+    });
+    if (e != cudaSuccess) return e;
     batch_kernel<TX, ST, FAST><<<grid, TX, K::SMEM_BYTES, s>>>(Ps, As, items, nitems);
     return cudaGetLastError();
 }

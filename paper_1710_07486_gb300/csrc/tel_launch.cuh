@@ -2,6 +2,7 @@
 #pragma once
 
 #include "tel_kernels.cuh"
+#include "tel_once.cuh"
 
 namespace tel {
 
@@ -9,13 +10,12 @@ template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = fa
 static cudaError_t launch_one(const DevParams &P, const LaunchArgs &A, cudaStream_t s)
 {
     typedef Fused<D, TX, TY, ST, MODE, FAST, VEC> K;
-    static bool configured = false;  // per-instantiation: opt in to > 48 KB of shared memory
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(fused_kernel<D, TX, TY, ST, MODE, FAST, VEC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;  // per instantiation and device: opt in to > 48 KB of shared memory
+    cudaError_t e = once.run([] {
+        return cudaFuncSetAttribute(fused_kernel<D, TX, TY, ST, MODE, FAST, VEC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM_BYTES);
+    });
+    if (e != cudaSuccess) return e;
     const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
     dim3 grid((PX + TX - 1) / TX, 1, 1);
     const int nch = (PM + P.chunk - 1) / P.chunk;

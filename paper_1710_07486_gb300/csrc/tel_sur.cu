@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "tel_once.cuh"
+
 #include <cstdint>
 
 #include "ternelbm.h"
@@ -220,13 +222,11 @@ int launch_conv(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, long l
                 int relu, cudaStream_t s)
 {
     typedef ConvCfg<COUT, BK> C;
-    static bool attr = false;  // one attribute call per instantiation (per process, current device)
-    if (!attr) {
-        if (cudaFuncSetAttribute(conv3x3_kernel<COUT, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)C::SMEM) != cudaSuccess)
-            return TEL_ECUDA;
-        attr = true;
-    }
+    static tel::DeviceOnce once;  // one attribute call per instantiation and device
+    const cudaError_t ea = once.run([] {
+        return cudaFuncSetAttribute(conv3x3_kernel<COUT, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
+    if (ea != cudaSuccess) return TEL_ECUDA;
     const unsigned grid = (unsigned)(P / CONV_BM);
     conv3x3_kernel<COUT, BK><<<grid, CONV_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu);
     return launched();
@@ -455,13 +455,11 @@ int launch_conv_tc(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, lon
                    int relu, unsigned *err, cudaStream_t s)
 {
     typedef TcCfg<COUT> C;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(conv3x3_tc_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)C::SMEM) != cudaSuccess)
-            return TEL_ECUDA;
-        attr = true;
-    }
+    static tel::DeviceOnce once;  // one attribute call per instantiation and device
+    const cudaError_t ea = once.run([] {
+        return cudaFuncSetAttribute(conv3x3_tc_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
+    if (ea != cudaSuccess) return TEL_ECUDA;
     conv3x3_tc_kernel<COUT><<<(unsigned)(P / C::BM), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu, err);
     return launched();
 }
@@ -648,13 +646,11 @@ int launch_conv_tch(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, lo
                     int relu, unsigned *err, cudaStream_t s, int up = 0, const bf16 *skip = nullptr)
 {
     typedef TchCfg<COUT, R> C;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(conv3x3_tch_kernel<COUT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)C::SMEM) != cudaSuccess)
-            return TEL_ECUDA;
-        attr = true;
-    }
+    static tel::DeviceOnce once;  // one attribute call per instantiation and device
+    const cudaError_t ea = once.run([] {
+        return cudaFuncSetAttribute(conv3x3_tch_kernel<COUT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
+    if (ea != cudaSuccess) return TEL_ECUDA;
     conv3x3_tch_kernel<COUT, R><<<(unsigned)(P / (128 * R)), TC_THREADS, C::SMEM, s>>>(x, w, bias, y, H, W, cin, relu,
                                                                                      err, up, skip);
     return launched();
@@ -800,13 +796,11 @@ int launch_wgrad(const bf16 *x, const bf16 *dz, float *dw, long long P, int H, i
                  cudaStream_t s)
 {
     typedef WgCfg<BMO, BNI> C;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(wgrad_kernel<BMO, BNI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)C::SMEM) != cudaSuccess)
-            return TEL_ECUDA;
-        attr = true;
-    }
+    static tel::DeviceOnce once;  // one attribute call per instantiation and device
+    const cudaError_t ea = once.run([] {
+        return cudaFuncSetAttribute(wgrad_kernel<BMO, BNI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
+    if (ea != cudaSuccess) return TEL_ECUDA;
     dim3 grid((unsigned)((P + WG_CHUNK - 1) / WG_CHUNK), TAPS, (unsigned)((cout / BMO) * (cin / BNI)));
     wgrad_kernel<BMO, BNI><<<grid, WG_THREADS, C::SMEM, s>>>(x, dz, dw, H, W, cin, cout, P);
     return launched();

@@ -18,14 +18,17 @@ from tests.cases import A, B, RGAS, base
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("lattice,shape,precision,tol", [
-    (tel.D2Q9, (64, 48, 1), tel.FP64, 1e-12),
-    (tel.D3Q27, (20, 16, 12), tel.FP32_SHIFTED, 1e-4),
+@pytest.mark.parametrize("lattice,shape,precision,tol,with_p,bc", [
+    (tel.D2Q9, (64, 48, 1), tel.FP64, 1e-12, True, (0, 0, 0)),
+    (tel.D3Q27, (20, 16, 12), tel.FP32_SHIFTED, 1e-4, True, (0, 0, 0)),
+    # no pressure output, bounce-back walls on one axis (the walled pull path)
+    (tel.D2Q9, (40, 36, 1), tel.FP64, 1e-12, False, (0, 1, 0)),
+    (tel.D3Q27, (16, 20, 12), tel.FP32_SHIFTED, 1e-4, False, (1, 0, 0)),
 ])
-def test_fields_noalloc_matches_context(lattice, shape, precision, tol):
+def test_fields_noalloc_matches_context(lattice, shape, precision, tol, with_p, bc):
     torch = pytest.importorskip("torch")
     T = tel.temperature_for_ratio(A, B, RGAS, 10.0)
-    p = dict(base(T), precision=precision)
+    p = dict(base(T), precision=precision, bc=bc)
     nx, ny, nz = shape
     lat = tel.Lattice(lattice, nx, ny, nz, p)
     D = lat.D
@@ -39,7 +42,7 @@ def test_fields_noalloc_matches_context(lattice, shape, precision, tol):
     shift = lat.rho_g if precision == tel.FP32_SHIFTED else 0.0
     for call in range(2):
         lat.step(3 + call)
-        ref = lat.fields()
+        ref = lat.fields(with_p=with_p)
         f, g = lat.get_state()
         if precision == tel.FP64:
             fd = torch.tensor(f, dtype=torch.float64, device="cuda")
@@ -48,8 +51,10 @@ def test_fields_noalloc_matches_context(lattice, shape, precision, tol):
             fd = torch.tensor(f - w[:, None] * shift, dtype=torch.float32, device="cuda")
             gd = torch.tensor(g, dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
-        got = tel.fields_noalloc(lattice, nx, ny, nz, p, fd, gd)
-        for k in ("rho", "phi", "u", "p"):
+        got = tel.fields_noalloc(lattice, nx, ny, nz, p, fd, gd, with_p=with_p)
+        if not with_p:
+            assert got["p"] is None
+        for k in ("rho", "phi", "u") + (("p",) if with_p else ()):
             scale = max(np.abs(ref[k]).max(), 1e-3)
             assert np.max(np.abs(got[k] - ref[k])) / scale < tol, (call, k)
 
@@ -68,3 +73,27 @@ def tel_w(lattice, i):
     c = [i % 3 - 1, (i // 3) % 3 - 1] + ([i // 9 - 1] if lattice == tel.D3Q27 else [])
     w1 = {0: 2.0 / 3.0, 1: 1.0 / 6.0, -1: 1.0 / 6.0}
     return float(np.prod([w1[v] for v in c]))
+
+
+def test_fields_noalloc_reports_a_flagged_node_then_recovers():
+    """A state whose density is zero everywhere makes the fields kernel raise
+    its error word (non-positive density): the call returns TEL_EUNSTABLE.
+    The next call clears the shared error word and succeeds."""
+    torch = pytest.importorskip("torch")
+    T = tel.temperature_for_ratio(A, B, RGAS, 10.0)
+    p = base(T)
+    nx, ny = 16, 12
+    zeros = torch.zeros(9 * nx * ny, dtype=torch.float64, device="cuda")
+    with pytest.raises(tel.TelError) as ei:
+        tel.fields_noalloc(tel.D2Q9, nx, ny, 1, p, zeros, zeros, with_p=False)
+    assert ei.value.code == tel.TEL_EUNSTABLE
+    lat = tel.Lattice(tel.D2Q9, nx, ny, 1, p)
+    rho, phi, u = inputs.drops((nx, ny), lat.rho_g, lat.rho_l, p["chi"],
+                               [dict(center=(8.0, 6.0), R=4.0, kind=1)], width=4.0)
+    lat.init(rho, phi, u)
+    f, g = lat.get_state()
+    fd = torch.tensor(f, dtype=torch.float64, device="cuda")
+    gd = torch.tensor(g, dtype=torch.float64, device="cuda")
+    got = tel.fields_noalloc(tel.D2Q9, nx, ny, 1, p, fd, gd, with_p=False)
+    ref = lat.fields(with_p=False)
+    assert np.max(np.abs(got["rho"] - ref["rho"])) / lat.rho_l < 1e-12
