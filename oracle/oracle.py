@@ -31,10 +31,11 @@ class Params(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "a", "b", "R", "T", "lambda1", "lambda2", "lambda3",
         "kappa1", "kappa2", "kappa3", "chi", "nu", "Gamma", "tau_g")] + [
-        ("force_form", C.c_int), ("eos", C.c_int), ("omega", C.c_double)]
+        ("force_form", C.c_int), ("eos", C.c_int), ("omega", C.c_double), ("gamma_mode", C.c_int)]
 
 
 CS, VDW, PR = 0, 1, 2  # equations of state
+GAMMA_CLOSED, GAMMA_EXACT = 0, 1  # stabiliser: closed form or exact root
 
 
 class Eos(C.Structure):
@@ -108,6 +109,10 @@ def lib():
         L.orc_feq.restype = None
         L.orc_collide_f.argtypes = [C.c_void_p, dp, dp, dp, C.c_void_p, C.POINTER(d)]
         L.orc_collide_f.restype = C.c_int
+        L.orc_gamma_exact.argtypes = [C.c_void_p, dp, dp, dp, d, C.POINTER(d)]
+        L.orc_gamma_exact.restype = C.c_int
+        L.orc_gamma_fallbacks.argtypes = [C.c_void_p]
+        L.orc_gamma_fallbacks.restype = C.c_long
         L.orc_geq.argtypes = [C.c_void_p, d, d, dp, dp]
         L.orc_geq.restype = None
         L.orc_collide_g.argtypes = [C.c_void_p, dp, d, d, dp, dp]
@@ -224,9 +229,11 @@ class Oracle:
         self.lattice = lattice
         self.nx, self.ny, self.nz = nx, ny, nz
         self.params = dict(params)
-        vals = {k: float(params[k]) for k, _ in Params._fields_ if k not in ("force_form", "eos", "omega")}
+        ints = ("force_form", "eos", "omega", "gamma_mode")
+        vals = {k: float(params[k]) for k, _ in Params._fields_ if k not in ints}
         p = Params(force_form=int(params.get("force_form", 1)), eos=int(params.get("eos", CS)),
-                   omega=float(params.get("omega", 0.0)), **vals)
+                   omega=float(params.get("omega", 0.0)),
+                   gamma_mode=int(params.get("gamma_mode", GAMMA_CLOSED)), **vals)
         bca = np.asarray(bc, dtype=np.int32)
         self._h = lib().orc_create(lattice, nx, ny, nz, C.byref(p), bca)
         if not self._h:
@@ -270,6 +277,16 @@ class Oracle:
         if rc != 0:
             raise FloatingPointError(f"orc_collide_f rc={rc}")
         return fo, ds, g.value
+
+    def gamma_exact(self, feq, ds, dh, gamma0):
+        """(iterations or -1 on fallback, gamma) of the exact stabiliser."""
+        g = C.c_double()
+        it = lib().orc_gamma_exact(self._h, _f64(feq, self.Q), _f64(ds, self.Q), _f64(dh, self.Q),
+                                   float(gamma0), C.byref(g))
+        return it, g.value
+
+    def gamma_fallbacks(self):
+        return int(lib().orc_gamma_fallbacks(self._h))
 
     def geq(self, phi, mu_phi, u):
         out = np.zeros(self.Q)

@@ -30,6 +30,7 @@ struct orc_ctx {
     double w[27];
     int opp[27];
     int rest;
+    long *gamma_fallbacks;  /* counter of exact-stabiliser fallbacks */
 };
 
 /* ------------------------------------------------------------------------- */
@@ -351,6 +352,8 @@ orc_ctx *orc_create(int lattice, int nx, int ny, int nz, const orc_params *p,
     if (lattice == 0 && nz != 1) return NULL;
     orc_ctx *o = (orc_ctx *)calloc(1, sizeof(orc_ctx));
     if (!o) return NULL;
+    o->gamma_fallbacks = (long *)calloc(1, sizeof(long));
+    if (!o->gamma_fallbacks) { free(o); return NULL; }
     o->D = lattice == 0 ? 2 : 3;
     o->Q = lattice == 0 ? 9 : 27;
     o->nx = nx; o->ny = ny; o->nz = nz;
@@ -384,7 +387,7 @@ orc_ctx *orc_create(int lattice, int nx, int ny, int nz, const orc_params *p,
     }
     double co[4];
     orc_eos e = {p->eos, p->a, p->b, p->R, p->T, p->omega};
-    if (orc_eos_coexistence(&e, co)) { free(o); return NULL; }
+    if (orc_eos_coexistence(&e, co)) { free(o->gamma_fallbacks); free(o); return NULL; }
     o->rho_g = co[0]; o->rho_l = co[1]; o->mu_coex = co[2]; o->p_coex = co[3];
     /* nu = c_s^2 (tau - 1/2) with c_s^2 = 1/3; KBC uses beta = 1/(2 tau) */
     o->tau = 3.0 * p->nu + 0.5;
@@ -392,7 +395,12 @@ orc_ctx *orc_create(int lattice, int nx, int ny, int nz, const orc_params *p,
     return o;
 }
 
-void orc_destroy(orc_ctx *o) { free(o); }
+void orc_destroy(orc_ctx *o)
+{
+    if (o) free(o->gamma_fallbacks);
+    free(o);
+}
+long orc_gamma_fallbacks(const orc_ctx *o) { return *o->gamma_fallbacks; }
 int orc_Q(const orc_ctx *o) { return o->Q; }
 long orc_N(const orc_ctx *o) { return o->N; }
 
@@ -650,6 +658,73 @@ static double dual_vec(const orc_ctx *o, int i, const int e[3])
     return v;
 }
 
+/* Exact stabiliser (reading of "gamma solved per node"): the KBC collision
+   f'(gamma) = f - beta (2 Delta s + gamma Delta h) keeps the relaxation of the
+   stress part fixed and picks gamma so that the post-collision state has the
+   largest entropy along this line, i.e. minimises H(f') = sum_i f'_i ln(f'_i/w_i).
+   dH/dgamma = -beta sum_i Delta h_i (ln(f'_i/w_i) + 1); the +1 drops because
+   Delta h carries no mass, and ln(feq_i/w_i) is affine in c_i for the entropic
+   equilibrium while Delta h carries no mass or momentum, so the condition is
+     G = sum_i Delta h_i ln(f'_i / feq_i) = 0.
+   Its second-order expansion in f - f^eq is the closed form of the collision.
+   Written in t = 1 - beta gamma:  f'_i(t) = A_i + t Delta h_i with
+   A_i = feq_i + (1 - 2 beta) Delta s_i, so G(t) is strictly increasing,
+   G'(t) = sum_i Delta h_i^2 / f'_i(t), on the interval where every f'_i > 0,
+   and runs from -inf to +inf across it: the root is unique.  Found by Newton
+   from the closed form, kept inside a bracket by bisection. */
+int orc_gamma_exact(const orc_ctx *o, const double *feq, const double *ds, const double *dh,
+                    double gamma0, double *gamma)
+{
+    int Q = o->Q;
+    double beta = o->beta;
+    double A[27];
+    double lo = -HUGE_VAL, hi = HUGE_VAL;
+    *gamma = gamma0;
+    for (int i = 0; i < Q; i++) {
+        A[i] = feq[i] + (1.0 - 2.0 * beta) * ds[i];
+        if (dh[i] > 0.0) {
+            double b = -A[i] / dh[i];
+            if (b > lo) lo = b;
+        } else if (dh[i] < 0.0) {
+            double b = -A[i] / dh[i];
+            if (b < hi) hi = b;
+        } else if (!(A[i] > 0.0)) {
+            return -1;
+        }
+    }
+    if (!(lo < hi) || !isfinite(lo) || !isfinite(hi)) return -1;
+    double t = 1.0 - beta * gamma0;
+    if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+    double a = lo, b = hi;
+    for (int it = 1; it <= ORC_GAMMA_MAX_ITER; it++) {
+        double G = 0.0, dG = 0.0, S = 0.0;
+        for (int i = 0; i < Q; i++) {
+            double x = ((1.0 - 2.0 * beta) * ds[i] + t * dh[i]) / feq[i];
+            double term = dh[i] * log1p(x);
+            G += term;
+            S += fabs(term);
+            dG += dh[i] * dh[i] / (feq[i] * (1.0 + x));
+        }
+        /* converged: G vanishes to the rounding of its terms */
+        if (fabs(G) <= 1e-13 * S) {
+            *gamma = (1.0 - t) / beta;
+            return it;
+        }
+        if (G > 0.0) b = t; else a = t;
+        if (!(b - a > 1e-15 * (1.0 + fabs(t)))) {
+            *gamma = (1.0 - 0.5 * (a + b)) / beta;
+            return it;
+        }
+        /* Newton step, or bisection when it leaves the bracket or stalls
+           (next to a pole of ln f'_i the derivative is huge and the step
+           tiny) */
+        double tn = t - G / dG;
+        if (!(tn > a && tn < b) || fabs(tn - t) <= 1e-15 * (1.0 + fabs(t))) tn = 0.5 * (a + b);
+        t = tn;
+    }
+    return -1;
+}
+
 int orc_collide_f(const orc_ctx *o, const double *f, const double F[3],
                   double *fout, double *ds_out, double *gamma)
 {
@@ -707,7 +782,14 @@ int orc_collide_f(const orc_ctx *o, const double *f, const double F[3],
     }
     double beta = o->beta;
     double g = 2.0;
-    if (hh > 1e-30 * rho * rho) g = 1.0 / beta - (2.0 - 1.0 / beta) * sh / hh;
+    if (hh > 1e-30 * rho * rho) {
+        g = 1.0 / beta - (2.0 - 1.0 / beta) * sh / hh;
+        if (o->p.gamma_mode == ORC_GAMMA_EXACT) {
+            double ge;
+            if (orc_gamma_exact(o, feq, ds, dh, g, &ge) >= 0) g = ge;
+            else (*o->gamma_fallbacks)++;
+        }
+    }
     for (int i = 0; i < Q; i++) {
         fout[i] = f[i] - beta * (2.0 * ds[i] + g * dh[i]) + (feqF[i] - feq[i]);
         if (ds_out) ds_out[i] = ds[i];

@@ -38,7 +38,14 @@ typedef struct {
     int force_form;                    /* 0 potential form, 1 lattice-consistent */
     int eos;                           /* ORC_EOS_CS (Eq. 4), ORC_EOS_VDW, ORC_EOS_PR */
     double omega;                      /* Peng-Robinson acentric factor          */
+    int gamma_mode;                    /* ORC_GAMMA_CLOSED or ORC_GAMMA_EXACT    */
 } orc_params;
+
+/* Stabiliser of the KBC collision: the closed form (the root of the entropy
+   condition to second order in f - f^eq) or the exact per-node root of the
+   entropy condition (safeguarded Newton, falling back to the closed form). */
+enum { ORC_GAMMA_CLOSED = 0, ORC_GAMMA_EXACT = 1 };
+#define ORC_GAMMA_MAX_ITER 20
 
 /* Equations of state: Carnahan-Starling (Eq. 4), and the van der Waals and
    Peng-Robinson forms the text names as alternatives (textbook forms). */
@@ -90,6 +97,18 @@ void orc_feq(const orc_ctx *o, double rho, const double u[3], double *feq);
    Returns gamma in *gamma. */
 int orc_collide_f(const orc_ctx *o, const double *f, const double F[3],
                   double *fout, double *ds_out, double *gamma);
+/* Exact stabiliser: the root gamma of the entropy condition
+     sum_i dh_i ln(f'_i(gamma) / feq_i) = 0,  f'(gamma) = f - beta (2 ds + gamma dh)
+   for one node, given f^eq, Delta s and Delta h = f - f^eq - Delta s.  Starts
+   from gamma0.  Returns the number of Newton/bisection iterations (>= 0) with
+   *gamma the root, or -1 when there is no admissible gamma (some f'_i <= 0
+   for every gamma) or the iteration did not converge in ORC_GAMMA_MAX_ITER
+   steps; then *gamma = gamma0. */
+int orc_gamma_exact(const orc_ctx *o, const double *feq, const double *ds, const double *dh,
+                    double gamma0, double *gamma);
+/* Number of nodes whose exact stabiliser fell back to the closed form since
+   the context was created (ORC_GAMMA_EXACT only). */
+long orc_gamma_fallbacks(const orc_ctx *o);
 void orc_geq(const orc_ctx *o, double phi, double mu_phi, const double u[3],
              double *geq);
 void orc_collide_g(const orc_ctx *o, const double *g, double phi, double mu_phi,
