@@ -89,7 +89,26 @@ typedef struct {
     int bc[3];                        /* tel_bc per axis (bc[2] ignored for D2Q9) */
     int eos;                          /* tel_eos: TEL_EOS_CS (Eq. 4, default 0), TEL_EOS_VDW, TEL_EOS_PR */
     double omega;                     /* Peng-Robinson acentric factor (TEL_EOS_PR only) */
+    int gamma_mode;                   /* tel_gamma_mode: TEL_GAMMA_CLOSED (default 0) or TEL_GAMMA_EXACT */
 } tel_params;
+
+/* Stabiliser gamma of the KBC collision f' = f - beta (2 Delta s + gamma
+ * Delta h) (the entropic scheme named after Eq. 8):
+ *   TEL_GAMMA_CLOSED: gamma = 1/beta - (2 - 1/beta) <Delta s|Delta h>/<Delta h|Delta h>,
+ *     <X|Y> = sum_i X_i Y_i / feq_i, the root of the entropy condition below
+ *     expanded to second order in f - f^eq;
+ *   TEL_GAMMA_EXACT: per node, the root of the entropy condition
+ *     sum_i Delta h_i ln(f'_i / feq_i) = 0 (the gamma that maximises the
+ *     entropy of f' on the collision line), by bracketed Newton from the
+ *     closed form (at most 20 evaluations; FP64, or FP32 in the FP32 mode).
+ *     Where no gamma keeps every f'_i positive, or the iteration does not
+ *     converge, the node keeps the closed form and a device counter is
+ *     incremented (tel_gamma_fallbacks).  Where Delta h has entries of one
+ *     sign only -- a massless Delta h does so only as rounding noise -- the
+ *     closed form is kept without counting.
+ * gamma = 2 (BGK) wherever <Delta h|Delta h> <= 1e-30 rho^2.  Batches
+ * (tel_batch_*) use the closed form. */
+typedef enum { TEL_GAMMA_CLOSED = 0, TEL_GAMMA_EXACT = 1 } tel_gamma_mode;
 
 /* Equations of state.  TEL_EOS_CS is Eq. 4 (Carnahan-Starling).  The text
  * names van der Waals and Peng-Robinson as alternatives (their formulas are
@@ -147,6 +166,10 @@ int tel_step(tel_ctx *ctx, int nsteps);
 /* Wait for the context's stream and report the device's instability flag
  * (TEL_EUNSTABLE), then clear it. */
 int tel_sync(tel_ctx *ctx);
+
+/* Number of nodes (summed over steps) whose exact stabiliser fell back to the
+ * closed form since tel_create (TEL_GAMMA_EXACT only).  Synchronises. */
+int tel_gamma_fallbacks(tel_ctx *ctx, unsigned long long *count);
 
 /* Macroscopic fields of the current state, on the host: rho, phi, physical
  * velocity u = (j + F/2)/rho [D*N], and (if p != NULL) the isotropic part of

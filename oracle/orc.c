@@ -679,7 +679,15 @@ int orc_gamma_exact(const orc_ctx *o, const double *feq, const double *ds, const
     double beta = o->beta;
     double A[27];
     double lo = -HUGE_VAL, hi = HUGE_VAL;
+    int npos = 0, nneg = 0;
     *gamma = gamma0;
+    /* Delta h carries no mass, so it has entries of both signs unless it is
+       rounding noise; then the closed form is kept (not a failure) */
+    for (int i = 0; i < Q; i++) {
+        npos += dh[i] > 0.0;
+        nneg += dh[i] < 0.0;
+    }
+    if (npos == 0 || nneg == 0) return -2;
     for (int i = 0; i < Q; i++) {
         A[i] = feq[i] + (1.0 - 2.0 * beta) * ds[i];
         if (dh[i] > 0.0) {
@@ -786,8 +794,9 @@ int orc_collide_f(const orc_ctx *o, const double *f, const double F[3],
         g = 1.0 / beta - (2.0 - 1.0 / beta) * sh / hh;
         if (o->p.gamma_mode == ORC_GAMMA_EXACT) {
             double ge;
-            if (orc_gamma_exact(o, feq, ds, dh, g, &ge) >= 0) g = ge;
-            else (*o->gamma_fallbacks)++;
+            int it = orc_gamma_exact(o, feq, ds, dh, g, &ge);
+            if (it >= 0) g = ge;
+            else if (it == -1) (*o->gamma_fallbacks)++;
         }
     }
     for (int i = 0; i < Q; i++) {

@@ -101,9 +101,11 @@ int orc_collide_f(const orc_ctx *o, const double *f, const double F[3],
      sum_i dh_i ln(f'_i(gamma) / feq_i) = 0,  f'(gamma) = f - beta (2 ds + gamma dh)
    for one node, given f^eq, Delta s and Delta h = f - f^eq - Delta s.  Starts
    from gamma0.  Returns the number of Newton/bisection iterations (>= 0) with
-   *gamma the root, or -1 when there is no admissible gamma (some f'_i <= 0
-   for every gamma) or the iteration did not converge in ORC_GAMMA_MAX_ITER
-   steps; then *gamma = gamma0. */
+   *gamma the root; -1 when there is no admissible gamma (some f'_i <= 0 for
+   every gamma) or the iteration did not converge in ORC_GAMMA_MAX_ITER steps
+   (a fallback); -2 when Delta h has entries of one sign only, which a
+   massless Delta h can only have as rounding noise (not a fallback).  In
+   both negative cases *gamma = gamma0. */
 int orc_gamma_exact(const orc_ctx *o, const double *feq, const double *ds, const double *dh,
                     double gamma0, double *gamma);
 /* Number of nodes whose exact stabiliser fell back to the closed form since

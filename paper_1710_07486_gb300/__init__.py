@@ -17,12 +17,13 @@ import numpy as np
 
 __all__ = ["Lattice", "lib", "coexistence", "temperature_for_ratio", "TelError",
            "D2Q9", "D3Q27", "FP64", "FP32_SHIFTED", "PERIODIC", "BOUNCEBACK",
-           "FORCE_POTENTIAL", "FORCE_LATTICE"]
+           "FORCE_POTENTIAL", "FORCE_LATTICE", "GAMMA_CLOSED", "GAMMA_EXACT"]
 
 D2Q9, D3Q27 = 0, 1
 FP64, FP32_SHIFTED = 0, 1
 PERIODIC, BOUNCEBACK = 0, 1
 FORCE_POTENTIAL, FORCE_LATTICE = 0, 1
+GAMMA_CLOSED, GAMMA_EXACT = 0, 1
 EOS_CS, EOS_VDW, EOS_PR = 0, 1, 2
 
 TEL_OK, TEL_EINVAL, TEL_ENOMEM, TEL_ECUDA, TEL_EUNSTABLE, TEL_ESTATE = 0, -1, -2, -3, -4, -5
@@ -44,12 +45,12 @@ class Params(C.Structure):
         "a", "b", "R", "T", "lambda1", "lambda2", "lambda3", "kappa1", "kappa2",
         "kappa3", "chi", "nu", "Gamma", "tau_g", "rho_ref")] + [
         ("precision", C.c_int), ("force_form", C.c_int), ("bc", C.c_int * 3), ("eos", C.c_int),
-        ("omega", C.c_double)]
+        ("omega", C.c_double), ("gamma_mode", C.c_int)]
 
 
 _lib = None
 SYMBOLS = ("tel_create", "tel_destroy", "tel_last_error", "tel_set_stream", "tel_init",
-           "tel_init_device", "tel_step", "tel_sync", "tel_fields", "tel_fields_device",
+           "tel_init_device", "tel_step", "tel_sync", "tel_gamma_fallbacks", "tel_fields", "tel_fields_device",
            "tel_get_state", "tel_set_state", "tel_info", "tel_coexistence",
            "tel_temperature_for_ratio", "tel_coexistence_eos", "tel_temperature_for_ratio_eos",
            "tel_fields_noalloc", "tel_batch_create",
@@ -81,6 +82,7 @@ def lib(build: bool = True):
         getattr(L, name).argtypes = [vp, vp, vp, vp]
     L.tel_step.argtypes = [vp, i]
     L.tel_sync.argtypes = [vp]
+    L.tel_gamma_fallbacks.argtypes = [vp, C.POINTER(C.c_ulonglong)]
     for name in ("tel_fields", "tel_fields_device"):
         getattr(L, name).argtypes = [vp, vp, vp, vp, vp]
     L.tel_get_state.argtypes = [vp, vp, vp]
@@ -150,6 +152,7 @@ def _params_struct(p):
         s.bc[k] = int(bcs[k])
     s.eos = int(p.get("eos", EOS_CS))
     s.omega = float(p.get("omega", 0.0))
+    s.gamma_mode = int(p.get("gamma_mode", GAMMA_CLOSED))
     return s
 
 
@@ -339,6 +342,12 @@ class Lattice:
 
     def sync(self):
         self._check(self._L.tel_sync(self._h))
+
+    def gamma_fallbacks(self):
+        """Nodes whose exact stabiliser fell back to the closed form so far."""
+        n = C.c_ulonglong()
+        self._check(self._L.tel_gamma_fallbacks(self._h, C.byref(n)))
+        return int(n.value)
 
     def fields(self, with_p=True):
         rho = np.empty(self.N)

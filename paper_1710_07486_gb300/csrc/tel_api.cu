@@ -23,6 +23,7 @@ struct tel_ctx {
     int cur;
     unsigned *d_err;
     unsigned *h_err;  // pinned
+    unsigned long long *d_gfall;  // exact-stabiliser fallbacks
     double *scratch;  // FP64 fields / state staging, lazily allocated
     size_t scratch_elems;
     cudaStream_t own_stream, stream;
@@ -274,6 +275,7 @@ static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
     if (p->precision != TEL_FP64 && p->precision != TEL_FP32_SHIFTED) return fail(nullptr, TEL_EINVAL, "bad precision");
     if (p->eos != TEL_EOS_CS && p->eos != TEL_EOS_VDW && p->eos != TEL_EOS_PR) return fail(nullptr, TEL_EINVAL, "bad eos");
     if (p->force_form != TEL_FORCE_POTENTIAL && p->force_form != TEL_FORCE_LATTICE) return fail(nullptr, TEL_EINVAL, "bad force_form");
+    if (p->gamma_mode != TEL_GAMMA_CLOSED && p->gamma_mode != TEL_GAMMA_EXACT) return fail(nullptr, TEL_EINVAL, "bad gamma_mode");
     for (int a = 0; a < 3; ++a)
         if (p->bc[a] != TEL_PERIODIC && p->bc[a] != TEL_BOUNCEBACK) return fail(nullptr, TEL_EINVAL, "bad bc[%d]", a);
     if (((long long)nx * ny * nz) >= (1LL << 31)) return fail(nullptr, TEL_EINVAL, "lattice too large (N must be < 2^31)");
@@ -345,6 +347,7 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
     d.Gamma = p.Gamma;
     d.inv_tau_g = 1.0 / p.tau_g;
     d.rho_ref = p.precision == TEL_FP32_SHIFTED ? (p.rho_ref > 0 ? p.rho_ref : co[0]) : 0.0;
+    d.gamma_mode = p.gamma_mode;
     fill_coef(d, d.cf);
     fill_coef(d, d.cd);
 }
@@ -383,9 +386,11 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
         if (e == cudaSuccess) e = cudaMalloc(&c->g[k], bytes);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_gfall, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->own_stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gfall, 0, sizeof(unsigned long long), c->own_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->own_stream);
     if (e != cudaSuccess) {
         const bool oom = e == cudaErrorMemoryAllocation;
@@ -395,6 +400,7 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     }
     c->stream = c->own_stream;
     d.err = c->d_err;
+    d.gfall = c->d_gfall;
     *out = c;
     return TEL_OK;
 }
@@ -408,6 +414,7 @@ extern "C" void tel_destroy(tel_ctx *c)
         if (c->g[k]) cudaFree(c->g[k]);
     }
     if (c->d_err) cudaFree(c->d_err);
+    if (c->d_gfall) cudaFree(c->d_gfall);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->scratch) cudaFree(c->scratch);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -508,7 +515,7 @@ extern "C" int tel_step(tel_ctx *c, int nsteps)
         tel::LaunchArgs A{};
         A.fsrc = c->f[c->cur]; A.gsrc = c->g[c->cur];
         A.fdst = c->f[1 - c->cur]; A.gdst = c->g[1 - c->cur];
-        CUDA_OR_FAIL(c, launch(c, tel::MODE_STEP, A));
+        CUDA_OR_FAIL(c, launch(c, c->p.gamma_mode == TEL_GAMMA_EXACT ? tel::MODE_STEP_EXACT : tel::MODE_STEP, A));
         c->cur = 1 - c->cur;
     }
     return TEL_OK;
@@ -518,6 +525,14 @@ extern "C" int tel_sync(tel_ctx *c)
 {
     if (!c) return TEL_EINVAL;
     return check_flag(c);
+}
+
+extern "C" int tel_gamma_fallbacks(tel_ctx *c, unsigned long long *count)
+{
+    if (!c || !count) return c ? fail(c, TEL_EINVAL, "tel_gamma_fallbacks: NULL count") : TEL_EINVAL;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(count, c->d_gfall, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return TEL_OK;
 }
 
 extern "C" int tel_fields_device(tel_ctx *c, double *rho, double *phi, double *u, double *p)
@@ -793,6 +808,8 @@ extern "C" int tel_batch_create(int ncases, const int *nx, const int *ny, const 
         int rc = validate(TEL_D2Q9, nx[c], ny[c], 1, &params[c]);
         if (rc) return bfail(nullptr, rc, "case %d: %s", c, g_create_msg);
         if (params[c].precision != prec) return bfail(nullptr, TEL_EINVAL, "all cases must share one precision");
+        if (params[c].gamma_mode != TEL_GAMMA_CLOSED)
+            return bfail(nullptr, TEL_EINVAL, "case %d: batches use the closed-form stabiliser (gamma_mode 0)", c);
         walls = walls || params[c].bc[0] || params[c].bc[1];
         total += (long long)nx[c] * ny[c];
     }

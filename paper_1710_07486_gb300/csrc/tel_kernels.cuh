@@ -27,7 +27,9 @@
 
 namespace tel {
 
-enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_FIELDS = 2 };
+// MODE_STEP_EXACT: the step with the exact per-node stabiliser (root of the
+// entropy condition) instead of its closed form.
+enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_FIELDS = 2, MODE_STEP_EXACT = 3 };
 
 // Equations of state (values of tel_eos): Carnahan-Starling (Eq. 4), and the
 // textbook van der Waals and Peng-Robinson forms named as alternatives.
@@ -80,7 +82,9 @@ struct DevParams {
     double c_gb;                      // 2 beta - 1: beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh>
     double Gamma, inv_tau_g;
     double rho_ref;                   // FP32 shift (0 in FP64)
+    int gamma_mode;                   // 0 closed-form stabiliser, 1 exact root
     unsigned *err;                    // device error word
+    unsigned long long *gfall;        // count of exact-stabiliser fallbacks
     Coef<float> cf;
     Coef<double> cd;
 };
@@ -333,6 +337,72 @@ __device__ __forceinline__ void eq_factors_f(float u, float e[3])
     e[0] = (S - 2.f * u) * (1.f - u) * r;
 }
 
+// ---------------------------------------------------------------------------
+// Exact stabiliser.  The KBC collision f' = f - beta (2 Delta s + gamma
+// Delta h) fixes the relaxation of the stress part; gamma is the value that
+// maximises the entropy of f' on this line, i.e. the root of
+//   G = sum_i Delta h_i ln(f'_i / feq_i) = 0
+// (the +1 of dH/dgamma and ln(feq_i/w_i), affine in c_i, drop because Delta h
+// carries no mass or momentum).  In t = 1 - beta gamma,
+// f'_i = feq_i + (1 - 2 beta) Delta s_i + t Delta h_i, G is strictly
+// increasing on the interval where every f'_i > 0 and spans (-inf, inf)
+// there, so the root is unique.  Newton from the closed form's t, kept in a
+// bracket by bisection (also when a step next to a pole of ln f'_i stalls);
+// at most GAMMA_MAX_ITER evaluations.  parts(i, feq, ds, dh) supplies the
+// node's values of velocity i.  Returns 1 with t the root; 0 when Delta h has
+// entries of one sign only, which a massless Delta h has only as rounding
+// noise (the caller keeps the closed form); -1 when no t keeps every f'_i
+// positive or the iteration does not converge (the caller keeps the closed
+// form and counts a fallback).
+// ---------------------------------------------------------------------------
+constexpr int GAMMA_MAX_ITER = 20;
+template <typename T> __device__ __forceinline__ T log1p_(T x);
+template <> __device__ __forceinline__ double log1p_<double>(double x) { return log1p(x); }
+template <> __device__ __forceinline__ float log1p_<float>(float x) { return log1pf(x); }
+
+template <typename T, int Q, typename Parts>
+__device__ __forceinline__ int gamma_root(const Parts &parts, T beta, T &t, T tolG, T tolT)
+{
+    const T c = (T)1 - (T)2 * beta;
+    T lo = -(T)INFINITY, hi = (T)INFINITY;
+    bool ok = true, pos = false, neg = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T fe, ds, dh;
+        parts(i, fe, ds, dh);
+        const T A = fe + c * ds;
+        pos = pos || dh > (T)0;
+        neg = neg || dh < (T)0;
+        if (dh > (T)0) lo = fmax(lo, -A / dh);
+        else if (dh < (T)0) hi = fmin(hi, -A / dh);
+        else if (!(A > (T)0)) ok = false;
+    }
+    if (!pos || !neg) return 0;
+    if (!ok || !(lo < hi) || !isfinite(lo) || !isfinite(hi)) return -1;
+    T tt = (t > lo && t < hi) ? t : (T)0.5 * (lo + hi);
+    T a = lo, b = hi;
+    for (int it = 0; it < GAMMA_MAX_ITER; ++it) {
+        T G = 0, dG = 0, S = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T fe, ds, dh;
+            parts(i, fe, ds, dh);
+            const T x = (c * ds + tt * dh) / fe;
+            const T term = dh * log1p_<T>(x);
+            G += term;
+            S += fabs(term);
+            dG += dh * dh / (fe * ((T)1 + x));
+        }
+        if (fabs(G) <= tolG * S) { t = tt; return 1; }
+        if (G > (T)0) b = tt; else a = tt;
+        if (!(b - a > tolT * ((T)1 + fabs(tt)))) { t = (T)0.5 * (a + b); return 1; }
+        T tn = tt - G / dG;
+        if (!(tn > a && tn < b) || fabs(tn - tt) <= tolT * ((T)1 + fabs(tt))) tn = (T)0.5 * (a + b);
+        tt = tn;
+    }
+    return -1;
+}
+
 template <typename ST> struct StoreTraits;
 template <> struct StoreTraits<double> { typedef double CT; static constexpr bool shifted = false; };
 template <> struct StoreTraits<float> { typedef float CT; static constexpr bool shifted = true; };
@@ -353,6 +423,8 @@ struct Fused {
     typedef typename V::v4 V4;
     static constexpr int Q = L::Q;
     static constexpr int NT = TX * TY;
+    static constexpr bool STEPPING = MODE == MODE_STEP || MODE == MODE_STEP_EXACT;
+    static constexpr bool EXACT = MODE == MODE_STEP_EXACT;
     static constexpr int R2X = TX + 4, R2Y = (D == 3 ? TY + 4 : 1), NA = R2X * R2Y;
     static constexpr int R1X = TX + 2, R1Y = (D == 3 ? TY + 2 : 1), NB = R1X * R1Y;
     static constexpr int OY2 = (D == 3 ? 2 : 0), OY1 = (D == 3 ? 1 : 0);
@@ -360,7 +432,7 @@ struct Fused {
     // (x0 - 4 .. x0 + TX + 3) in lanes 0-29; warps 0-3 sum f, warps 4-7 g,
     // over the TY + 4 rows of tile + ring 2
     static constexpr int NAV = 256;
-    static_assert(!VEC || (D == 3 && TX == 32 && TY == 8 && MODE == MODE_STEP && FAST &&
+    static_assert(!VEC || (D == 3 && TX == 32 && TY == 8 && STEPPING && FAST &&
                            StoreTraits<ST>::shifted), "vector phase A: D3Q27 32 x 8 FP32 periodic step");
 
     // shared memory layout (in CT units)
@@ -379,7 +451,7 @@ struct Fused {
     // FP64 storage: [Q][NT] pulled populations.  FP32 storage: [REST][NT]
     // pairs of pulled populations (the rest population stays in a register).
     static constexpr int STASH = StoreTraits<ST>::shifted ? 2 * L::REST * NT : Q * NT;
-    static constexpr int SMEM_ELEMS = OFF_F + (MODE == MODE_STEP ? STASH : 0);
+    static constexpr int SMEM_ELEMS = OFF_F + (STEPPING ? STASH : 0);
     static constexpr size_t SMEM_BYTES = sizeof(CT) * SMEM_ELEMS;
 
     __device__ static __forceinline__ int idx2(int ox, int oy) { return (ox + 2) + R2X * (oy + OY2); }
@@ -674,7 +746,7 @@ struct Fused {
         // register).
         Nbr nbc;
         CT f_rest = 0;
-        if constexpr (StoreTraits<ST>::shifted && MODE == MODE_STEP) {
+        if constexpr (StoreTraits<ST>::shifted && STEPPING) {
             make_nbr(P, PX, PY, PM, x, y, m, nbc);
             CT *col = stash + 2 * (tx + TX * ty);
 #pragma unroll
@@ -770,7 +842,7 @@ struct Fused {
             init_node(P, A, n, x, y, m, rho, phi, mu_phi, F);
             return;
         }
-        if constexpr (StoreTraits<ST>::shifted && MODE == MODE_STEP) {
+        if constexpr (StoreTraits<ST>::shifted && STEPPING) {
             collide_pairs(P, A, gs, nbc, f_rest, reinterpret_cast<float2 *>(stash) + (tx + TX * ty), n, rho, phi,
                           mu_phi, F);
             return;
@@ -786,7 +858,7 @@ struct Fused {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const CT fi = pull(fs, nb, P.N, i);
-            if (MODE == MODE_STEP) fq[i * NT] = fi;
+            if (STEPPING) fq[i * NT] = fi;
             if (L::cx(i)) { j[0] += (CT)L::cx(i) * fi; Pi[0] += fi; }
             if (L::cy(i)) { j[1] += (CT)L::cy(i) * fi; Pi[1] += fi; }
             if (D == 3 && L::cz(i)) { j[2] += (CT)L::cz(i) * fi; Pi[2] += fi; }
@@ -893,7 +965,21 @@ struct Fused {
             // stabiliser gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>, applied
             // as beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh> (gamma = 2, i.e.
             // beta gamma = 2 beta, when <dh|dh> vanishes)
-            const CT gb = hh > (CT)1e-30 * rho * rho ? (CT)1 - (CT)P.c_gb * (sh / hh) : (CT)2 * K.beta;
+            CT gb = hh > (CT)1e-30 * rho * rho ? (CT)1 - (CT)P.c_gb * (sh / hh) : (CT)2 * K.beta;
+            if constexpr (EXACT) {
+                // exact root of the entropy condition, from the closed form
+                if (hh > (CT)1e-30 * rho * rho) {
+                    auto parts = [&](int i, CT &fe, CT &dsv, CT &dh) {
+                        fe = rho * e[0][L::cx(i) + 1] * e[1][L::cy(i) + 1] * e[2][L::cz(i) + 1];
+                        dsv = ds_of(i, dev, dPi);
+                        dh = fq[i * NT] - fe - dsv;
+                    };
+                    CT t = (CT)1 - gb;
+                    const int rc = gamma_root<CT, Q>(parts, K.beta, t, (CT)1e-13, (CT)1e-15);
+                    if (rc > 0) gb = (CT)1 - t;
+                    else if (rc < 0) atomicAdd(P.gfall, 1ull);
+                }
+            }
             const CT bet = K.beta;
             if (!isfinite(gb)) bad |= ERR_NAN;
             ST *fd = reinterpret_cast<ST *>(A.fdst);
@@ -1096,6 +1182,35 @@ struct Fused {
         // <dh|dh> vanishes)
         double gbd = 2.0 * P.beta;
         if (hh > 1e-30f * rho * rho) gbd = fma(-P.c_gb, (double)(sh * rcp_nr(hh)), 1.0);
+        if constexpr (EXACT) {
+            // exact root of the entropy condition, from the closed form, in
+            // FP32 on the stashed Delta of each pair
+            if (hh > 1e-30f * rho * rho) {
+                auto ds_pair = [&](int k) -> float {
+                    if (L::nnz(k) == 1) return DS1[L::cx(k) ? 0 : (L::cy(k) ? 1 : 2)].x;
+                    if (L::nnz(k) == 2) {
+                        const int pl = L::cz(k) == 0 ? 0 : (L::cy(k) == 0 ? 1 : 2);
+                        const int sg = L::cz(k) == 0 ? L::cx(k) * L::cy(k)
+                                                     : (L::cy(k) == 0 ? L::cx(k) * L::cz(k) : L::cy(k) * L::cz(k));
+                        return sg > 0 ? DS2[pl].x : -DS2[pl].x;
+                    }
+                    return 0.f;
+                };
+                auto parts = [&](int i, float &fe, float &dsv, float &dh) {
+                    if (i == L::REST) { fe = fe0; dsv = 0.f; dh = dl0; return; }
+                    const int k = i < L::REST ? i : Q - 1 - i;
+                    const float2 fe2 = feq2(k, X, Y, Z);
+                    const float2 dl2 = stash2[k * NT];
+                    dsv = ds_pair(k);
+                    fe = i < L::REST ? fe2.x : fe2.y;
+                    dh = (i < L::REST ? dl2.x : dl2.y) - dsv;
+                };
+                float t = (float)(1.0 - gbd);
+                const int rc = gamma_root<float, Q>(parts, K.beta, t, 1e-5f, 1e-7f);
+                if (rc > 0) gbd = 1.0 - (double)t;
+                else if (rc < 0) atomicAdd(P.gfall, 1ull);
+            }
+        }
         const float gb = (float)gbd;
         if (!isfinite(gb)) bad |= ERR_NAN;
 

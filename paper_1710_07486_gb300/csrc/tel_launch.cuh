@@ -34,14 +34,19 @@ static cudaError_t launch_prec(int precision, int mode, const DevParams &P, cons
 {
     if (precision == 0) {
         if (mode == MODE_STEP) return launch_one<D, TX, TY, double, MODE_STEP, FAST>(P, A, s);
+        if (mode == MODE_STEP_EXACT) return launch_one<D, TX, TY, double, MODE_STEP_EXACT, FAST>(P, A, s);
         if (mode == MODE_INIT) return launch_one<D, TX, TY, double, MODE_INIT, FAST>(P, A, s);
         return launch_one<D, TX, TY, double, MODE_FIELDS, FAST>(P, A, s);
     }
-    if (mode == MODE_STEP) {
+    if (mode == MODE_STEP || mode == MODE_STEP_EXACT) {
+        const bool exact = mode == MODE_STEP_EXACT;
         // aligned four-node vectors in phase A (D3Q27 32 x 8, periodic, nx % 4 == 0)
         if constexpr (D == 3 && TX == 32 && TY == 8 && FAST)
-            if (P.nx % 4 == 0) return launch_one<D, TX, TY, float, MODE_STEP, FAST, true>(P, A, s);
-        return launch_one<D, TX, TY, float, MODE_STEP, FAST>(P, A, s);
+            if (P.nx % 4 == 0)
+                return exact ? launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST, true>(P, A, s)
+                             : launch_one<D, TX, TY, float, MODE_STEP, FAST, true>(P, A, s);
+        return exact ? launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST>(P, A, s)
+                     : launch_one<D, TX, TY, float, MODE_STEP, FAST>(P, A, s);
     }
     if (mode == MODE_INIT) return launch_one<D, TX, TY, float, MODE_INIT, FAST>(P, A, s);
     return launch_one<D, TX, TY, float, MODE_FIELDS, FAST>(P, A, s);

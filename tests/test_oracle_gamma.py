@@ -218,3 +218,16 @@ def test_exact_mode_collision_invariants(orc, T10, lattice):
         assert fo.sum() == pytest.approx(f.sum(), rel=1e-14)
         assert np.allclose(fo @ c, f @ c + F[:o.D], rtol=0, atol=1e-13 * f.sum())
     assert o.gamma_fallbacks() == 0
+
+
+@pytest.mark.parametrize("lattice", LATTICES)
+def test_exact_gamma_one_signed_delta_h_is_rounding(orc, T10, lattice):
+    """Delta h carries no mass, so a Delta h of one sign can only be rounding
+    noise: the solver returns -2 (closed form kept) and it is not counted as a
+    fallback."""
+    o = oracle(orc, lattice, T10)
+    feq = np.full(o.Q, 0.1)
+    ds = np.zeros(o.Q)
+    dh = np.full(o.Q, 1e-18)
+    it, g = o.gamma_exact(feq, ds, dh, 1.9)
+    assert it == -2 and g == 1.9

@@ -61,3 +61,35 @@ def test_laplace_law_oracle(orc):
         Re = np.sqrt((rr - d.rho_g).sum() / (d.rho_l - d.rho_g) / np.pi)
         ratio = (P[n // 2, n // 2] - P[0, 0]) * Re / sigma
         assert 0.8 < ratio < 1.2, (R, ratio)
+
+
+@pytest.mark.slow
+def test_oblique_flat_interface_matches_the_axis_aligned_one(orc):
+    """A flat liquid-gas interface along the diagonal (normal (1, 1)/sqrt 2)
+    relaxes to the same coexistence densities as one normal to x: the
+    lattice-consistent force couples both gradient components there, so a
+    wrong cross term would shift the diagonal case only.  96^2 box: the
+    diagonal coordinate x + y has period 96 along the diagonal, 67.9 nodes
+    along the normal, matched by a 68-node axis-aligned box."""
+    T = orc.temperature_for_ratio(A, B, RGAS, 10.0)
+    p = base(T, lambda2=0.0, lambda3=0.0, kappa1=0.05, kappa2=0.0, kappa3=0.0, force_form=1)
+    N = 96
+    L = N / np.sqrt(2.0)
+    o = orc.Oracle(orc.D2Q9, N, N, 1, p)
+    y, x = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    dn = ((x + y) % N).ravel() / np.sqrt(2.0)
+    prof = 0.5 * (np.tanh((dn - L / 4) / 3.0) - np.tanh((dn - 3 * L / 4) / 3.0))
+    f, g = o.init(o.rho_g + (o.rho_l - o.rho_g) * prof, np.zeros(N * N), np.zeros((2, N * N)))
+    assert o.step(f, g, 3000) == 0
+    r = o.fields(f, g)["rho"]
+    gas_d, liq_d = r[np.argmin(dn)], r[np.argmin(np.abs(dn - L / 2))]
+    a = orc.Oracle(orc.D2Q9, 68, 1, 1, p)
+    xa = np.arange(68) * (L / 68)
+    pa = 0.5 * (np.tanh((xa - L / 4) / 3.0) - np.tanh((xa - 3 * L / 4) / 3.0))
+    fa, ga = a.init(a.rho_g + (a.rho_l - a.rho_g) * pa, np.zeros(68), np.zeros((2, 68)))
+    assert a.step(fa, ga, 3000) == 0
+    ra = a.fields(fa, ga)["rho"]
+    for gas, liq in ((gas_d, liq_d), (ra[0], ra[34])):
+        assert abs(gas / o.rho_g - 1) < 0.02
+        assert abs(liq / o.rho_l - 1) < 0.005
+    assert abs(gas_d / ra[0] - 1) < 2e-3 and abs(liq_d / ra[34] - 1) < 2e-4
