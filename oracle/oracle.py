@@ -31,7 +31,8 @@ class Params(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "a", "b", "R", "T", "lambda1", "lambda2", "lambda3",
         "kappa1", "kappa2", "kappa3", "chi", "nu", "Gamma", "tau_g")] + [
-        ("force_form", C.c_int), ("eos", C.c_int), ("omega", C.c_double), ("gamma_mode", C.c_int)]
+        ("force_form", C.c_int), ("eos", C.c_int), ("omega", C.c_double), ("gamma_mode", C.c_int),
+        ("solid", C.c_void_p)]
 
 
 CS, VDW, PR = 0, 1, 2  # equations of state
@@ -229,11 +230,16 @@ class Oracle:
         self.lattice = lattice
         self.nx, self.ny, self.nz = nx, ny, nz
         self.params = dict(params)
-        ints = ("force_form", "eos", "omega", "gamma_mode")
+        ints = ("force_form", "eos", "omega", "gamma_mode", "solid")
         vals = {k: float(params[k]) for k, _ in Params._fields_ if k not in ints}
+        solid = params.get("solid")
+        self.solid = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).ravel()
+        if self.solid is not None:
+            assert self.solid.size == nx * ny * nz
         p = Params(force_form=int(params.get("force_form", 1)), eos=int(params.get("eos", CS)),
                    omega=float(params.get("omega", 0.0)),
-                   gamma_mode=int(params.get("gamma_mode", GAMMA_CLOSED)), **vals)
+                   gamma_mode=int(params.get("gamma_mode", GAMMA_CLOSED)),
+                   solid=None if self.solid is None else self.solid.ctypes.data, **vals)
         bca = np.asarray(bc, dtype=np.int32)
         self._h = lib().orc_create(lattice, nx, ny, nz, C.byref(p), bca)
         if not self._h:

@@ -31,6 +31,7 @@ struct orc_ctx {
     int opp[27];
     int rest;
     long *gamma_fallbacks;  /* counter of exact-stabiliser fallbacks */
+    unsigned char *solid;   /* copy of the solid mask, or NULL */
 };
 
 /* ------------------------------------------------------------------------- */
@@ -361,6 +362,12 @@ orc_ctx *orc_create(int lattice, int nx, int ny, int nz, const orc_params *p,
     for (int a = 0; a < 3; a++) o->bc[a] = bc ? bc[a] : 0;
     if (lattice == 0) o->bc[2] = 0;
     o->p = *p;
+    o->p.solid = NULL;
+    if (p->solid) {
+        o->solid = (unsigned char *)malloc((size_t)o->N);
+        if (!o->solid) { free(o->gamma_fallbacks); free(o); return NULL; }
+        for (long n = 0; n < o->N; n++) o->solid[n] = p->solid[n] != 0;
+    }
     if (lattice == 0) {
         for (int i = 0; i < 9; i++) {
             o->c[i][0] = C_D2Q9[i][0];
@@ -387,7 +394,7 @@ orc_ctx *orc_create(int lattice, int nx, int ny, int nz, const orc_params *p,
     }
     double co[4];
     orc_eos e = {p->eos, p->a, p->b, p->R, p->T, p->omega};
-    if (orc_eos_coexistence(&e, co)) { free(o->gamma_fallbacks); free(o); return NULL; }
+    if (orc_eos_coexistence(&e, co)) { free(o->solid); free(o->gamma_fallbacks); free(o); return NULL; }
     o->rho_g = co[0]; o->rho_l = co[1]; o->mu_coex = co[2]; o->p_coex = co[3];
     /* nu = c_s^2 (tau - 1/2) with c_s^2 = 1/3; KBC uses beta = 1/(2 tau) */
     o->tau = 3.0 * p->nu + 0.5;
@@ -397,9 +404,14 @@ orc_ctx *orc_create(int lattice, int nx, int ny, int nz, const orc_params *p,
 
 void orc_destroy(orc_ctx *o)
 {
-    if (o) free(o->gamma_fallbacks);
+    if (o) {
+        free(o->gamma_fallbacks);
+        free(o->solid);
+    }
     free(o);
 }
+
+static int is_solid(const orc_ctx *o, long n) { return o->solid && o->solid[n]; }
 long orc_gamma_fallbacks(const orc_ctx *o) { return *o->gamma_fallbacks; }
 int orc_Q(const orc_ctx *o) { return o->Q; }
 long orc_N(const orc_ctx *o) { return o->N; }
@@ -450,19 +462,64 @@ double orc_f_bulk(const orc_ctx *o, double rho, double phi)
            + 0.5 * o->p.lambda3 * c2 * c2 * (1.0 - c2) * (1.0 - c2);
 }
 
-/* Neighbour of node (x,y,z) along c for the stencils.  Periodic axes wrap.
-   Reading (wall ghosts; not in the paper): on a bounce-back axis the ghost
-   node beyond the half-way wall mirrors the first fluid node, so -1 -> 0 and
-   n -> n-1 (zero normal gradient, neutral wetting). */
-static long stencil_nb(const orc_ctx *o, int x, int y, int z, const int *c)
+/* Neighbour of node (x,y,z) along c under the axis rules only: periodic
+   axes wrap; on a bounce-back axis the ghost node beyond the half-way wall
+   mirrors the first fluid node, so -1 -> 0 and n -> n-1 (reading: zero
+   normal gradient, neutral wetting).  sgn[a] is -1 for each axis on which the
+   neighbour was mirrored (the component of a vector normal to the mirror
+   changes sign). */
+static long axis_nb(const orc_ctx *o, int x, int y, int z, const int *c, int sgn[3])
 {
     int q[3] = {x + c[0], y + c[1], z + c[2]};
     int n[3] = {o->nx, o->ny, o->nz};
     for (int a = 0; a < 3; a++) {
-        if (q[a] < 0) q[a] = o->bc[a] == 0 ? q[a] + n[a] : 0;
-        else if (q[a] >= n[a]) q[a] = o->bc[a] == 0 ? q[a] - n[a] : n[a] - 1;
+        sgn[a] = 1;
+        if (q[a] < 0) {
+            if (o->bc[a] == 0) q[a] += n[a]; else { q[a] = 0; sgn[a] = -1; }
+        } else if (q[a] >= n[a]) {
+            if (o->bc[a] == 0) q[a] -= n[a]; else { q[a] = n[a] - 1; sgn[a] = -1; }
+        }
     }
     return (long)q[0] + (long)o->nx * ((long)q[1] + (long)o->ny * q[2]);
+}
+
+/* Neighbour for the stencils, with solid nodes (reading, the same neutral
+   wetting as at the axis walls): when the neighbour along c is solid, the
+   stencil reads a ghost that mirrors a fluid node across the solid surface:
+   the components of c are set to zero, fewest first and in axis order
+   ({x}, {y}, {z}, {x,y}, {x,z}, {y,z}, {x,y,z}), until the node reached is
+   fluid; the vector components along the zeroed axes change sign.  Zeroing
+   every component reaches the node itself.  Where solid layers fill the ends
+   of an axis this is exactly the axis wall rule above. */
+static long stencil_nb_vec(const orc_ctx *o, int x, int y, int z, const int *c, int sgn[3])
+{
+    static const int subsets[7] = {1, 2, 4, 3, 5, 6, 7};
+    long m = axis_nb(o, x, y, z, c, sgn);
+    if (!is_solid(o, m)) return m;
+    for (int k = 0; k < 7; k++) {
+        int S = subsets[k], cc[3], sg[3], skip = 0;
+        for (int a = 0; a < 3; a++) {
+            if ((S >> a) & 1) {
+                if (c[a] == 0) skip = 1;
+                cc[a] = 0;
+            } else {
+                cc[a] = c[a];
+            }
+        }
+        if (skip) continue;
+        long q = axis_nb(o, x, y, z, cc, sg);
+        if (!is_solid(o, q)) {
+            for (int a = 0; a < 3; a++) sgn[a] = ((S >> a) & 1) ? -sg[a] : sg[a];
+            return q;
+        }
+    }
+    return m;  /* a solid node with no fluid neighbour: its values are unused */
+}
+
+static long stencil_nb(const orc_ctx *o, int x, int y, int z, const int *c)
+{
+    int sg[3];
+    return stencil_nb_vec(o, x, y, z, c, sg);
 }
 
 /* Reading (stencils; not in the paper): the lattice-weight isotropic
@@ -533,24 +590,6 @@ void orc_chem_pot(const orc_ctx *o, const double *rho, const double *phi,
     }
     free(lr);
     free(lp);
-}
-
-/* Neighbour for a vector-valued stencil input: like stencil_nb, and sgn[a]
-   is -1 for each axis on which the neighbour was mirrored at a wall (the
-   component of a gradient normal to the wall changes sign under the mirror). */
-static long stencil_nb_vec(const orc_ctx *o, int x, int y, int z, const int *c, int sgn[3])
-{
-    int q[3] = {x + c[0], y + c[1], z + c[2]};
-    int n[3] = {o->nx, o->ny, o->nz};
-    for (int a = 0; a < 3; a++) {
-        sgn[a] = 1;
-        if (q[a] < 0) {
-            if (o->bc[a] == 0) q[a] += n[a]; else { q[a] = 0; sgn[a] = -1; }
-        } else if (q[a] >= n[a]) {
-            if (o->bc[a] == 0) q[a] -= n[a]; else { q[a] = n[a] - 1; sgn[a] = -1; }
-        }
-    }
-    return (long)q[0] + (long)o->nx * ((long)q[1] + (long)o->ny * q[2]);
 }
 
 /* Force on the density populations.  The paper gives div P = rho grad mu_rho
@@ -845,7 +884,7 @@ void orc_collide_g(const orc_ctx *o, const double *g, double phi, double mu_phi,
 /* ------------------------------------------------------------------------- */
 
 /* Source of population i at node (x,y,z): returns the source node index, or
-   -1 when x - c_i lies beyond a bounce-back wall. */
+   -1 when x - c_i lies beyond a bounce-back wall or is a solid node. */
 static long pull_src(const orc_ctx *o, int x, int y, int z, int i)
 {
     int q[3] = {x - o->c[i][0], y - o->c[i][1], z - o->c[i][2]};
@@ -856,7 +895,8 @@ static long pull_src(const orc_ctx *o, int x, int y, int z, int i)
             q[a] = (q[a] + n[a]) % n[a];
         }
     }
-    return (long)q[0] + (long)o->nx * ((long)q[1] + (long)o->ny * q[2]);
+    long s = (long)q[0] + (long)o->nx * ((long)q[1] + (long)o->ny * q[2]);
+    return is_solid(o, s) ? -1 : s;  /* half-way bounce-back at a solid node */
 }
 
 void orc_stream(const orc_ctx *o, const double *post, double *pre)
@@ -868,7 +908,8 @@ void orc_stream(const orc_ctx *o, const double *post, double *pre)
                 long n = x + (long)o->nx * (y + (long)o->ny * z);
                 for (int i = 0; i < o->Q; i++) {
                     long s = pull_src(o, x, y, z, i);
-                    pre[i * N + n] = s >= 0 ? post[i * N + s] : post[o->opp[i] * N + n];
+                    if (is_solid(o, n)) pre[i * N + n] = 0.0;
+                    else pre[i * N + n] = s >= 0 ? post[i * N + s] : post[o->opp[i] * N + n];
                 }
             }
 }
@@ -880,6 +921,10 @@ void orc_unstream(const orc_ctx *o, const double *pre, double *post)
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
                 long n = x + (long)o->nx * (y + (long)o->ny * z);
+                if (is_solid(o, n)) {
+                    for (int i = 0; i < o->Q; i++) post[i * N + n] = 0.0;
+                    continue;
+                }
                 for (int i = 0; i < o->Q; i++) {
                     long s = pull_src(o, x, y, z, i);
                     if (s >= 0) post[i * N + s] = pre[i * N + n];
@@ -935,6 +980,13 @@ static void pre_collision(const orc_ctx *o, const double *f, const double *g, wo
         w->rho[n] = r;
         w->phi[n] = p;
         for (int a = 0; a < 3; a++) w->j[a * N + n] = jj[a];
+        if (is_solid(o, n)) {
+            /* placeholder moments of a solid node: no stencil of a fluid node
+               reads them (ghosts), they only keep the arithmetic finite */
+            w->rho[n] = o->rho_l;
+            w->phi[n] = 0.0;
+            for (int a = 0; a < 3; a++) w->j[a * N + n] = 0.0;
+        }
     }
     orc_chem_pot(o, w->rho, w->phi, w->mr, w->mp);
     orc_force(o, w->rho, w->phi, w->mr, w->mp, w->F);
@@ -951,6 +1003,10 @@ int orc_step(const orc_ctx *o, double *f, double *g, int nsteps)
         pre_collision(o, f, g, &w);
         for (long n = 0; n < N; n++) {
             double fl[27], gl[27], fo[27], go[27], F[3], u[3];
+            if (is_solid(o, n)) {  /* the state of a solid node is zero */
+                for (int i = 0; i < Q; i++) f[i * N + n] = g[i * N + n] = 0.0;
+                continue;
+            }
             for (int i = 0; i < Q; i++) {
                 fl[i] = w.fpre[i * N + n];
                 gl[i] = w.gpre[i * N + n];
@@ -990,6 +1046,7 @@ int orc_init(const orc_ctx *o, const double *rho, const double *phi,
         orc_force(o, rho, phi, mr, mp, F);
         for (long n = 0; n < N && rc == 0; n++) {
             double us[3] = {0, 0, 0}, uu[3] = {0, 0, 0}, fe[27], ge[27];
+            if (is_solid(o, n)) continue;  /* zeroed by orc_unstream */
             if (!(rho[n] > 0.0)) { rc = -3; break; }
             for (int a = 0; a < D; a++) {
                 uu[a] = u[a * N + n];
@@ -1053,8 +1110,15 @@ int orc_fields(const orc_ctx *o, const double *f, const double *g, double *rho,
         free(gp);
     }
     int rc = 0;
-    for (long n = 0; n < N; n++)
+    for (long n = 0; n < N; n++) {
+        if (is_solid(o, n)) {  /* the fields of a solid node are zero */
+            rho[n] = phi[n] = 0.0;
+            for (int a = 0; a < D; a++) u[a * N + n] = 0.0;
+            if (p) p[n] = 0.0;
+            continue;
+        }
         if (!(w.rho[n] > 0.0) || !isfinite(w.phi[n])) rc = -3;
+    }
     work_free(&w);
     return rc;
 }

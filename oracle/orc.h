@@ -14,6 +14,9 @@
  *   node index n = x + nx*(y + ny*z);  populations are SoA: f[i*N + n].
  *   bc[a] = 0 periodic along axis a, 1 = half-way bounce-back walls at both
  *   ends of axis a.
+ *   Solid nodes (params.solid): half-way bounce-back wherever a pull would
+ *   read a solid node; stencil reads of a solid neighbour take a fluid ghost
+ *   (see orc.c, ghost_nb); the state and fields of a solid node are zero.
  *   The stored state is the post-collision population set, i.e. what the
  *   next step streams (pulls) from.
  *
@@ -39,6 +42,8 @@ typedef struct {
     int eos;                           /* ORC_EOS_CS (Eq. 4), ORC_EOS_VDW, ORC_EOS_PR */
     double omega;                      /* Peng-Robinson acentric factor          */
     int gamma_mode;                    /* ORC_GAMMA_CLOSED or ORC_GAMMA_EXACT    */
+    const unsigned char *solid;        /* per-node solid mask [N] (nonzero =
+                                          solid), copied at create; NULL: none */
 } orc_params;
 
 /* Stabiliser of the KBC collision: the closed form (the root of the entropy
