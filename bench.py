@@ -192,7 +192,12 @@ def run_c4(args):
         "gpu_launches": args.steps,
         "clocks": summarize_clocks(clk, int(os.environ.get("LOCAL_RANK", "0"))),
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def next_summary(line):
+    """A C4 or C5 line, nested in the main line without the training log."""
+    return {k: v for k, v in line.items() if k not in ("loss", "n_gpus", "scaling", "vs_baseline")}
 
 
 def c5_setup(seed, n, H, rmin=100.0, rmax=1000.0):
@@ -304,6 +309,49 @@ def run_c5(args):
     e1.synchronize()
     ms_lbm = e0.elapsed_time(e1) / args.steps
     b.close()
+
+    # hybrid end to end: the surrogate with its fallback and judge (mass
+    # check on every advance, a lattice check every 4th advance, the lattice
+    # alone after a failed check) over every advance of the held-out
+    # trajectories, against the plain lattice update producing the same
+    # fields (k steps, then the fields of every case) from the same start
+    nadv = nsnap - 1
+    hy = S.Hybrid(net, [params[i] for i in test], H, H, k, tr.scale_host, mass_tol=1e-4, err_tol=1e-2,
+                  check_every=4)
+    cur = sn.store[0, test].contiguous().clone()
+    for _ in range(4):  # warm-up: first calls, and the batch's step graphs via a check
+        hy.advance(cur.clone())
+    hy.n, hy.lbm_only, hy.log = 0, False, []
+    outs = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(nadv):
+        hy.advance(cur)
+        outs.append(cur.clone())
+    torch.cuda.synchronize()
+    t_hybrid = time.perf_counter() - t0
+    e_hy = np.array([pr.errors(outs[s], sn.store[s + 1, test].contiguous()) for s in range(nadv)])
+    plain = tel.Batch([(H, H)] * Bt, [params[i] for i in test])
+    plain.set_stream(stream)
+    N2 = H * H
+    d_rho = torch.empty((Bt, N2), dtype=torch.float64, device="cuda")
+    d_phi = torch.empty((Bt, N2), dtype=torch.float64, device="cuda")
+    d_u = torch.empty((Bt, 2, N2), dtype=torch.float64, device="cuda")
+    for j, i in enumerate(test):
+        plain.init(j, *fields[i])
+    plain.step(3)
+    plain.step(3)
+    plain.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(nadv):
+        plain.step(k)
+        for j in range(Bt):
+            plain.fields_device(j, d_rho[j], d_phi[j], d_u[j])
+    plain.sync()
+    t_plain = time.perf_counter() - t0
+    plain.close()
+    paths = {p_: hy.log.count(p_) for p_ in sorted(set(hy.log))}
     mean_net = e_net.mean(axis=(0, 1))
     max_net = e_net.max(axis=(0, 1))
     mean_per = e_per.mean(axis=(0, 1))
@@ -337,8 +385,22 @@ def run_c5(args):
                    "train_ms_per_iter": round(1e3 * t_train / max(args.c5_iters, 1), 3)},
         "loss": [[i, round(l, 6)] for i, l in hist],
         "gpu_launches": pr.launches * args.steps,
+        "hybrid": {"speedup_vs_lattice": round(t_plain / t_hybrid, 3), "advances": nadv, "k": k,
+                   "trajectories": int(Bt), "wall_s": round(t_hybrid, 4), "lattice_wall_s": round(t_plain, 4),
+                   "paths": paths, "check_every": 4, "mass_tol": 1e-4, "err_tol": 1e-2,
+                   "error_mean": {"rho": round(float(e_hy[:, :, 0].mean()), 6),
+                                  "phi": round(float(e_hy[:, :, 1].mean()), 6),
+                                  "u": round(float(e_hy[:, :, 2].mean()), 6)},
+                   "error_max": {"rho": round(float(e_hy[:, :, 0].max()), 6),
+                                 "phi": round(float(e_hy[:, :, 1].max()), 6),
+                                 "u": round(float(e_hy[:, :, 2].max()), 6)},
+                   "within_1pct_rho_phi_mean": bool(e_hy[:, :, 0].mean() <= 0.01 and e_hy[:, :, 1].mean() <= 0.01),
+                   "what": "surrogate advances with mass checks, a lattice check every 4th advance and the "
+                           "lattice alone after a failed check, over every advance of the held-out trajectories; "
+                           "against the batched lattice producing the same fields every k steps; errors of the "
+                           "hybrid's fields against the lattice snapshots"},
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def sample_clocks(stop, out):
@@ -533,9 +595,10 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded drop collision; no dataset)",
             "config": {"workload": f"D3Q27 {n}^3 periodic, density ratio 1000, FP32-shifted populations "
-                                   "with FP64 stabiliser and gas-side chemical potential, off-centre "
-                                   "collision of immiscible drops R=30",
-                       "lattice": "D3Q27", "nodes": N, "precision": "fp32_shifted+fp64_gamma_eos",
+                                   "(closed-form stabiliser), off-centre collision of immiscible drops R=30",
+                       "lattice": "D3Q27", "nodes": N,
+                       "precision": "fp32_shifted storage; fp32 arithmetic with fp64 beta*gamma and fp64 sum of "
+                                    "the gas-side chemical potential's two pieces",
                        "force_form": "lattice", "B": round(w["B"], 4), "We": round(w["We"], 3),
                        "sigma12_over_sigma1g": w["sigma_ratio"], "seed": args.seed,
                        "l2": "state 7.2 GB per step (read 3.6 GB + write 3.6 GB) > L2; no flush needed",
@@ -551,26 +614,31 @@ def run_gpu(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        lat.close()
+        if world == 1 and not args.no_next:
+            line["batched"] = next_summary(run_c4(args))
+            line["surrogate"] = next_summary(run_c5(args))
         print(json.dumps(line), flush=True)
-    lat.close()
+    else:
+        lat.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline(args, steps=None, n=None):
-    """The FP64 CPU oracle as it stands, single-threaded, on a bounded sample:
-    the same collision scaled into a 64^3 periodic box (R = 7.5), 30 steps."""
+def oracle_run(n, steps, seed, openmp):
+    """Time `steps` steps of the FP64 oracle (as it stands: the plain build,
+    or its OpenMP timing copy on all host cores) on the C3 collision scaled
+    into an n^3 periodic box.  Returns (MLUPS, steps done, seconds)."""
     from oracle import oracle as orc
     from paper_1710_07486_gb300 import inputs
-    n = n or args.cpu_n
-    steps = steps or args.cpu_steps
-    w = workload_c3(args.seed, n=n)
+    w = workload_c3(seed, n=n)
     T = orc.temperature_for_ratio(A_, B_, R_, w["ratio"])
     rg, rl = orc.coexistence(A_, B_, R_, T)[:2]
     p, V, R = c3_params(w, T, rg, rl)
-    o = orc.Oracle(orc.D3Q27, n, n, n, p)
-    rho, phi, u = inputs.off_centre_3d(args.seed, n, rg, rl, p["chi"], V, w["B"], R=R * n / 256.0, width=10.0)
+    o = orc.Oracle(orc.D3Q27, n, n, n, p, openmp=openmp)
+    rho, phi, u = inputs.off_centre_3d(seed, n, rg, rl, p["chi"], V, w["B"], R=R * n / 256.0, width=10.0)
     f, g = o.init(rho, phi, u)
+    del rho, phi, u
     done, dt = 0, 0.0
     while done < steps:  # one step at a time: only completed, stable steps count
         t0 = time.perf_counter()
@@ -579,11 +647,38 @@ def cpu_baseline(args, steps=None, n=None):
         if rc != 0:
             break
         done += 1
-    note = "" if done == steps else f" (oracle flagged the state unstable after {done} steps)"
-    return {"value": round(n ** 3 * max(done, 1) / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"D3Q27 {n}^3 periodic box, same collision scaled (R={R * n / 256.0:g}, interface width 10), "
-                      f"{done} steps, FP64, single thread, {dt:.1f} s{note}",
-            "host": host_cpu()}
+    del o, f, g
+    return n ** 3 * max(done, 1) / dt / 1e6, done, dt
+
+
+def omp_threads():
+    """Threads of the OpenMP oracle: OMP_NUM_THREADS, else every host core."""
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
+    except ValueError:
+        return os.cpu_count()
+
+
+def cpu_baseline(args):
+    """The FP64 CPU oracle as it stands, on the host cores: the C3 collision
+    scaled into a 64^3 periodic box (R = 7.5) on every core (the oracle's
+    OpenMP timing copy) and on one core (the plain build), and one step of
+    the full 256^3 workload on every core."""
+    n = args.cpu_n
+    v_all, d_all, t_all = oracle_run(n, args.cpu_steps, args.seed, openmp=True)
+    v_one, d_one, t_one = oracle_run(n, max(args.cpu_steps // 3, 1), args.seed, openmp=False)
+    out = {"value": round(v_all, 4), "unit": "MLUPS", "cores": omp_threads(), "kind": "oracle",
+           "sample": f"D3Q27 {n}^3 periodic box, the same collision scaled (R={30.0 * n / 256.0:g}, interface "
+                     f"width 10), {d_all} steps, FP64, OpenMP over {omp_threads()} threads, {t_all:.1f} s",
+           "single_thread": {"value": round(v_one, 4), "unit": "MLUPS", "cores": 1,
+                             "sample": f"same box, {d_one} steps, plain build, {t_one:.1f} s"},
+           "host": host_cpu()}
+    if args.cpu_full_steps > 0:
+        v_f, d_f, t_f = oracle_run(args.n, args.cpu_full_steps, args.seed, openmp=True)
+        out["full_size"] = {"value": round(v_f, 4), "unit": "MLUPS", "cores": omp_threads(),
+                            "sample": f"D3Q27 {args.n}^3, the bench's own collision, {d_f} step(s), FP64, "
+                                      f"OpenMP, {t_f:.1f} s"}
+    return out
 
 
 def host_cpu():
@@ -607,25 +702,28 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    vals = []
+    n = args.cpu_n
     for _ in range(args.warmup):
-        cpu_baseline(args, steps=1, n=args.ref_n)
+        oracle_run(n, 1, args.seed, openmp=True)
+    vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args, steps=1, n=args.ref_n)["value"])
+        vals.append(oracle_run(n, 1, args.seed, openmp=True)[0])
     wall = time.perf_counter() - t0
     v = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world,
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded drop collision; no dataset)",
             "config": {"workload": "D3Q27 ternary ELBM, density ratio 1000, off-centre drop collision "
-                                   f"(bounded sample: {args.ref_n}^3 box, 1 step per timed step)",
-                       "parallelism": "cpu, 1 thread"},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"D3Q27 {args.ref_n}^3 periodic box, one step per timed step",
+                                   f"(bounded sample: the collision scaled into a {n}^3 box, one oracle step per "
+                                   "timed step)",
+                       "parallelism": f"cpu, OpenMP over {omp_threads()} threads"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": omp_threads(), "kind": "oracle",
+                             "sample": f"D3Q27 {n}^3 periodic box (the cpu_baseline sample of the main line), "
+                                       "one step per timed step, OpenMP timing copy of the oracle",
                              "host": host_cpu()},
-            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -639,8 +737,11 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--cpu-n", type=int, default=64)
     ap.add_argument("--cpu-steps", type=int, default=30)
-    ap.add_argument("--ref-n", type=int, default=48)
+    ap.add_argument("--cpu-full-steps", type=int, default=1,
+                    help="oracle steps timed at the full size (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the batched (C4) and surrogate (C5) measurements nested in the main line")
     ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5"],
                     help="c3: D3Q27 256^3 collision (default); c4: batched uneven D2Q9 cases; "
                          "c5: learned surrogate (train + evaluate)")
@@ -661,9 +762,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "c4":
-        run_c4(args)
+        print(json.dumps(run_c4(args)), flush=True)
     elif args.workload == "c5":
-        run_c5(args)
+        print(json.dumps(run_c5(args)), flush=True)
     else:
         run_gpu(args)
 

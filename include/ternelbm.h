@@ -90,7 +90,21 @@ typedef struct {
     int eos;                          /* tel_eos: TEL_EOS_CS (Eq. 4, default 0), TEL_EOS_VDW, TEL_EOS_PR */
     double omega;                     /* Peng-Robinson acentric factor (TEL_EOS_PR only) */
     int gamma_mode;                   /* tel_gamma_mode: TEL_GAMMA_CLOSED (default 0) or TEL_GAMMA_EXACT */
+    const unsigned char *solid;       /* optional host solid mask [nz][ny][nx] (nonzero = solid),
+                                         copied by tel_create; NULL = no solid nodes (see below) */
 } tel_params;
+
+/* Solid nodes (tel_params.solid; not in the paper, which names wetting
+ * boundaries only as an outlook): half-way bounce-back wherever a pull would
+ * read a solid node, f_i(x) = f*_{Q-1-i}(x); a stencil that would read a
+ * solid neighbour along c reads a fluid ghost instead -- the components of c
+ * set to zero, fewest first and in axis order x, y, z, until the node reached
+ * is fluid; the vector components along zeroed axes change sign -- the same
+ * neutral-wetting rule as the walls at the ends of a bounce-back axis, which
+ * solid layers there reproduce exactly.  The state (populations) and the
+ * fields of a solid node are zero; tel_init ignores its input fields there.
+ * A lattice with solid nodes takes the kernel's walled path (64-bit indices,
+ * per-pull tests).  Not available for batches or tel_fields_noalloc. */
 
 /* Stabiliser gamma of the KBC collision f' = f - beta (2 Delta s + gamma
  * Delta h) (the entropic scheme named after Eq. 8):
@@ -106,9 +120,12 @@ typedef struct {
  *     incremented (tel_gamma_fallbacks).  Where Delta h has entries of one
  *     sign only -- a massless Delta h does so only as rounding noise -- the
  *     closed form is kept without counting.
+ *   TEL_GAMMA_CLOSED_F64SUM: the closed form with its two scalar products
+ *     accumulated in FP64 (a precision variant of TEL_FP32_SHIFTED; with
+ *     TEL_FP64 storage it is TEL_GAMMA_CLOSED).
  * gamma = 2 (BGK) wherever <Delta h|Delta h> <= 1e-30 rho^2.  Batches
  * (tel_batch_*) use the closed form. */
-typedef enum { TEL_GAMMA_CLOSED = 0, TEL_GAMMA_EXACT = 1 } tel_gamma_mode;
+typedef enum { TEL_GAMMA_CLOSED = 0, TEL_GAMMA_EXACT = 1, TEL_GAMMA_CLOSED_F64SUM = 2 } tel_gamma_mode;
 
 /* Equations of state.  TEL_EOS_CS is Eq. 4 (Carnahan-Starling).  The text
  * names van der Waals and Peng-Robinson as alternatives (their formulas are
@@ -225,6 +242,10 @@ const char *tel_batch_last_error(const tel_batch *b);
  * (step pairs are captured into a graph on it). */
 int tel_batch_set_stream(tel_batch *b, void *cuda_stream);
 int tel_batch_init(tel_batch *b, int c, const double *rho, const double *phi, const double *u);
+/* As tel_batch_init from device FP64 arrays (rho[N], phi[N], u[2N]) on the
+ * batch's stream; asynchronous (no host copy, no synchronisation; a flagged
+ * node shows in tel_batch_sync / tel_batch_errors). */
+int tel_batch_init_device(tel_batch *b, int c, const double *rho, const double *phi, const double *u);
 int tel_batch_step(tel_batch *b, int nsteps);
 int tel_batch_sync(tel_batch *b);
 int tel_batch_fields(tel_batch *b, int c, double *rho, double *phi, double *u, double *p);

@@ -20,6 +20,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liborc.so")
+OMP_LIB_PATH = os.path.join(BUILD_DIR, "liborc_omp.so")
 
 D2Q9, D3Q27 = 0, 1
 PERIODIC, BOUNCEBACK = 0, 1
@@ -45,28 +46,34 @@ class Eos(C.Structure):
     _fields_ = [("kind", C.c_int)] + [(n, C.c_double) for n in ("a", "b", "R", "T", "omega")]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (plain C, -O2, no fast-math) and return its path."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle (plain C, -O2, no fast-math) and return its path.
+    ``openmp``: the timing copy of the same source with its loops over nodes
+    spread over the host cores (``liborc_omp.so``); the tests use the plain,
+    single-threaded build."""
     src = os.path.join(HERE, "orc.c")
-    if not force and os.path.exists(LIB_PATH) and \
-            os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(src),
-                                              os.path.getmtime(os.path.join(HERE, "orc.h"))):
-        return LIB_PATH
+    path = OMP_LIB_PATH if openmp else LIB_PATH
+    if not force and os.path.exists(path) and \
+            os.path.getmtime(path) >= max(os.path.getmtime(src),
+                                          os.path.getmtime(os.path.join(HERE, "orc.h"))):
+        return path
     os.makedirs(BUILD_DIR, exist_ok=True)
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = path + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared",
-                           "-fno-fast-math", "-ffp-contract=off", src, "-o", tmp, "-lm"])
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+                           "-fno-fast-math", "-ffp-contract=off"] + (["-fopenmp"] if openmp else [])
+                          + [src, "-o", tmp, "-lm"])
+    os.replace(tmp, path)
+    return path
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(openmp: bool = False):
+    """The oracle library: the plain single-threaded build, or (``openmp``)
+    the timing copy that spreads the loops over nodes across the host cores."""
+    if openmp not in _libs:
+        L = C.CDLL(build(openmp=openmp))
         dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
         ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
         d = C.c_double
@@ -134,8 +141,8 @@ def lib():
         L.orc_step.restype = C.c_int
         L.orc_fields.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, C.c_void_p]
         L.orc_fields.restype = C.c_int
-        _lib = L
-    return _lib
+        _libs[openmp] = L
+    return _libs[openmp]
 
 
 def _f64(x, n=None):
@@ -226,7 +233,8 @@ class Oracle:
     """One lattice (D2Q9 or D3Q27) with its parameters; state arrays are numpy
     float64 ``[Q, N]`` (post-collision populations)."""
 
-    def __init__(self, lattice, nx, ny, nz, params: dict, bc=(0, 0, 0)):
+    def __init__(self, lattice, nx, ny, nz, params: dict, bc=(0, 0, 0), openmp=False):
+        self._L = lib(openmp)
         self.lattice = lattice
         self.nx, self.ny, self.nz = nx, ny, nz
         self.params = dict(params)
@@ -241,35 +249,35 @@ class Oracle:
                    gamma_mode=int(params.get("gamma_mode", GAMMA_CLOSED)),
                    solid=None if self.solid is None else self.solid.ctypes.data, **vals)
         bca = np.asarray(bc, dtype=np.int32)
-        self._h = lib().orc_create(lattice, nx, ny, nz, C.byref(p), bca)
+        self._h = self._L.orc_create(lattice, nx, ny, nz, C.byref(p), bca)
         if not self._h:
             raise ValueError("orc_create failed (bad lattice/size or no coexistence)")
-        self.Q = lib().orc_Q(self._h)
-        self.N = lib().orc_N(self._h)
+        self.Q = self._L.orc_Q(self._h)
+        self.N = self._L.orc_N(self._h)
         self.D = 2 if lattice == D2Q9 else 3
         c = np.zeros(27 * 3, dtype=np.int32)
         w = np.zeros(27)
-        lib().orc_velocities(self._h, c, w)
+        self._L.orc_velocities(self._h, c, w)
         self.c = c.reshape(27, 3)[: self.Q].copy()
         self.w = w[: self.Q].copy()
         der = np.zeros(6)
-        lib().orc_derived(self._h, der)
+        self._L.orc_derived(self._h, der)
         (self.rho_g, self.rho_l, self.mu_coex, self.p_coex,
          self.tau, self.beta) = (float(v) for v in der)
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     # single node
     def f_bulk(self, rho, phi):
-        return lib().orc_f_bulk(self._h, rho, phi)
+        return self._L.orc_f_bulk(self._h, rho, phi)
 
     def feq(self, rho, u):
         out = np.zeros(self.Q)
-        lib().orc_feq(self._h, rho, _f64(np.resize(np.asarray(u, float), 3)), out)
+        self._L.orc_feq(self._h, rho, _f64(np.resize(np.asarray(u, float), 3)), out)
         return out
 
     def collide_f(self, f, F):
@@ -277,7 +285,7 @@ class Oracle:
         fo = np.zeros(self.Q)
         ds = np.zeros(self.Q)
         g = C.c_double()
-        rc = lib().orc_collide_f(self._h, _f64(f, self.Q),
+        rc = self._L.orc_collide_f(self._h, _f64(f, self.Q),
                                  _f64(np.resize(np.asarray(F, float), 3)), fo,
                                  ds.ctypes.data_as(C.c_void_p), C.byref(g))
         if rc != 0:
@@ -287,61 +295,61 @@ class Oracle:
     def gamma_exact(self, feq, ds, dh, gamma0):
         """(iterations or -1 on fallback, gamma) of the exact stabiliser."""
         g = C.c_double()
-        it = lib().orc_gamma_exact(self._h, _f64(feq, self.Q), _f64(ds, self.Q), _f64(dh, self.Q),
+        it = self._L.orc_gamma_exact(self._h, _f64(feq, self.Q), _f64(ds, self.Q), _f64(dh, self.Q),
                                    float(gamma0), C.byref(g))
         return it, g.value
 
     def gamma_fallbacks(self):
-        return int(lib().orc_gamma_fallbacks(self._h))
+        return int(self._L.orc_gamma_fallbacks(self._h))
 
     def geq(self, phi, mu_phi, u):
         out = np.zeros(self.Q)
-        lib().orc_geq(self._h, phi, mu_phi, _f64(np.resize(np.asarray(u, float), 3)), out)
+        self._L.orc_geq(self._h, phi, mu_phi, _f64(np.resize(np.asarray(u, float), 3)), out)
         return out
 
     def collide_g(self, g, phi, mu_phi, u):
         out = np.zeros(self.Q)
-        lib().orc_collide_g(self._h, _f64(g, self.Q), phi, mu_phi,
+        self._L.orc_collide_g(self._h, _f64(g, self.Q), phi, mu_phi,
                             _f64(np.resize(np.asarray(u, float), 3)), out)
         return out
 
     # lattice
     def stream(self, post):
         pre = np.zeros((self.Q, self.N))
-        lib().orc_stream(self._h, _f64(post, self.Q * self.N), pre)
+        self._L.orc_stream(self._h, _f64(post, self.Q * self.N), pre)
         return pre
 
     def unstream(self, pre):
         post = np.zeros((self.Q, self.N))
-        lib().orc_unstream(self._h, _f64(pre, self.Q * self.N), post)
+        self._L.orc_unstream(self._h, _f64(pre, self.Q * self.N), post)
         return post
 
     def laplacian(self, psi):
         out = np.zeros(self.N)
-        lib().orc_laplacian(self._h, _f64(psi, self.N), out)
+        self._L.orc_laplacian(self._h, _f64(psi, self.N), out)
         return out
 
     def gradient(self, psi):
         out = np.zeros((3, self.N))
-        lib().orc_gradient(self._h, _f64(psi, self.N), out)
+        self._L.orc_gradient(self._h, _f64(psi, self.N), out)
         return out
 
     def chem_pot(self, rho, phi):
         mr = np.zeros(self.N)
         mp = np.zeros(self.N)
-        lib().orc_chem_pot(self._h, _f64(rho, self.N), _f64(phi, self.N), mr, mp)
+        self._L.orc_chem_pot(self._h, _f64(rho, self.N), _f64(phi, self.N), mr, mp)
         return mr, mp
 
     def force(self, rho, phi, mu_rho, mu_phi):
         F = np.zeros((3, self.N))
-        lib().orc_force(self._h, _f64(rho, self.N), _f64(phi, self.N),
+        self._L.orc_force(self._h, _f64(rho, self.N), _f64(phi, self.N),
                         _f64(mu_rho, self.N), _f64(mu_phi, self.N), F)
         return F
 
     def init(self, rho, phi, u):
         f = np.zeros((self.Q, self.N))
         g = np.zeros((self.Q, self.N))
-        rc = lib().orc_init(self._h, _f64(rho, self.N), _f64(phi, self.N),
+        rc = self._L.orc_init(self._h, _f64(rho, self.N), _f64(phi, self.N),
                             _f64(u, self.D * self.N), f, g)
         if rc != 0:
             raise FloatingPointError(f"orc_init rc={rc}")
@@ -351,14 +359,14 @@ class Oracle:
         """Advance (f, g) in place; returns the status code (0 ok, -3 unstable)."""
         assert f.dtype == np.float64 and f.flags.c_contiguous
         assert g.dtype == np.float64 and g.flags.c_contiguous
-        return lib().orc_step(self._h, f, g, int(nsteps))
+        return self._L.orc_step(self._h, f, g, int(nsteps))
 
     def fields(self, f, g, with_p=True):
         rho = np.zeros(self.N)
         phi = np.zeros(self.N)
         u = np.zeros((self.D, self.N))
         p = np.zeros(self.N) if with_p else None
-        rc = lib().orc_fields(self._h, _f64(f, self.Q * self.N), _f64(g, self.Q * self.N),
+        rc = self._L.orc_fields(self._h, _f64(f, self.Q * self.N), _f64(g, self.Q * self.N),
                               rho, phi, u,
                               p.ctypes.data_as(C.c_void_p) if with_p else None)
         return {"rho": rho, "phi": phi, "u": u, "p": p, "rc": rc}

@@ -5,7 +5,10 @@
  * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
  * benchmark's CPU-baseline leg, never by the product path.  It shares no code
  * with the CUDA library.  Every step is written out in the order of the
- * algorithm, single-threaded, without blocking or fusion.
+ * algorithm, without blocking or fusion.  The plain build is single-threaded;
+ * the OpenMP pragmas on the loops over nodes (independent per node, no
+ * reductions) only take effect in the separately built timing copy
+ * (-fopenmp) that the CPU baseline uses on all host cores.
  *
  * The paper states the continuum model (Eqs. 1-8) and names the discrete
  * schemes (entropic LBM with exact-difference forcing for the density
@@ -526,6 +529,7 @@ static long stencil_nb(const orc_ctx *o, int x, int y, int z, const int *c)
    Laplacian  lap psi = (2/c_s^2) sum_i w_i (psi(x+c_i) - psi(x)). */
 void orc_laplacian(const orc_ctx *o, const double *psi, double *lap)
 {
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < o->nz; z++)
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
@@ -542,6 +546,7 @@ void orc_laplacian(const orc_ctx *o, const double *psi, double *lap)
 void orc_gradient(const orc_ctx *o, const double *psi, double *grad)
 {
     long N = o->N;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < o->nz; z++)
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
@@ -575,6 +580,7 @@ void orc_chem_pot(const orc_ctx *o, const double *rho, const double *phi,
     orc_laplacian(o, phi, lp);
     double Dl = o->rho_g - o->rho_l, chi = p->chi;
     orc_eos e = {p->eos, p->a, p->b, p->R, p->T, p->omega};
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; n++) {
         double c1 = conc_l1(o, rho[n], phi[n]), c2 = conc_l2(o, rho[n], phi[n]);
         double w1 = c1 * (1.0 - c1) * (1.0 - 2.0 * c1);
@@ -620,11 +626,13 @@ void orc_force(const orc_ctx *o, const double *rho, const double *phi,
     orc_gradient(o, mu_phi, gp);
     orc_gradient(o, rho, gr);
     for (int a = 0; a < 3; a++)
+#pragma omp parallel for schedule(static)
         for (long n = 0; n < N; n++)
             F[a * N + n] = -rho[n] * gm[a * N + n] - phi[n] * gp[a * N + n];
     if (o->p.force_form == 0) {
         for (long n = 0; n < 3 * N; n++) F[n] += cs2 * gr[n];
     } else {
+#pragma omp parallel for collapse(2) schedule(static)
         for (int z = 0; z < o->nz; z++)
             for (int y = 0; y < o->ny; y++)
                 for (int x = 0; x < o->nx; x++) {
@@ -747,9 +755,10 @@ int orc_gamma_exact(const orc_ctx *o, const double *feq, const double *ds, const
         double G = 0.0, dG = 0.0, S = 0.0;
         for (int i = 0; i < Q; i++) {
             double x = ((1.0 - 2.0 * beta) * ds[i] + t * dh[i]) / feq[i];
-            double term = dh[i] * log1p(x);
-            G += term;
-            S += fabs(term);
+            G += dh[i] * log1p(x);
+            /* size of the term before the two parts of x cancel: the scale
+               of G's rounding */
+            S += fabs(dh[i]) * (fabs((1.0 - 2.0 * beta) * ds[i]) + fabs(t * dh[i])) / feq[i];
             dG += dh[i] * dh[i] / (feq[i] * (1.0 + x));
         }
         /* converged: G vanishes to the rounding of its terms */
@@ -762,11 +771,21 @@ int orc_gamma_exact(const orc_ctx *o, const double *feq, const double *ds, const
             *gamma = (1.0 - 0.5 * (a + b)) / beta;
             return it;
         }
-        /* Newton step, or bisection when it leaves the bracket or stalls
-           (next to a pole of ln f'_i the derivative is huge and the step
-           tiny) */
+        /* Newton step, or bisection when it leaves the bracket.  A step
+           below rounding ends the iteration when G is at its rounding floor
+           (within 1e3 of the bar), and bisects when it is not: next to a
+           pole of ln f'_i the derivative is huge and the step tiny while G
+           is large */
         double tn = t - G / dG;
-        if (!(tn > a && tn < b) || fabs(tn - t) <= 1e-15 * (1.0 + fabs(t))) tn = 0.5 * (a + b);
+        if (!(tn > a && tn < b)) {
+            tn = 0.5 * (a + b);
+        } else if (fabs(tn - t) <= 1e-15 * (1.0 + fabs(t))) {
+            if (fabs(G) <= 1e-10 * S) {
+                *gamma = (1.0 - tn) / beta;
+                return it;
+            }
+            tn = 0.5 * (a + b);
+        }
         t = tn;
     }
     return -1;
@@ -835,7 +854,10 @@ int orc_collide_f(const orc_ctx *o, const double *f, const double F[3],
             double ge;
             int it = orc_gamma_exact(o, feq, ds, dh, g, &ge);
             if (it >= 0) g = ge;
-            else if (it == -1) (*o->gamma_fallbacks)++;
+            else if (it == -1) {
+#pragma omp atomic
+                (*o->gamma_fallbacks)++;
+            }
         }
     }
     for (int i = 0; i < Q; i++) {
@@ -902,6 +924,7 @@ static long pull_src(const orc_ctx *o, int x, int y, int z, int i)
 void orc_stream(const orc_ctx *o, const double *post, double *pre)
 {
     long N = o->N;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < o->nz; z++)
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
@@ -917,6 +940,7 @@ void orc_stream(const orc_ctx *o, const double *post, double *pre)
 void orc_unstream(const orc_ctx *o, const double *pre, double *post)
 {
     long N = o->N;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < o->nz; z++)
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
@@ -970,6 +994,7 @@ static void pre_collision(const orc_ctx *o, const double *f, const double *g, wo
     long N = o->N;
     orc_stream(o, f, w->fpre);
     orc_stream(o, g, w->gpre);
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; n++) {
         double r = 0.0, p = 0.0, jj[3] = {0, 0, 0};
         for (int i = 0; i < o->Q; i++) {
@@ -1001,6 +1026,7 @@ int orc_step(const orc_ctx *o, double *f, double *g, int nsteps)
     if (work_alloc(o, &w)) { work_free(&w); return -2; }
     for (int s = 0; s < nsteps && rc == 0; s++) {
         pre_collision(o, f, g, &w);
+#pragma omp parallel for schedule(static)
         for (long n = 0; n < N; n++) {
             double fl[27], gl[27], fo[27], go[27], F[3], u[3];
             if (is_solid(o, n)) {  /* the state of a solid node is zero */
@@ -1013,7 +1039,10 @@ int orc_step(const orc_ctx *o, double *f, double *g, int nsteps)
             }
             for (int a = 0; a < 3; a++) F[a] = w.F[a * N + n];
             int e = orc_collide_f(o, fl, F, fo, NULL, NULL);
-            if (e) rc = e;
+            if (e) {
+#pragma omp atomic write
+                rc = e;
+            }
             /* the phase field is advected with u = (j + F/2)/rho (reading) */
             for (int a = 0; a < 3; a++) u[a] = (w.j[a * N + n] + 0.5 * F[a]) / w.rho[n];
             orc_collide_g(o, gl, w.phi[n], w.mp[n], u, go);

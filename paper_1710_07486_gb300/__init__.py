@@ -17,13 +17,13 @@ import numpy as np
 
 __all__ = ["Lattice", "lib", "coexistence", "temperature_for_ratio", "TelError",
            "D2Q9", "D3Q27", "FP64", "FP32_SHIFTED", "PERIODIC", "BOUNCEBACK",
-           "FORCE_POTENTIAL", "FORCE_LATTICE", "GAMMA_CLOSED", "GAMMA_EXACT"]
+           "FORCE_POTENTIAL", "FORCE_LATTICE", "GAMMA_CLOSED", "GAMMA_EXACT", "GAMMA_CLOSED_F64SUM"]
 
 D2Q9, D3Q27 = 0, 1
 FP64, FP32_SHIFTED = 0, 1
 PERIODIC, BOUNCEBACK = 0, 1
 FORCE_POTENTIAL, FORCE_LATTICE = 0, 1
-GAMMA_CLOSED, GAMMA_EXACT = 0, 1
+GAMMA_CLOSED, GAMMA_EXACT, GAMMA_CLOSED_F64SUM = 0, 1, 2
 EOS_CS, EOS_VDW, EOS_PR = 0, 1, 2
 
 TEL_OK, TEL_EINVAL, TEL_ENOMEM, TEL_ECUDA, TEL_EUNSTABLE, TEL_ESTATE = 0, -1, -2, -3, -4, -5
@@ -45,7 +45,7 @@ class Params(C.Structure):
         "a", "b", "R", "T", "lambda1", "lambda2", "lambda3", "kappa1", "kappa2",
         "kappa3", "chi", "nu", "Gamma", "tau_g", "rho_ref")] + [
         ("precision", C.c_int), ("force_form", C.c_int), ("bc", C.c_int * 3), ("eos", C.c_int),
-        ("omega", C.c_double), ("gamma_mode", C.c_int)]
+        ("omega", C.c_double), ("gamma_mode", C.c_int), ("solid", C.c_void_p)]
 
 
 _lib = None
@@ -54,7 +54,7 @@ SYMBOLS = ("tel_create", "tel_destroy", "tel_last_error", "tel_set_stream", "tel
            "tel_get_state", "tel_set_state", "tel_info", "tel_coexistence",
            "tel_temperature_for_ratio", "tel_coexistence_eos", "tel_temperature_for_ratio_eos",
            "tel_fields_noalloc", "tel_batch_create",
-           "tel_batch_destroy", "tel_batch_last_error", "tel_batch_set_stream", "tel_batch_init", "tel_batch_step",
+           "tel_batch_destroy", "tel_batch_last_error", "tel_batch_set_stream", "tel_batch_init", "tel_batch_init_device", "tel_batch_step",
            "tel_batch_sync", "tel_batch_fields", "tel_batch_fields_device", "tel_batch_errors",
            "tel_batch_tune", "tel_batch_info")
 
@@ -100,6 +100,7 @@ def lib(build: bool = True):
     L.tel_batch_last_error.restype = C.c_char_p
     L.tel_batch_set_stream.argtypes = [vp, vp]
     L.tel_batch_init.argtypes = [vp, i, vp, vp, vp]
+    L.tel_batch_init_device.argtypes = [vp, i, vp, vp, vp]
     L.tel_batch_step.argtypes = [vp, i]
     L.tel_batch_sync.argtypes = [vp]
     L.tel_batch_fields.argtypes = [vp, i, vp, vp, vp, vp]
@@ -153,6 +154,11 @@ def _params_struct(p):
     s.eos = int(p.get("eos", EOS_CS))
     s.omega = float(p.get("omega", 0.0))
     s.gamma_mode = int(p.get("gamma_mode", GAMMA_CLOSED))
+    solid = p.get("solid")
+    if solid is not None:
+        # kept alive on the struct until the call that copies it returns
+        s._solid = np.ascontiguousarray(solid, dtype=np.uint8).ravel()
+        s.solid = s._solid.ctypes.data
     return s
 
 
@@ -236,6 +242,17 @@ class Batch:
             raise ValueError(f"case {c}: expected fields of {N}, {N} and {2 * N} values")
         self._check(self._L.tel_batch_init(self._h, int(c), _ptr(a[0]), _ptr(a[1]), _ptr(a[2])))
 
+    def init_device(self, c, rho, phi, u):
+        """Case c from device float64 tensors of N, N and 2N elements
+        (asynchronous on the batch's stream)."""
+        nx, ny = self.shapes[c]
+        N = nx * ny
+        for t, n in ((rho, N), (phi, N), (u, 2 * N)):
+            if t.numel() != n or not t.is_contiguous() or str(t.dtype) != "torch.float64" or not t.is_cuda:
+                raise ValueError("init_device wants contiguous CUDA float64 tensors")
+        self._check(self._L.tel_batch_init_device(self._h, int(c), C.c_void_p(rho.data_ptr()),
+                                                  C.c_void_p(phi.data_ptr()), C.c_void_p(u.data_ptr())))
+
     def step(self, n=1):
         self._check(self._L.tel_batch_step(self._h, int(n)))
 
@@ -292,6 +309,8 @@ class Lattice:
             p["precision"] = precision
         if force_form is not None:
             p["force_form"] = force_form
+        if p.get("solid") is not None and np.asarray(p["solid"]).size != nx * ny * nz:
+            raise ValueError(f"solid mask: expected {nx * ny * nz} values")
         s = _params_struct(p)
         self._L = lib()
         h = C.c_void_p()

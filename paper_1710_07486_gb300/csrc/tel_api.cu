@@ -24,6 +24,7 @@ struct tel_ctx {
     unsigned *d_err;
     unsigned *h_err;  // pinned
     unsigned long long *d_gfall;  // exact-stabiliser fallbacks
+    unsigned char *d_solid;       // device copy of the solid mask, or NULL
     double *scratch;  // FP64 fields / state staging, lazily allocated
     size_t scratch_elems;
     cudaStream_t own_stream, stream;
@@ -275,7 +276,8 @@ static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
     if (p->precision != TEL_FP64 && p->precision != TEL_FP32_SHIFTED) return fail(nullptr, TEL_EINVAL, "bad precision");
     if (p->eos != TEL_EOS_CS && p->eos != TEL_EOS_VDW && p->eos != TEL_EOS_PR) return fail(nullptr, TEL_EINVAL, "bad eos");
     if (p->force_form != TEL_FORCE_POTENTIAL && p->force_form != TEL_FORCE_LATTICE) return fail(nullptr, TEL_EINVAL, "bad force_form");
-    if (p->gamma_mode != TEL_GAMMA_CLOSED && p->gamma_mode != TEL_GAMMA_EXACT) return fail(nullptr, TEL_EINVAL, "bad gamma_mode");
+    if (p->gamma_mode != TEL_GAMMA_CLOSED && p->gamma_mode != TEL_GAMMA_EXACT && p->gamma_mode != TEL_GAMMA_CLOSED_F64SUM)
+        return fail(nullptr, TEL_EINVAL, "bad gamma_mode");
     for (int a = 0; a < 3; ++a)
         if (p->bc[a] != TEL_PERIODIC && p->bc[a] != TEL_BOUNCEBACK) return fail(nullptr, TEL_EINVAL, "bad bc[%d]", a);
     if (((long long)nx * ny * nz) >= (1LL << 31)) return fail(nullptr, TEL_EINVAL, "lattice too large (N must be < 2^31)");
@@ -348,6 +350,7 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
     d.inv_tau_g = 1.0 / p.tau_g;
     d.rho_ref = p.precision == TEL_FP32_SHIFTED ? (p.rho_ref > 0 ? p.rho_ref : co[0]) : 0.0;
     d.gamma_mode = p.gamma_mode;
+    d.solid = nullptr;  // the device copy is set by tel_create
     fill_coef(d, d.cf);
     fill_coef(d, d.cd);
 }
@@ -387,6 +390,16 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_gfall, sizeof(unsigned long long));
+    if (e == cudaSuccess && params->solid) {
+        e = cudaMalloc(&c->d_solid, (size_t)c->N);
+        unsigned char *h = e == cudaSuccess ? new (std::nothrow) unsigned char[(size_t)c->N] : nullptr;
+        if (e == cudaSuccess && !h) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) {
+            for (long long n = 0; n < c->N; ++n) h[n] = params->solid[n] ? 1 : 0;
+            e = cudaMemcpy(c->d_solid, h, (size_t)c->N, cudaMemcpyHostToDevice);
+        }
+        delete[] h;
+    }
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->own_stream);
@@ -401,6 +414,8 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     c->stream = c->own_stream;
     d.err = c->d_err;
     d.gfall = c->d_gfall;
+    d.solid = c->d_solid;
+    c->p.solid = nullptr;  // the host mask is not retained
     *out = c;
     return TEL_OK;
 }
@@ -415,6 +430,7 @@ extern "C" void tel_destroy(tel_ctx *c)
     }
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_gfall) cudaFree(c->d_gfall);
+    if (c->d_solid) cudaFree(c->d_solid);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->scratch) cudaFree(c->scratch);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -515,7 +531,9 @@ extern "C" int tel_step(tel_ctx *c, int nsteps)
         tel::LaunchArgs A{};
         A.fsrc = c->f[c->cur]; A.gsrc = c->g[c->cur];
         A.fdst = c->f[1 - c->cur]; A.gdst = c->g[1 - c->cur];
-        CUDA_OR_FAIL(c, launch(c, c->p.gamma_mode == TEL_GAMMA_EXACT ? tel::MODE_STEP_EXACT : tel::MODE_STEP, A));
+        const int mode = c->p.gamma_mode == TEL_GAMMA_EXACT ? tel::MODE_STEP_EXACT
+                         : (c->p.gamma_mode == TEL_GAMMA_CLOSED_F64SUM ? tel::MODE_STEP_G64 : tel::MODE_STEP);
+        CUDA_OR_FAIL(c, launch(c, mode, A));
         c->cur = 1 - c->cur;
     }
     return TEL_OK;
@@ -658,6 +676,7 @@ extern "C" int tel_fields_noalloc(int lattice, int nx, int ny, int nz, const tel
         return noalloc_fail(TEL_EINVAL, "tel_fields_noalloc: %lld nodes exceed the fixed scratch of %d nodes",
                             N, TEL_NOALLOC_MAX_NODES);
     if (!f_state || !g_state) return noalloc_fail(TEL_EINVAL, "tel_fields_noalloc: NULL state buffer");
+    if (params->solid) return noalloc_fail(TEL_EINVAL, "tel_fields_noalloc: solid masks need a context (tel_create)");
     double co[4];
     if (tel_coexistence_eos(params->eos, params->a, params->b, params->R, params->T, params->omega, co) != TEL_OK)
         return noalloc_fail(TEL_EINVAL, "no liquid-gas coexistence at T=%g", params->T);
@@ -810,6 +829,8 @@ extern "C" int tel_batch_create(int ncases, const int *nx, const int *ny, const 
         if (params[c].precision != prec) return bfail(nullptr, TEL_EINVAL, "all cases must share one precision");
         if (params[c].gamma_mode != TEL_GAMMA_CLOSED)
             return bfail(nullptr, TEL_EINVAL, "case %d: batches use the closed-form stabiliser (gamma_mode 0)", c);
+        if (params[c].solid)
+            return bfail(nullptr, TEL_EINVAL, "case %d: batches take no solid mask (walls only)", c);
         walls = walls || params[c].bc[0] || params[c].bc[1];
         total += (long long)nx[c] * ny[c];
     }
@@ -927,6 +948,19 @@ static int batch_scratch(tel_batch *b, size_t elems)
     cudaError_t e = cudaMalloc(&b->scratch, elems * sizeof(double));
     if (e != cudaSuccess) { cudaGetLastError(); return bfail(b, TEL_ENOMEM, "scratch: %s", cudaGetErrorString(e)); }
     b->scratch_elems = elems;
+    return TEL_OK;
+}
+
+extern "C" int tel_batch_init_device(tel_batch *b, int c, const double *rho, const double *phi, const double *u)
+{
+    if (!b) return TEL_EINVAL;
+    if (c < 0 || c >= b->ncases || !rho || !phi || !u)
+        return bfail(b, TEL_EINVAL, "tel_batch_init_device: bad case or NULL field");
+    tel::LaunchArgs A = batch_case_args(b, c, 1 - b->cur);  // writes the buffer the next step reads
+    A.in_rho = rho; A.in_phi = phi; A.in_u = u;
+    A.fsrc = A.gsrc = nullptr;
+    BCUDA(b, tel::launch_d2q9(b->precision, tel::MODE_INIT, b->hP[c], A, b->stream));
+    b->initialized = 1;
     return TEL_OK;
 }
 

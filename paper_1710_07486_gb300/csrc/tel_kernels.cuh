@@ -28,8 +28,9 @@
 namespace tel {
 
 // MODE_STEP_EXACT: the step with the exact per-node stabiliser (root of the
-// entropy condition) instead of its closed form.
-enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_FIELDS = 2, MODE_STEP_EXACT = 3 };
+// entropy condition) instead of its closed form.  MODE_STEP_G64: the closed
+// form with its two scalar products accumulated in FP64 (FP32 storage).
+enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_FIELDS = 2, MODE_STEP_EXACT = 3, MODE_STEP_G64 = 4 };
 
 // Equations of state (values of tel_eos): Carnahan-Starling (Eq. 4), and the
 // textbook van der Waals and Peng-Robinson forms named as alternatives.
@@ -83,6 +84,7 @@ struct DevParams {
     double Gamma, inv_tau_g;
     double rho_ref;                   // FP32 shift (0 in FP64)
     int gamma_mode;                   // 0 closed-form stabiliser, 1 exact root
+    const unsigned char *solid;       // per-node solid mask (device), or NULL
     unsigned *err;                    // device error word
     unsigned long long *gfall;        // count of exact-stabiliser fallbacks
     Coef<float> cf;
@@ -388,16 +390,26 @@ __device__ __forceinline__ int gamma_root(const Parts &parts, T beta, T &t, T to
             T fe, ds, dh;
             parts(i, fe, ds, dh);
             const T x = (c * ds + tt * dh) / fe;
-            const T term = dh * log1p_<T>(x);
-            G += term;
-            S += fabs(term);
+            G += dh * log1p_<T>(x);
+            // size of the term before the two parts of x cancel: the scale
+            // of G's rounding
+            S += fabs(dh) * (fabs(c * ds) + fabs(tt * dh)) / fe;
             dG += dh * dh / (fe * ((T)1 + x));
         }
         if (fabs(G) <= tolG * S) { t = tt; return 1; }
         if (G > (T)0) b = tt; else a = tt;
         if (!(b - a > tolT * ((T)1 + fabs(tt)))) { t = (T)0.5 * (a + b); return 1; }
+        // Newton step, or bisection when it leaves the bracket; a step below
+        // rounding ends the iteration when G is at its rounding floor
+        // (within 1e3 of the bar) and bisects when it is not (next to a pole
+        // of ln f'_i the derivative is huge and the step tiny while G is large)
         T tn = tt - G / dG;
-        if (!(tn > a && tn < b) || fabs(tn - tt) <= tolT * ((T)1 + fabs(tt))) tn = (T)0.5 * (a + b);
+        if (!(tn > a && tn < b)) {
+            tn = (T)0.5 * (a + b);
+        } else if (fabs(tn - tt) <= tolT * ((T)1 + fabs(tt))) {
+            if (fabs(G) <= (T)1e3 * tolG * S) { t = tn; return 1; }
+            tn = (T)0.5 * (a + b);
+        }
         tt = tn;
     }
     return -1;
@@ -423,7 +435,7 @@ struct Fused {
     typedef typename V::v4 V4;
     static constexpr int Q = L::Q;
     static constexpr int NT = TX * TY;
-    static constexpr bool STEPPING = MODE == MODE_STEP || MODE == MODE_STEP_EXACT;
+    static constexpr bool STEPPING = MODE == MODE_STEP || MODE == MODE_STEP_EXACT || MODE == MODE_STEP_G64;
     static constexpr bool EXACT = MODE == MODE_STEP_EXACT;
     static constexpr int R2X = TX + 4, R2Y = (D == 3 ? TY + 4 : 1), NA = R2X * R2Y;
     static constexpr int R1X = TX + 2, R1Y = (D == 3 ? TY + 2 : 1), NB = R1X * R1Y;
@@ -452,12 +464,57 @@ struct Fused {
     // pairs of pulled populations (the rest population stays in a register).
     static constexpr int STASH = StoreTraits<ST>::shifted ? 2 * L::REST * NT : Q * NT;
     static constexpr int SMEM_ELEMS = OFF_F + (STEPPING ? STASH : 0);
-    static constexpr size_t SMEM_BYTES = sizeof(CT) * SMEM_ELEMS;
+    // walled path: solid flags of the moment ring, RS slots of NA bytes after
+    // the CT data (none on the fast path, which has no solid nodes)
+    static constexpr size_t SOL_OFF = sizeof(CT) * SMEM_ELEMS;
+    static constexpr size_t SOL_BYTES = FAST ? 0 : (((size_t)RS * NA + 15) / 16) * 16;
+    static constexpr size_t SMEM_BYTES = SOL_OFF + SOL_BYTES;
 
     __device__ static __forceinline__ int idx2(int ox, int oy) { return (ox + 2) + R2X * (oy + OY2); }
     __device__ static __forceinline__ int idx1(int ox, int oy) { return (ox + 1) + R1X * (oy + OY1); }
     __device__ static __forceinline__ int slotR(int m) { int s = m % RS; return s < 0 ? s + RS : s; }
     __device__ static __forceinline__ int slotM(int m) { int s = m % MS; return s < 0 ? s + MS : s; }
+
+    // Solid nodes (walled path only).  Phase A records, per moment slot, a
+    // flag for every node of the tile + ring 2.  A stencil centred at ring
+    // position (ox, oy) of plane m that reads along (cX, cY, cM) gets the
+    // neighbour, or, when that is solid, a fluid ghost mirroring it across
+    // the solid surface: the components of c are set to zero, fewest first
+    // and in axis order x, y, z, until the node reached is fluid (the
+    // reading of the axis walls' neutral wetting, which it reproduces where
+    // solid layers fill the ends of an axis).  flip gets bit a for each
+    // physical axis a that was zeroed: the vector component that changes sign.
+    __device__ static __forceinline__ unsigned char *sol_ring()
+    {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        return smem_raw + SOL_OFF;
+    }
+    __device__ static __forceinline__ bool ring_solid(const unsigned char *sol, int ox, int oy, int m)
+    {
+        return sol[slotR(m) * NA + idx2(ox, oy)] != 0;
+    }
+    __device__ static __forceinline__ void resolve(const unsigned char *sol, int ox, int oy, int m, int &cX, int &cY,
+                                                   int &cM, unsigned &flip)
+    {
+        flip = 0u;
+        if (!ring_solid(sol, ox + cX, oy + cY, m + cM)) return;
+        // physical axes: D3Q27 (x, y, z) = (X, Y, M); D2Q9 (x, y) = (X, M)
+        const int c0 = cX, c1 = D == 3 ? cY : cM, c2 = D == 3 ? cM : 0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const unsigned S = k < 3 ? (1u << k) : (k == 3 ? 3u : (k == 4 ? 5u : (k == 5 ? 6u : 7u)));
+            if (((S & 1u) && !c0) || ((S & 2u) && !c1) || ((S & 4u) && !c2)) continue;
+            const int t0 = (S & 1u) ? 0 : c0, t1 = (S & 2u) ? 0 : c1, t2 = (S & 4u) ? 0 : c2;
+            const int tX = t0, tY = D == 3 ? t1 : 0, tM = D == 3 ? t2 : t1;
+            if (!ring_solid(sol, ox + tX, oy + tY, m + tM)) {
+                cX = tX; cY = tY; cM = tM;
+                flip = S;
+                return;
+            }
+        }
+        flip = (c0 ? 1u : 0u) | (c1 ? 2u : 0u) | (c2 ? 4u : 0u);  // the centre itself
+        cX = cY = cM = 0;
+    }
 
     // Sources of the populations pulled into node (x, y, m): per axis the
     // source coordinate x - c for c = -1, 0, 1 (periodic wrap) as an offset,
@@ -467,6 +524,7 @@ struct Fused {
         int n;                // node index (N < 2^31 is enforced at creation)
         int off[3][3];        // [axis X, Y, M][c + 1]
         unsigned out;         // bit 3*axis + (c + 1)
+        unsigned sol;         // bit i: the source x - c_i is a solid node (walled path only)
     };
 
     __device__ static __forceinline__ void make_nbr(const DevParams &P, int PX, int PY, int PM, int x, int y,
@@ -493,6 +551,18 @@ struct Fused {
                 }
                 b.off[a][c + 1] = sc * stride[a];
                 if (o) b.out |= 1u << (3 * a + c + 1);
+            }
+        }
+        b.sol = 0u;
+        if constexpr (!FAST) {
+            // half-way bounce-back wherever the source of a pull is solid
+            if (P.solid) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int cX = L::pX(i) + 1, cY = L::pY(i) + 1, cM = L::pM(i) + 1;
+                    const unsigned mask = (1u << cX) | (D == 3 ? (1u << (3 + cY)) : 0u) | (1u << (6 + cM));
+                    if (!(b.out & mask) && P.solid[b.off[0][cX] + b.off[1][cY] + b.off[2][cM]]) b.sol |= 1u << i;
+                }
             }
         }
     }
@@ -523,7 +593,7 @@ struct Fused {
     {
         const int cX = L::pX(i) + 1, cY = L::pY(i) + 1, cM = L::pM(i) + 1;
         const unsigned mask = (1u << cX) | (D == 3 ? (1u << (3 + cY)) : 0u) | (1u << (6 + cM));
-        if (b.out & mask) return (long long)(Q - 1 - i) * N + b.n;
+        if ((b.out & mask) || ((b.sol >> i) & 1u)) return (long long)(Q - 1 - i) * N + b.n;
         return (long long)i * N + (b.off[0][cX] + b.off[1][cY] + b.off[2][cM]);
     }
 
@@ -566,7 +636,9 @@ struct Fused {
         // mC = mA - 3; with RS = 6 and MS = 4 the next A/B pass never writes a
         // slot that phase C is still reading.
         const int tid_x = tid % TX, tid_y = tid / TX;
-        const bool need_grp = (MODE == MODE_FIELDS) || P.force_form == 0;
+        // phase C reads the neighbouring planes' moments (or, with solid
+        // nodes, their flags): then one more barrier per iteration
+        const bool need_grp = (MODE == MODE_FIELDS) || P.force_form == 0 || (!FAST && P.solid != nullptr);
         const int iters = (m1 - m0) + (SPLIT ? 4 : 5);
         for (int it = 0; it < iters; ++it) {
             const int mA = m0 - 2 + it;
@@ -587,7 +659,19 @@ struct Fused {
                 const int xx = map_coord(x0 + ox, PX, bX);
                 const int yy = (D == 3 ? map_coord(y0 + oy, PY, bY) : 0);
                 CT rho, phi;
-                if (MODE == MODE_INIT) {
+                bool solid = false;
+                if constexpr (!FAST) {
+                    if (P.solid) {
+                        const long long n = (long long)xx + (long long)PX * ((long long)yy + (long long)PY * mm);
+                        solid = P.solid[n] != 0;
+                        sol_ring()[slotR(mA) * NA + r] = solid ? 1 : 0;
+                    }
+                }
+                if (solid) {
+                    // placeholder moments of a solid node: no fluid stencil reads them
+                    rho = coef<CT>(P).rho_l;
+                    phi = 0;
+                } else if (MODE == MODE_INIT) {
                     const long long n = (long long)xx + (long long)PX * ((long long)yy + (long long)PY * mm);
                     rho = (CT)A.in_rho[n];
                     phi = (CT)A.in_phi[n];
@@ -614,20 +698,46 @@ struct Fused {
                 const V2 ncp = V::pair(-r0, -p0);
                 V2 lap = V::pair((CT)0, (CT)0);
                 CT gx = 0, gy = 0, gz = 0;
-                // over opposite neighbours (i, Q-1-i): the Laplacian takes
-                // both differences to the centre, the gradient the
-                // difference of the two
+                bool masked = false;
+                if constexpr (!FAST) masked = P.solid != nullptr;
+                if (masked) {
+                    // solid nodes: each neighbour through its ghost; a solid
+                    // centre is never read by a fluid stencil
+                    const unsigned char *sol = sol_ring();
+                    if (ring_solid(sol, ox, oy, mB)) {
+                        mu_s[sB * NB + s] = V::pair((CT)0, (CT)0);
+                        if (P.force_form == 1) g_s[sB * NB + s] = V::quad((CT)0, (CT)0, (CT)0, (CT)0);
+                        return;
+                    }
 #pragma unroll
-                for (int i = 0; i < L::REST; ++i) {
-                    const int io = Q - 1 - i;
-                    const V2 va = rp_s[slotR(mB + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
-                    const V2 vb = rp_s[slotR(mB + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))];
-                    const CT wi = (CT)L::w(i);
-                    lap = V::fma(V::pair(wi, wi), V::add(V::add(va, ncp), V::add(vb, ncp)), lap);
-                    const CT d = va.x - vb.x;
-                    if (L::cx(i)) gx += wi * (CT)L::cx(i) * d;
-                    if (L::cy(i)) gy += wi * (CT)L::cy(i) * d;
-                    if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * d;
+                    for (int i = 0; i < Q; ++i) {
+                        if (i == L::REST) continue;
+                        int cX = L::pX(i), cY = L::pY(i), cM = L::pM(i);
+                        unsigned fl;
+                        resolve(sol, ox, oy, mB, cX, cY, cM, fl);
+                        const V2 v = rp_s[slotR(mB + cM) * NA + idx2(ox + cX, oy + cY)];
+                        const CT wi = (CT)L::w(i);
+                        lap = V::fma(V::pair(wi, wi), V::add(v, ncp), lap);
+                        if (L::cx(i)) gx += wi * (CT)L::cx(i) * v.x;
+                        if (L::cy(i)) gy += wi * (CT)L::cy(i) * v.x;
+                        if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * v.x;
+                    }
+                } else {
+                    // over opposite neighbours (i, Q-1-i): the Laplacian takes
+                    // both differences to the centre, the gradient the
+                    // difference of the two
+#pragma unroll
+                    for (int i = 0; i < L::REST; ++i) {
+                        const int io = Q - 1 - i;
+                        const V2 va = rp_s[slotR(mB + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))];
+                        const V2 vb = rp_s[slotR(mB + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))];
+                        const CT wi = (CT)L::w(i);
+                        lap = V::fma(V::pair(wi, wi), V::add(V::add(va, ncp), V::add(vb, ncp)), lap);
+                        const CT d = va.x - vb.x;
+                        if (L::cx(i)) gx += wi * (CT)L::cx(i) * d;
+                        if (L::cy(i)) gy += wi * (CT)L::cy(i) * d;
+                        if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * d;
+                    }
                 }
                 const CT lr = (CT)6 * lap.x;
                 const CT lp = (CT)6 * lap.y;
@@ -739,6 +849,26 @@ struct Fused {
         const CT rho = rp0.x, phi = rp0.y;
         const Coef<CT> &K = coef<CT>(P);
         const CT shift = K.rho_ref;
+        bool masked = false;
+        if constexpr (!FAST) masked = P.solid != nullptr;
+        if (masked && ring_solid(sol_ring(), ox, oy, m)) {
+            // a solid node: zero state (own slots) and zero fields
+            if constexpr (MODE == MODE_FIELDS) {
+                if (A.out_rho) A.out_rho[n] = 0.0;
+                if (A.out_phi) A.out_phi[n] = 0.0;
+                if (A.out_u)
+                    for (int a = 0; a < D; ++a) A.out_u[(long long)a * P.N + n] = 0.0;
+                if (A.out_p) A.out_p[n] = 0.0;
+            } else {
+                ST *fd = reinterpret_cast<ST *>(A.fdst);
+                ST *gd = reinterpret_cast<ST *>(A.gdst);
+                for (int i = 0; i < Q; ++i) {
+                    fd[(long long)i * P.N + n] = (ST)0;
+                    gd[(long long)i * P.N + n] = (ST)0;
+                }
+            }
+            return;
+        }
 
         // FP32 storage, step mode: start the copies of the node's f pulls into
         // its column of the stash now, so that they are in flight during the
@@ -765,25 +895,48 @@ struct Fused {
 #pragma unroll
         for (int a = 0; a < 3; ++a) { gmu[a] = V::pair((CT)0, (CT)0); grp[a] = V::pair((CT)0, (CT)0); }
         const bool need_grp = (MODE == MODE_FIELDS) || P.force_form == 0;
-        // over opposite neighbours (i, Q-1-i): w_i c_i (v(x + c_i) - v(x - c_i))
+        if (masked) {
+            // solid nodes: each neighbour through its ghost (scalar fields)
+            const unsigned char *sol = sol_ring();
 #pragma unroll
-        for (int i = 0; i < L::REST; ++i) {
-            const int io = Q - 1 - i;
-            const V2 vm = V::sub(mu_s[slotM(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i))],
-                                 mu_s[slotM(m + L::pM(io)) * NB + idx1(ox + L::pX(io), oy + L::pY(io))]);
-            const CT wi = (CT)L::w(i);
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const int ca = L::c(i, a);
-                if (ca) gmu[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vm, gmu[a]);
-            }
-            if (need_grp) {
-                const V2 vr = V::sub(rp_s[slotR(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))],
-                                     rp_s[slotR(m + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))]);
+            for (int i = 0; i < Q; ++i) {
+                if (i == L::REST) continue;
+                int cX = L::pX(i), cY = L::pY(i), cM = L::pM(i);
+                unsigned fl;
+                resolve(sol, ox, oy, m, cX, cY, cM, fl);
+                const V2 vm = mu_s[slotM(m + cM) * NB + idx1(ox + cX, oy + cY)];
+                const V2 vr = rp_s[slotR(m + cM) * NA + idx2(ox + cX, oy + cY)];
+                const CT wi = (CT)L::w(i);
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     const int ca = L::c(i, a);
-                    if (ca) grp[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vr, grp[a]);
+                    if (ca) {
+                        gmu[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vm, gmu[a]);
+                        if (need_grp) grp[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vr, grp[a]);
+                    }
+                }
+            }
+        } else {
+            // over opposite neighbours (i, Q-1-i): w_i c_i (v(x + c_i) - v(x - c_i))
+#pragma unroll
+            for (int i = 0; i < L::REST; ++i) {
+                const int io = Q - 1 - i;
+                const V2 vm = V::sub(mu_s[slotM(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i))],
+                                     mu_s[slotM(m + L::pM(io)) * NB + idx1(ox + L::pX(io), oy + L::pY(io))]);
+                const CT wi = (CT)L::w(i);
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const int ca = L::c(i, a);
+                    if (ca) gmu[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vm, gmu[a]);
+                }
+                if (need_grp) {
+                    const V2 vr = V::sub(rp_s[slotR(m + L::pM(i)) * NA + idx2(ox + L::pX(i), oy + L::pY(i))],
+                                         rp_s[slotR(m + L::pM(io)) * NA + idx2(ox + L::pX(io), oy + L::pY(io))]);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        const int ca = L::c(i, a);
+                        if (ca) grp[a] = V::fma(V::pair(wi * (CT)ca, wi * (CT)ca), vr, grp[a]);
+                    }
                 }
             }
         }
@@ -812,10 +965,14 @@ struct Fused {
             for (int i = 0; i < Q; ++i) {
                 if (L::nnz(i) == 0) continue;
                 const CT wi3 = (CT)(3.0 * L::w(i));
-                const int sp_ = slotM(m + L::pM(i));
-                const int kp = idx1(ox + L::pX(i), oy + L::pY(i));
+                int cX = L::pX(i), cY = L::pY(i), cM = L::pM(i);
+                unsigned fl = 0u;
+                if (masked) resolve(sol_ring(), ox, oy, m, cX, cY, cM, fl);
+                const int sp_ = slotM(m + cM);
+                const int kp = idx1(ox + cX, oy + cY);
                 const V4 gq = g_s[sp_ * NB + kp];
-                const CT Gp[3] = {gq.x, gq.y, gq.z};
+                // G at a ghost: the components along mirrored axes change sign
+                const CT Gp[3] = {(fl & 1u) ? -gq.x : gq.x, (fl & 2u) ? -gq.y : gq.y, (fl & 4u) ? -gq.z : gq.z};
                 const CT sj = gq.w;
                 CT cG = 0;
 #pragma unroll
@@ -1181,7 +1338,33 @@ struct Fused {
         // in FP64 from the FP32 ratio (gamma = 2, beta gamma = 2 beta, when
         // <dh|dh> vanishes)
         double gbd = 2.0 * P.beta;
-        if (hh > 1e-30f * rho * rho) gbd = fma(-P.c_gb, (double)(sh * rcp_nr(hh)), 1.0);
+        if constexpr (MODE == MODE_STEP_G64) {
+            // variant: both scalar products accumulated in FP64 from the
+            // FP32 Delta s, Delta h and the FP32 weights 1/f^eq
+            double hhd = 0.0, shd = 0.0;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float2 dh = dh2(k, stash2[k * NT]);
+                const float2 fe = feq2(k, X, Y, Z);
+                const double tx = (double)dh.x * (double)rcp_approx(fe.x);
+                const double ty = (double)dh.y * (double)rcp_approx(fe.y);
+                hhd = fma((double)dh.x, tx, fma((double)dh.y, ty, hhd));
+                float dsk = 0.f;
+                if (L::nnz(k) == 1) {
+                    dsk = DS1[L::cx(k) ? 0 : (L::cy(k) ? 1 : 2)].x;
+                } else if (L::nnz(k) == 2) {
+                    const int pl = L::cz(k) == 0 ? 0 : (L::cy(k) == 0 ? 1 : 2);
+                    const int sg = L::cz(k) == 0 ? L::cx(k) * L::cy(k)
+                                                 : (L::cy(k) == 0 ? L::cx(k) * L::cz(k) : L::cy(k) * L::cz(k));
+                    dsk = sg > 0 ? DS2[pl].x : -DS2[pl].x;
+                }
+                if (L::nnz(k) == 1 || L::nnz(k) == 2) shd = fma((double)dsk, tx + ty, shd);
+            }
+            hhd = fma((double)dl0 * (double)dl0, (double)rcp_approx(fe0), hhd);
+            if (hhd > 1e-30 * (double)rho * (double)rho) gbd = fma(-P.c_gb, shd / hhd, 1.0);
+        } else {
+            if (hh > 1e-30f * rho * rho) gbd = fma(-P.c_gb, (double)(sh * rcp_nr(hh)), 1.0);
+        }
         if constexpr (EXACT) {
             // exact root of the entropy condition, from the closed form, in
             // FP32 on the stashed Delta of each pair
@@ -1323,6 +1506,12 @@ struct Fused {
             if (sx < 0) { if (bx) bb = true; else sx += PX; } else if (sx >= PX) { if (bx) bb = true; else sx -= PX; }
             if (D == 3) { if (sy < 0) { if (by) bb = true; else sy += PY; } else if (sy >= PY) { if (by) bb = true; else sy -= PY; } }
             if (sm < 0) { if (bm) bb = true; else sm += PM; } else if (sm >= PM) { if (bm) bb = true; else sm -= PM; }
+            if constexpr (!FAST) {
+                // a solid source: the node's own reversed slot (bounce-back)
+                if (!bb && P.solid &&
+                    P.solid[(long long)sx + (long long)PX * ((long long)sy + (long long)PY * sm)])
+                    bb = true;
+            }
             const long long k = bb ? (long long)(Q - 1 - i) * P.N + n
                                    : (long long)i * P.N + (long long)sx + (long long)PX * ((long long)sy + (long long)PY * sm);
             fd[k] = (ST)feq;

@@ -33,20 +33,23 @@ template <int D, int TX, int TY, bool FAST>
 static cudaError_t launch_prec(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s)
 {
     if (precision == 0) {
-        if (mode == MODE_STEP) return launch_one<D, TX, TY, double, MODE_STEP, FAST>(P, A, s);
+        // FP64 storage sums everything in FP64 already
+        if (mode == MODE_STEP || mode == MODE_STEP_G64) return launch_one<D, TX, TY, double, MODE_STEP, FAST>(P, A, s);
         if (mode == MODE_STEP_EXACT) return launch_one<D, TX, TY, double, MODE_STEP_EXACT, FAST>(P, A, s);
         if (mode == MODE_INIT) return launch_one<D, TX, TY, double, MODE_INIT, FAST>(P, A, s);
         return launch_one<D, TX, TY, double, MODE_FIELDS, FAST>(P, A, s);
     }
-    if (mode == MODE_STEP || mode == MODE_STEP_EXACT) {
-        const bool exact = mode == MODE_STEP_EXACT;
+    if (mode == MODE_STEP || mode == MODE_STEP_EXACT || mode == MODE_STEP_G64) {
         // aligned four-node vectors in phase A (D3Q27 32 x 8, periodic, nx % 4 == 0)
         if constexpr (D == 3 && TX == 32 && TY == 8 && FAST)
-            if (P.nx % 4 == 0)
-                return exact ? launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST, true>(P, A, s)
-                             : launch_one<D, TX, TY, float, MODE_STEP, FAST, true>(P, A, s);
-        return exact ? launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST>(P, A, s)
-                     : launch_one<D, TX, TY, float, MODE_STEP, FAST>(P, A, s);
+            if (P.nx % 4 == 0) {
+                if (mode == MODE_STEP_EXACT) return launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST, true>(P, A, s);
+                if (mode == MODE_STEP_G64) return launch_one<D, TX, TY, float, MODE_STEP_G64, FAST, true>(P, A, s);
+                return launch_one<D, TX, TY, float, MODE_STEP, FAST, true>(P, A, s);
+            }
+        if (mode == MODE_STEP_EXACT) return launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST>(P, A, s);
+        if (mode == MODE_STEP_G64) return launch_one<D, TX, TY, float, MODE_STEP_G64, FAST>(P, A, s);
+        return launch_one<D, TX, TY, float, MODE_STEP, FAST>(P, A, s);
     }
     if (mode == MODE_INIT) return launch_one<D, TX, TY, float, MODE_INIT, FAST>(P, A, s);
     return launch_one<D, TX, TY, float, MODE_FIELDS, FAST>(P, A, s);
@@ -55,8 +58,8 @@ static cudaError_t launch_prec(int precision, int mode, const DevParams &P, cons
 template <int D, int TX, int TY>
 static cudaError_t launch_lattice(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s)
 {
-    // fast pulls: no bounce-back axis and 32-bit population indices
-    const bool walls = P.bc[0] || P.bc[1] || (D == 3 && P.bc[2]);
+    // fast pulls: no bounce-back axis, no solid node and 32-bit population indices
+    const bool walls = P.bc[0] || P.bc[1] || (D == 3 && P.bc[2]) || P.solid != nullptr;
     const bool fast = !walls && (long long)Lat<D>::Q * P.N < (1LL << 31);
     if (fast) return launch_prec<D, TX, TY, true>(precision, mode, P, A, s);
     return launch_prec<D, TX, TY, false>(precision, mode, P, A, s);

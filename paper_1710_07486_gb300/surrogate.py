@@ -623,9 +623,11 @@ class Hybrid:
         L, B, H, W = self.L, self.B, self.H, self.W
         _ok(L.tel_sur_unpack(_p(f32), _p(self.norm), _p(self.rho), _p(self.phi), _p(self.u), B, H, W, _stream()),
             "unpack")
-        r, p, u = self.rho.cpu().numpy(), self.phi.cpu().numpy(), self.u.cpu().numpy()
+        # the batch works on its own stream: the fields stay on the device,
+        # and only the two stream hand-overs wait on the host
+        self.torch.cuda.current_stream().synchronize()
         for c in range(B):
-            self.lbm.init(c, r[c], p[c], u[c])
+            self.lbm.init_device(c, self.rho[c], self.phi[c], self.u[c])
         self.lbm.step(self.k)
         for c in range(B):
             self.lbm.fields_device(c, self.rho[c], self.phi[c], self.u[c])

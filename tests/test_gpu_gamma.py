@@ -83,10 +83,11 @@ def test_exact_gamma_changes_the_update(orc, T10):
     (1, (36, 10, 21), (1, 0, 1)),      # FP32, walls, scalar phase A
     (1, (13, 12, 11), (0, 1, 0)),
 ])
-@pytest.mark.parametrize("mode", [tel.GAMMA_CLOSED, tel.GAMMA_EXACT])
+@pytest.mark.parametrize("mode", [tel.GAMMA_CLOSED, tel.GAMMA_EXACT, tel.GAMMA_CLOSED_F64SUM])
 def test_fp32_one_step_state_parity(orc, T10, lattice, shape, bc, mode):
     """One FP32-shifted step against the oracle started from the same state,
-    with either stabiliser, periodic and walled."""
+    with each stabiliser variant (the FP64-summed closed form is the closed
+    form for the oracle), periodic and walled."""
     p = asymmetric(T10, force_form=1, gamma_mode=mode)
     g, o, rho, phi, u = setup_pair(orc, lattice, shape, p, bc, precision=tel.FP32_SHIFTED, amp=1e-2)
     g.init(rho, phi, u)

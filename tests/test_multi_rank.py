@@ -68,7 +68,7 @@ REF = r"""
 import os, sys
 sys.path.insert(0, sys.argv[1])
 import bench
-sys.argv = ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3", "--ref-n", "8", "--gpus", "2"]
+sys.argv = ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3", "--cpu-n", "8", "--gpus", "2"]
 bench.main()
 """
 
