@@ -640,11 +640,19 @@ struct Fused {
         // nodes, their flags): then one more barrier per iteration
         const bool need_grp = (MODE == MODE_FIELDS) || P.force_form == 0 || (!FAST && P.solid != nullptr);
         const int iters = (m1 - m0) + (SPLIT ? 4 : 5);
+        // marching direction: with TEL_ALT_MARCH, odd chunks march downwards,
+        // so that two neighbouring chunks read their shared halo planes at
+        // about the same time
+#ifdef TEL_ALT_MARCH
+        const int dir = (bm & 1) ? -1 : 1;
+#else
+        const int dir = 1;
+#endif
         for (int it = 0; it < iters; ++it) {
-            const int mA = m0 - 2 + it;
-            const int mB = mA - (SPLIT ? 1 : 2);
-            const int mC = mA - (SPLIT ? 2 : 3);
-            const bool doA = mA <= m1 + 1;
+            const int mA = dir > 0 ? m0 - 2 + it : m1 + 1 - it;
+            const int mB = mA - dir * (SPLIT ? 1 : 2);
+            const int mC = mA - dir * (SPLIT ? 2 : 3);
+            const bool doA = dir > 0 ? mA <= m1 + 1 : mA >= m0 - 2;
             const bool doB = mB >= m0 - 1 && mB <= m1;
             const int nA = doA ? (VEC ? NAV : NA) : 0;
             const int mm = map_coord(mA, PM, bM);

@@ -616,10 +616,13 @@ class Hybrid:
         self.n = 0
         self.lbm_only = False
         self.log = []
+        self.failed = np.zeros(self.B, dtype=bool)
 
     def lattice_advance(self, f32, out):
         """out = the lattice update's k steps from the fields f32 (the
-        populations restart at their equilibrium for those fields)."""
+        populations restart at their equilibrium for those fields).  Returns
+        a boolean mask of the cases whose lattice stayed stable; a flagged
+        case's output is not a lattice result."""
         L, B, H, W = self.L, self.B, self.H, self.W
         _ok(L.tel_sur_unpack(_p(f32), _p(self.norm), _p(self.rho), _p(self.phi), _p(self.u), B, H, W, _stream()),
             "unpack")
@@ -631,17 +634,29 @@ class Hybrid:
         self.lbm.step(self.k)
         for c in range(B):
             self.lbm.fields_device(c, self.rho[c], self.phi[c], self.u[c])
-        self.lbm.sync()
+        ok = np.array(self.lbm.errors()) == 0  # synchronises and clears the flags
         _ok(L.tel_sur_pack(_p(self.rho), _p(self.phi), _p(self.u), _p(self.norm), _p(out), None, B, H, W,
                            _stream()), "pack")
+        return ok
+
+    def _take(self, f32, src, ok):
+        """f32[c] = src[c] for the cases in ok (the others keep f32)."""
+        if ok.all():
+            f32.copy_(src)
+        else:
+            idx = self.torch.from_numpy(np.nonzero(ok)[0]).to(f32.device)
+            f32[idx] = src[idx]
 
     def advance(self, f32):
-        """Advance f32 in place by k steps; returns which path produced it."""
+        """Advance f32 in place by k steps; returns which path produced it.
+        A case whose restarted lattice flags an unstable node has no judge:
+        it keeps the surrogate's proposal and is marked in ``failed``."""
         B, HW = self.B, self.H * self.W
         self.n += 1
         if self.lbm_only:
-            self.lattice_advance(f32, self.ref)
-            f32.copy_(self.ref)
+            ok = self.lattice_advance(f32, self.ref)
+            self.failed |= ~ok
+            self._take(f32, self.ref, ok)
             self.log.append("lattice")
             return "lattice"
         _ok(self.L.tel_sur_sums(_p(f32), _p(self.sums), B, self.H, self.W, _stream()), "sums")
@@ -652,14 +667,18 @@ class Hybrid:
         resid = np.abs(after - before) / HW
         path = "surrogate"
         if np.any(resid > self.mass_tol):
-            self.lattice_advance(f32, self.ref)
-            f32.copy_(self.ref)
+            ok = self.lattice_advance(f32, self.ref)
+            self.failed |= ~ok
+            f32.copy_(self.prop)
+            self._take(f32, self.ref, ok)
             path = "lattice (mass residual)"
         elif self.check_every and self.n % self.check_every == 0:
-            self.lattice_advance(f32, self.ref)
+            ok = self.lattice_advance(f32, self.ref)
+            self.failed |= ~ok
             err = self.pred.errors(self.prop, self.ref)
-            if np.any(err[:, :2] > self.err_tol):
-                f32.copy_(self.ref)
+            if np.any(err[ok, :2] > self.err_tol):
+                f32.copy_(self.prop)
+                self._take(f32, self.ref, ok)
                 self.lbm_only = True
                 path = "lattice (error check failed)"
             else:

@@ -377,7 +377,7 @@ def test_hybrid_hands_back_to_the_lattice_update(snaps):
     assert [hy.advance(f) for _ in range(2)] == ["surrogate", "surrogate (checked)"]
     # the lattice path of the hybrid reproduces the lattice update from the same fields
     ref = torch.empty_like(st)
-    hy.lattice_advance(st, ref)
+    assert hy.lattice_advance(st, ref).all() and not hy.failed.any()
     e = hy.pred.errors(ref, sn.store[1, :4].contiguous())
     assert np.all(e[:, :2] < 5e-2), e
 
