@@ -321,7 +321,7 @@ def run_c5(args):
     cur = sn.store[0, test].contiguous().clone()
     for _ in range(4):  # warm-up: first calls, and the batch's step graphs via a check
         hy.advance(cur.clone())
-    hy.n, hy.lbm_only, hy.log = 0, False, []
+    hy.n, hy.lbm_only, hy.lbm_live, hy.log = 0, False, False, []
     hy.failed[:] = False
     outs = []
     torch.cuda.synchronize()

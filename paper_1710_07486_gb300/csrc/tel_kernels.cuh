@@ -39,6 +39,14 @@ enum Eos : int { EOS_CS = 0, EOS_VDW = 1, EOS_PR = 2 };
 // Error bits raised by the device (see TEL_EUNSTABLE).
 enum : unsigned { ERR_RHO = 1u, ERR_VEL = 2u, ERR_NAN = 4u };
 
+// Raise error bits in the device error word.  The word is read first and the
+// atomic skipped when the bits are already set: when a whole lattice goes
+// bad every node would otherwise queue an atomic on the same address.
+__device__ __forceinline__ void raise_err(unsigned *err, unsigned bits)
+{
+    if ((*reinterpret_cast<volatile unsigned *>(err) & bits) != bits) atomicOr(err, bits);
+}
+
 // Model coefficients in the compute precision (float copies for the FP32
 // path so that no double-to-float conversion runs on the slow FP64 pipe).
 template <typename T>
@@ -1044,7 +1052,7 @@ struct Fused {
 
         if (MODE == MODE_FIELDS) {
             fields_node(P, A, n, rho, phi, j, F, gr, gf, mu0.x, mu_phi);
-            if (bad) atomicOr(P.err, bad);
+            if (bad) raise_err(P.err, bad);
             return;
         }
 
@@ -1157,7 +1165,7 @@ struct Fused {
                 const CT dh = fi - feq - ds;
                 fd[(long long)i * P.N + n] = fi - ((CT)2 * bet * ds + gb * dh) + (feqF - feq);
             }
-            if (bad) atomicOr(P.err, bad);
+            if (bad) raise_err(P.err, bad);
         }
     }
 
@@ -1442,7 +1450,7 @@ struct Fused {
         }
         fd[didx(L::REST)] = fsum - (oth.x + oth.y);
 
-        if (bad) atomicOr(P.err, bad);
+        if (bad) raise_err(P.err, bad);
     }
 
     // Delta s_i: the population vector whose natural moments vanish except
@@ -1525,7 +1533,7 @@ struct Fused {
             fd[k] = (ST)feq;
             gd[k] = (ST)ge;
         }
-        if (bad) atomicOr(P.err, bad);
+        if (bad) raise_err(P.err, bad);
     }
 
     __device__ static void fields_node(const DevParams &P, const LaunchArgs &A, long long n, CT rho, CT phi,

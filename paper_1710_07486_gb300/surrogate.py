@@ -591,7 +591,8 @@ class Hybrid:
         the lattice update from the same fields exceeds ``err_tol`` for
         density or composition in any sample;
     a rejected advance is replaced by the lattice update's result, and after
-    a failed error check the remaining advances use the lattice update only.
+    a failed error check the remaining advances use the lattice update only,
+    continuing from its own populations.
     """
 
     def __init__(self, net, params, H, W, k, scale, mass_tol=1e-4, err_tol=1e-2, check_every=4):
@@ -615,22 +616,26 @@ class Hybrid:
         self.mass_tol, self.err_tol, self.check_every = mass_tol, err_tol, check_every
         self.n = 0
         self.lbm_only = False
+        self.lbm_live = False
         self.log = []
         self.failed = np.zeros(self.B, dtype=bool)
 
-    def lattice_advance(self, f32, out):
-        """out = the lattice update's k steps from the fields f32 (the
-        populations restart at their equilibrium for those fields).  Returns
-        a boolean mask of the cases whose lattice stayed stable; a flagged
+    def lattice_advance(self, f32, out, restart=True):
+        """out = the lattice update's k steps from the fields f32 (restart:
+        the populations restart at their equilibrium for those fields), or
+        from the lattice's own populations left by its previous advance
+        (restart=False, when f32 is that advance's result).  Returns a
+        boolean mask of the cases whose lattice stayed stable; a flagged
         case's output is not a lattice result."""
         L, B, H, W = self.L, self.B, self.H, self.W
-        _ok(L.tel_sur_unpack(_p(f32), _p(self.norm), _p(self.rho), _p(self.phi), _p(self.u), B, H, W, _stream()),
-            "unpack")
-        # the batch works on its own stream: the fields stay on the device,
-        # and only the two stream hand-overs wait on the host
-        self.torch.cuda.current_stream().synchronize()
-        for c in range(B):
-            self.lbm.init_device(c, self.rho[c], self.phi[c], self.u[c])
+        if restart:
+            _ok(L.tel_sur_unpack(_p(f32), _p(self.norm), _p(self.rho), _p(self.phi), _p(self.u), B, H, W,
+                                 _stream()), "unpack")
+            # the batch works on its own stream: the fields stay on the
+            # device, and only the two stream hand-overs wait on the host
+            self.torch.cuda.current_stream().synchronize()
+            for c in range(B):
+                self.lbm.init_device(c, self.rho[c], self.phi[c], self.u[c])
         self.lbm.step(self.k)
         for c in range(B):
             self.lbm.fields_device(c, self.rho[c], self.phi[c], self.u[c])
@@ -654,7 +659,9 @@ class Hybrid:
         B, HW = self.B, self.H * self.W
         self.n += 1
         if self.lbm_only:
-            ok = self.lattice_advance(f32, self.ref)
+            # the lattice continues from its own populations (no restart)
+            ok = self.lattice_advance(f32, self.ref, restart=not self.lbm_live)
+            self.lbm_live = True
             self.failed |= ~ok
             self._take(f32, self.ref, ok)
             self.log.append("lattice")
@@ -680,6 +687,7 @@ class Hybrid:
                 f32.copy_(self.prop)
                 self._take(f32, self.ref, ok)
                 self.lbm_only = True
+                self.lbm_live = bool(ok.all())  # the lattice's populations hold f32's state
                 path = "lattice (error check failed)"
             else:
                 f32.copy_(self.prop)
