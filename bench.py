@@ -323,12 +323,15 @@ def run_c5(args):
         hy.advance(cur.clone())
     hy.n, hy.lbm_only, hy.lbm_live, hy.log = 0, False, False, []
     hy.failed[:] = False
-    outs = []
+    outs, adv_ms = [], []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in range(nadv):
+        ta = time.perf_counter()
         hy.advance(cur)
         outs.append(cur.clone())
+        torch.cuda.synchronize()
+        adv_ms.append(round(1e3 * (time.perf_counter() - ta), 3))
     torch.cuda.synchronize()
     t_hybrid = time.perf_counter() - t0
     e_all = np.array([pr.errors(outs[s], sn.store[s + 1, test].contiguous()) for s in range(nadv)])
@@ -392,6 +395,7 @@ def run_c5(args):
                    "trajectories": int(Bt), "wall_s": round(t_hybrid, 4), "lattice_wall_s": round(t_plain, 4),
                    "paths": paths, "check_every": 4, "mass_tol": 1e-4, "err_tol": 1e-2,
                    "cases_without_judge": int(hy.failed.sum()),
+                   "advance_ms": adv_ms, "path_per_advance": list(hy.log),
                    "error_mean": {"rho": round(float(e_hy[:, :, 0].mean()), 6),
                                   "phi": round(float(e_hy[:, :, 1].mean()), 6),
                                   "u": round(float(e_hy[:, :, 2].mean()), 6)},
@@ -606,7 +610,8 @@ def run_gpu(args):
                                     "the gas-side chemical potential's two pieces",
                        "force_form": "lattice", "B": round(w["B"], 4), "We": round(w["We"], 3),
                        "sigma12_over_sigma1g": w["sigma_ratio"], "seed": args.seed,
-                       "l2": "state 7.2 GB per step (read 3.6 GB + write 3.6 GB) > L2; no flush needed",
+                       "l2": f"state {bpu * N / 1e9:.1f} GB per step (read {bpu * N / 2e9:.1f} GB + write "
+                             f"{bpu * N / 2e9:.1f} GB) > L2; no flush needed",
                        "parallelism": f"replicas x{world}", "state_after_timed_steps": status},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,

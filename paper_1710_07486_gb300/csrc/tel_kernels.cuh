@@ -1565,11 +1565,18 @@ struct Fused {
 #ifndef TEL_MIN_BLOCKS_FP32
 #define TEL_MIN_BLOCKS_FP32 2
 #endif
+#ifndef TEL_D2Q9_WARPS_PER_SM
+#define TEL_D2Q9_WARPS_PER_SM 24
+#endif
 template <typename ST> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<float> { static constexpr int value = TEL_MIN_BLOCKS_FP32; };
+// D2Q9 FP32 rows of 64 nodes: 12 CTAs (24 warps) per SM, as for the batches
+template <int D, int NTH, typename ST> struct KernelMinBlocks { static constexpr int value = MinBlocks<ST>::value; };
+template <int NTH> struct KernelMinBlocks<2, NTH, float> { static constexpr int value = TEL_D2Q9_WARPS_PER_SM * 32 / NTH; };
 
 template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false>
-__global__ void __launch_bounds__(TX * TY, MinBlocks<ST>::value) fused_kernel(const DevParams P, const LaunchArgs A)
+__global__ void __launch_bounds__(TX * TY, (KernelMinBlocks<D, TX * TY, ST>::value))
+    fused_kernel(const DevParams P, const LaunchArgs A)
 {
     Fused<D, TX, TY, ST, MODE, FAST, VEC>::run(P, A);
 }
@@ -1577,8 +1584,17 @@ __global__ void __launch_bounds__(TX * TY, MinBlocks<ST>::value) fused_kernel(co
 // Batched persistent D2Q9 step: each CTA walks a work list of (case, tile,
 // chunk) items over many independent lattices; each case's parameter block
 // and buffers are copied into shared memory before its item runs.
+// Resident CTAs per SM requested for the batched kernel.  FP32: 24 warps
+// per SM (24 CTAs of width 32, 12 of width 64), which caps the registers at
+// 80-85 per thread without spills (measured with width 32 on the 256-case
+// workload: 15640 MLUPS, against 14168 with 2 CTAs requested (115 registers,
+// 17 CTAs resident) and 13553 with 32 (64 registers, small spills)).  FP64:
+// 2, its collision needs its registers.
+template <int TX, typename ST> struct BatchMinBlocks { static constexpr int value = 2; };
+template <int TX> struct BatchMinBlocks<TX, float> { static constexpr int value = 768 / TX; };
+
 template <int TX, typename ST, bool FAST>
-__global__ void __launch_bounds__(TX, MinBlocks<ST>::value)
+__global__ void __launch_bounds__(TX, (BatchMinBlocks<TX, ST>::value))
     batch_kernel(const DevParams *Ps, const LaunchArgs *As, const int4 *items, int nitems)
 {
     __shared__ DevParams Psh;
