@@ -89,7 +89,8 @@ typedef struct {
     int bc[3];                        /* tel_bc per axis (bc[2] ignored for D2Q9) */
     int eos;                          /* tel_eos: TEL_EOS_CS (Eq. 4, default 0), TEL_EOS_VDW, TEL_EOS_PR */
     double omega;                     /* Peng-Robinson acentric factor (TEL_EOS_PR only) */
-    int gamma_mode;                   /* tel_gamma_mode: TEL_GAMMA_CLOSED (default 0) or TEL_GAMMA_EXACT */
+    int gamma_mode;                   /* tel_gamma_mode: TEL_GAMMA_CLOSED (default 0), TEL_GAMMA_EXACT,
+                                         TEL_GAMMA_CLOSED_F64SUM */
     const unsigned char *solid;       /* optional host solid mask [nz][ny][nx] (nonzero = solid),
                                          copied by tel_create; NULL = no solid nodes (see below) */
 } tel_params;
@@ -113,8 +114,9 @@ typedef struct {
  *     expanded to second order in f - f^eq;
  *   TEL_GAMMA_EXACT: per node, the root of the entropy condition
  *     sum_i Delta h_i ln(f'_i / feq_i) = 0 (the gamma that maximises the
- *     entropy of f' on the collision line), by bracketed Newton from the
- *     closed form (at most 20 evaluations; FP64, or FP32 in the FP32 mode).
+ *     entropy of f' on the collision line), by Newton from the closed form
+ *     kept in a bracket by bisection (at most 20 evaluations; FP64, or FP32
+ *     in the FP32 mode, where a few unbracketed Newton steps come first).
  *     Where no gamma keeps every f'_i positive, or the iteration does not
  *     converge, the node keeps the closed form and a device counter is
  *     incremented (tel_gamma_fallbacks).  Where Delta h has entries of one

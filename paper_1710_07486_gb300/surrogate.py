@@ -649,8 +649,9 @@ class Hybrid:
         if ok.all():
             f32.copy_(src)
         else:
-            idx = self.torch.from_numpy(np.nonzero(ok)[0]).to(f32.device)
-            f32[idx] = src[idx]
+            # one contiguous copy per case: no index tensor, no host upload
+            for c in np.nonzero(ok)[0]:
+                f32[c].copy_(src[c])
 
     def advance(self, f32):
         """Advance f32 in place by k steps; returns which path produced it.
