@@ -224,6 +224,64 @@ def test_network_gradients_against_oracle():
     assert max(ew) <= 2e-1, np.round(ew, 4)
 
 
+@pytest.mark.parametrize("B,H,W", [(2, 32, 32), (1, 8, 128)])
+def test_network_wiring_layer_by_layer(B, H, W):
+    """Every op of the library's forward and backward pass against the
+    oracle's op applied to the library's own stored inputs (tests/sur_wiring):
+    one BF16 rounding per comparison, so the bar is one BF16 ulp per element
+    for stored activations and gradients and 1e-4 (norm) for the FP32 weight
+    and bias gradients.  (1, 8, 128) runs the tcgen05 convolutions on the
+    top level, forward and input gradient."""
+    from tests.sur_wiring import check
+    widths = (16, 16, 32)
+    ops = so.arch(*widths)
+    net = S.Net(widths, seed=13)
+    pl = net.plan(B, H, W)
+    assert [r[0] for r in pl.recs] == [op[0] for op in ops]
+    g = np.random.default_rng(14)
+    w = torch.from_numpy(net.w32.cpu().numpy()).to(BF).float().numpy()
+    for k in range(len(net.convs)):
+        co = net.convs[k][2]
+        w[net.boff[k]:net.boff[k] + co] = g.normal(0, 0.05, co)
+    net.set_host_weights(w)
+    lay = net.host_layers()
+    Ws = [Wk.transpose(0, 2, 1) for Wk, _ in lay]
+    bs = [bk for _, bk in lay]
+    x = bf16_values(g, (B, H, W, so.CIN))
+    dout_h = bf16_values(g, (B, H, W, so.COUT))
+    dout = dev_bf16(dout_h)
+    net.zero_grad()
+    net.forward(dev_bf16(x), B, H, W)
+    net.backward(dout, B, H, W)
+    torch.cuda.synchronize()
+    gh = net.g.cpu().numpy().astype(np.float64)
+    fwd, bwd = [None] * len(ops), [None] * len(ops)
+    for i, r in enumerate(pl.recs):
+        kind = r[0]
+        if kind == "conv":
+            _, k, ci, co, relu, h, w_, _, y = r
+            fwd[i] = host(y)
+            bwd[i] = {"dz": host(pl.dz[k]) if relu else None,
+                      "dx": host(pl.dx[id(r)]) if k > 0 else None,
+                      "dW": gh[net.woff[k]:net.woff[k] + 9 * co * ci].reshape(9, co, ci).transpose(0, 2, 1),
+                      "db": gh[net.boff[k]:net.boff[k] + co]}
+        elif kind in ("pool", "up"):
+            fwd[i] = host(r[4])
+            bwd[i] = {"dx": host(pl.dx[id(r)])}
+        elif kind == "add":
+            fwd[i] = host(r[5])
+            bwd[i] = {}
+        elif kind == "save":
+            bwd[i] = {"dx": host(pl.dx[id(r)])}
+    # the last convolution has no ReLU: its dz is the incoming gradient
+    last = max(i for i, op in enumerate(ops) if op[0] == "conv")
+    assert not ops[last][4]
+    bwd[last]["dz"] = dout_h
+    mis = check(ops, Ws, bs, x, dout_h, fwd, bwd, to_bf16)
+    worst = sorted(mis, key=lambda m: -m[2])[:4]
+    assert max(m[2] for m in mis) <= 1.0, worst
+
+
 def test_adam_and_bf16_copy_against_oracle():
     g = np.random.default_rng(5)
     n = 5000

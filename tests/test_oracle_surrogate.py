@@ -141,3 +141,37 @@ def test_field_errors_definition():
     p[..., 0] *= 1.01
     e = so.field_errors(p, t)
     assert np.isclose(e["rho"], 0.01) and e["phi"] == 0 and e["u"] == 0
+
+
+def _wiring_case(seed=3, widths=(8, 8, 16), B=1, H=16, W=16):
+    from tests.sur_wiring import to_bf16
+    g = np.random.default_rng(seed)
+    ops = so.arch(*widths)
+    Ws, bs = so.init_params(ops, seed)
+    Ws = [to_bf16(w) for w in Ws]
+    bs = [g.normal(0.0, 0.05, size=b.shape) for b in bs]
+    x = to_bf16(g.normal(size=(B, H, W, so.CIN)))
+    dout = to_bf16(g.normal(size=(B, H, W, so.COUT)))
+    return ops, Ws, bs, x, dout
+
+
+def test_wiring_check_passes_a_correct_network():
+    from tests.sur_wiring import check, oracle_records, to_bf16
+    ops, Ws, bs, x, dout = _wiring_case()
+    fwd, bwd = oracle_records(ops, Ws, bs, x, dout, to_bf16)
+    mis = check(ops, Ws, bs, x, dout, fwd, bwd, to_bf16)
+    assert len(mis) > 3 * len(Ws)
+    assert max(m for _, _, m in mis) <= 1e-9, [m for m in mis if m[2] > 1e-9]
+
+
+@pytest.mark.parametrize("plant", ["skip_scale", "skip_source", "relu_mask", "weight_flip", "wgrad_tap",
+                                   "pool_scale"])
+def test_wiring_check_catches_planted_mistakes(plant):
+    """Each planted wiring mistake is flagged, at three times the pass bar
+    or more (a skip scaled by 0.97 is about four BF16 ulps)."""
+    from tests.sur_wiring import check, oracle_records, to_bf16
+    ops, Ws, bs, x, dout = _wiring_case()
+    fwd, bwd = oracle_records(ops, Ws, bs, x, dout, to_bf16, plant=plant)
+    mis = check(ops, Ws, bs, x, dout, fwd, bwd, to_bf16)
+    bad = [m for m in mis if m[2] > 1.0]
+    assert bad and max(m[2] for m in bad) > 3.0, (plant, sorted(mis, key=lambda m: -m[2])[:3])
