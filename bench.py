@@ -606,8 +606,9 @@ def run_gpu(args):
             "config": {"workload": f"D3Q27 {n}^3 periodic, density ratio 1000, FP32-shifted populations "
                                    "(closed-form stabiliser), off-centre collision of immiscible drops R=30",
                        "lattice": "D3Q27", "nodes": N,
-                       "precision": "fp32_shifted storage; fp32 arithmetic with fp64 beta*gamma and fp64 sum of "
-                                    "the gas-side chemical potential's two pieces",
+                       "precision": "fp32_shifted storage; fp32 arithmetic, with beta*gamma and the gas-side "
+                                    "chemical potential's two-piece sum in double-float form (error-free "
+                                    "transformations, rounded once to fp32)",
                        "force_form": "lattice", "B": round(w["B"], 4), "We": round(w["We"], 3),
                        "sigma12_over_sigma1g": w["sigma_ratio"], "seed": args.seed,
                        "l2": f"state {bpu * N / 1e9:.1f} GB per step (read {bpu * N / 2e9:.1f} GB + write "

@@ -57,12 +57,14 @@ typedef enum { TEL_D2Q9 = 0, TEL_D3Q27 = 1 } tel_lattice;
 
 /* TEL_FP64: populations stored and updated in FP64.
  * TEL_FP32_SHIFTED: populations stored in FP32 as f_i - w_i rho_ref (and
- * g_i - w_i * 0); arithmetic in FP32 except where a cancellation happens,
- * which is FP64: the entropic stabiliser beta gamma = 1 - (2 beta - 1) q from
- * the ratio q of its scalar products, and, on the gas side
- * (rho < sqrt(rho_g rho_l)), the sum of the cancellation-free pieces of the
- * equation-of-state chemical potential's difference to its value at rho_g
- * (Eq. 4; the van der Waals and Peng-Robinson gas sides are FP64 throughout). */
+ * g_i - w_i * 0); arithmetic in FP32.  Where a cancellation happens the
+ * value of the FP64 expression rounded to FP32 is obtained in double-float
+ * FP32 arithmetic (error-free transformations, one final rounding): the
+ * entropic stabiliser beta gamma = 1 - (2 beta - 1) q from the ratio q of its
+ * scalar products, and, on the gas side (rho < sqrt(rho_g rho_l)), the sum of
+ * the cancellation-free pieces of the equation-of-state chemical potential's
+ * difference to its value at rho_g (Eq. 4; the van der Waals and
+ * Peng-Robinson gas sides are FP64 throughout). */
 typedef enum { TEL_FP64 = 0, TEL_FP32_SHIFTED = 1 } tel_precision;
 
 typedef enum { TEL_PERIODIC = 0, TEL_BOUNCEBACK = 1 } tel_bc;

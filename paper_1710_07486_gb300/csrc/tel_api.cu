@@ -341,11 +341,15 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
         d.q_g_x2 = (float)(2.0 * q);
         d.gRT8b_f = (float)(d.lam1h * 8.0 * d.RT * p.b);
         d.ga2_f = (float)(d.lam1h * 2.0 * p.a);
+        d.gRT_hi = (float)d.gRT;
+        d.gRT_lo = (float)(d.gRT - (double)d.gRT_hi);
     }
     const double tau = 3.0 * p.nu + 0.5;
     d.beta = 1.0 / (2.0 * tau);
     d.inv_beta = 2.0 * tau;
     d.c_gb = 2.0 * d.beta - 1.0;
+    d.c_gb_hi = (float)d.c_gb;
+    d.c_gb_lo = (float)(d.c_gb - (double)d.c_gb_hi);
     d.Gamma = p.Gamma;
     d.inv_tau_g = 1.0 / p.tau_g;
     d.rho_ref = p.precision == TEL_FP32_SHIFTED ? (p.rho_ref > 0 ? p.rho_ref : co[0]) : 0.0;

@@ -86,9 +86,11 @@ struct DevParams {
     float b_f;                        // b
     float q_g, q_g2, q_g_x2;          // q = 1/(b rho_g - 4), q^2, 2q
     float gRT8b_f, ga2_f;             // lambda1/2 times 8 RT b and 2a
+    float gRT_hi, gRT_lo;             // lambda1/2 times RT as two floats (hi + lo)
     // collision
     double beta, inv_beta;            // beta = 1/(2 tau)
     double c_gb;                      // 2 beta - 1: beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh>
+    float c_gb_hi, c_gb_lo;           // 2 beta - 1 as two floats (hi + lo)
     double Gamma, inv_tau_g;
     double rho_ref;                   // FP32 shift (0 in FP64)
     int gamma_mode;                   // 0 closed-form stabiliser, 1 exact root
@@ -261,8 +263,13 @@ __device__ __forceinline__ void mu_wells(const DevParams &P, T rho, T phi, T &mr
 //    h(rho) - h(rho_g) = (r - q) [16 (r^2 + r q + q^2) - 2 (r + q)] = -b D B,
 //    B = 2 r q [8 (r^2 + r q + q^2) - (r + q)], a sum of terms of one sign
 //    (r, q < 0 for b rho < 4).
-// So the result is (lambda1/2) [RT ln(rho/rho_g) + D (8RT b B - 2a)], whose
-// two products are added in FP64.
+// So the result is (lambda1/2) [RT ln(rho/rho_g) + D (8RT b B - 2a)].  Its
+// two products are added in double-float arithmetic: each product's rounding
+// error recovered by an FMA, the sum's by Knuth's TwoSum, and everything
+// rounded once to FP32 at the end -- the value of an FP64 sum rounded to FP32,
+// to within one FP32 ulp, at the issue cost of a dozen FP32 operations (the
+// FP64 pipe of this GPU runs at 1/64 of the FP32 rate).  The _rn intrinsics
+// keep the compiler from contracting the products into the sums.
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float r;
@@ -295,7 +302,15 @@ __device__ __forceinline__ float mu_eos_gas(const DevParams &P, float rho)
     const float rq = r + P.q_g;
     const float B = (P.q_g_x2 * r) * fmaf(8.f, fmaf(r, rq, P.q_g2), -rq);
     const float c = fmaf(P.gRT8b_f, B, -P.ga2_f);
-    return (float)fma(P.gRT, (double)L, (double)D * (double)c);
+    const float p1 = __fmul_rn(P.gRT_hi, L);
+    const float p2 = __fmul_rn(D, c);
+    float e = fmaf(P.gRT_hi, L, -p1);
+    e = fmaf(P.gRT_lo, L, e);
+    e = __fadd_rn(e, fmaf(D, c, -p2));
+    const float sum = __fadd_rn(p1, p2);
+    const float bp = __fsub_rn(sum, p1);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(p1, __fsub_rn(sum, bp)), __fsub_rn(p2, bp)));
+    return __fadd_rn(sum, e);
 }
 
 // Bulk free energy f_B of Eq. 2 (Psi_eos - Psi_0 with the common tangent).
@@ -1404,11 +1419,15 @@ struct Fused {
         const float hh = fmaf(dl0 * dl0, rcp_approx(fe0), hh2.x + hh2.y);
         const float sh = (shp.x + shp.y) - (shn.x + shn.y);
 
-        // ---- stabiliser: beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh>, formed
-        // in FP64 from the FP32 ratio (gamma = 2, beta gamma = 2 beta, when
-        // <dh|dh> vanishes)
-        double gbd = 2.0 * P.beta;
+        // ---- stabiliser: beta gamma = 1 - (2 beta - 1) <ds|dh>/<dh|dh> from the
+        // FP32 ratio q, with 2 beta - 1 as two floats and one rounding (the
+        // value of the FP64 expression rounded to FP32); gamma = 2, beta gamma
+        // = 2 beta, when <dh|dh> vanishes
+        const bool has_q = hh > 1e-30f * rho * rho;
+        const float q = has_q ? sh * rcp_nr(hh) : 0.f;
+        float gb = 2.f * K.beta;
         if constexpr (MODE == MODE_STEP_G64) {
+            double gbd = 2.0 * P.beta;
             // variant: both scalar products accumulated in FP64 from the
             // FP32 Delta s, Delta h and the FP32 weights 1/f^eq
             double hhd = 0.0, shd = 0.0;
@@ -1432,13 +1451,14 @@ struct Fused {
             }
             hhd = fma((double)dl0 * (double)dl0, (double)rcp_approx(fe0), hhd);
             if (hhd > 1e-30 * (double)rho * (double)rho) gbd = fma(-P.c_gb, shd / hhd, 1.0);
+            gb = (float)gbd;
         } else {
-            if (hh > 1e-30f * rho * rho) gbd = fma(-P.c_gb, (double)(sh * rcp_nr(hh)), 1.0);
+            if (has_q) gb = fmaf(-P.c_gb_hi, q, fmaf(-P.c_gb_lo, q, 1.f));
         }
         if constexpr (EXACT) {
             // exact root of the entropy condition, from the closed form, in
             // FP32 on the stashed Delta of each pair
-            if (hh > 1e-30f * rho * rho) {
+            if (has_q) {
                 auto ds_pair = [&](int k) -> float {
                     if (L::nnz(k) == 1) return DS1[L::cx(k) ? 0 : (L::cy(k) ? 1 : 2)].x;
                     if (L::nnz(k) == 2) {
@@ -1458,13 +1478,13 @@ struct Fused {
                     fe = i < L::REST ? fe2.x : fe2.y;
                     dh = (i < L::REST ? dl2.x : dl2.y) - dsv;
                 };
-                float t = (float)(1.0 - gbd);
+                // t = 1 - beta gamma = (2 beta - 1) q, the closed form
+                float t = fmaf(P.c_gb_hi, q, P.c_gb_lo * q);
                 const int rc = gamma_root<float, Q>(parts, K.beta, t, 1e-5f, 1e-7f);
-                if (rc > 0) gbd = 1.0 - (double)t;
+                if (rc > 0) gb = 1.f - t;
                 else if (rc < 0) atomicAdd(P.gfall, 1ull);
             }
         }
-        const float gb = (float)gbd;
         if (!isfinite(gb)) bad |= ERR_NAN;
 
         // ---- output: f - beta (2 Delta s + gamma Delta h) + f^eq(u + F/rho) - f^eq(u)

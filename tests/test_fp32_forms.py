@@ -43,10 +43,11 @@ def test_gas_side_divided_difference_identity():
 
 @pytest.mark.parametrize("ratio", [3.0, 10.0, 100.0, 1000.0])
 def test_gas_side_float32_accuracy(orc, ratio):
-    """float32 pieces (rho_g as two floats, FP64 sum of the two products)
-    against the oracle's FP64 (lambda1/2)(dPsi~(rho) - dPsi~(rho_g)) over
-    [0.3 rho_g, sqrt(rho_g rho_l)]: within 1e-6 of the largest |mu| there
-    (measured 1e-7 to 5e-7)."""
+    """float32 pieces (rho_g as two floats; the two products summed in
+    double-float arithmetic -- FMA product errors and a TwoSum -- and rounded
+    once to float32, as the kernel does) against the oracle's FP64
+    (lambda1/2)(dPsi~(rho) - dPsi~(rho_g)) over [0.3 rho_g, sqrt(rho_g rho_l)]:
+    within 1e-6 of the largest |mu| there (measured 1e-7 to 5e-7)."""
     T = orc.temperature_for_ratio(A, B, RGAS, ratio)
     rg, rl, _, _ = orc.coexistence(A, B, RGAS, T)
     RT, lam1h = RGAS * T, 0.3
@@ -62,7 +63,25 @@ def test_gas_side_float32_accuracy(orc, ratio):
     rq = r + q
     Bv = (f32(2) * q * r) * (f32(8) * (r * rq + f32(q * q)) - rq)
     c = f32(lam1h * 8 * RT * B) * Bv - f32(lam1h * 2 * A)
-    got = lam1h * RT * L.astype(np.float64) + D.astype(np.float64) * c.astype(np.float64)
+    def fmaf(a, b, c):
+        # float32 inputs: the product is exact in float64, one rounding to float32
+        return f32(np.float64(a) * np.float64(b) + np.float64(c))
+
+    g = lam1h * RT
+    g_hi = f32(g)
+    g_lo = f32(g - float(g_hi))
+    p1 = g_hi * L
+    p2 = D * c
+    e = fmaf(g_hi, L, -p1)
+    e = fmaf(g_lo, L, e)
+    e = e + fmaf(D, c, -p2)
+    sm = p1 + p2
+    bp = sm - p1
+    e = e + ((p1 - (sm - bp)) + (p2 - bp))
+    got = (sm + e).astype(np.float64)
+    ref64 = f32(g * L.astype(np.float64) + D.astype(np.float64) * c.astype(np.float64))
+    # the double-float sum rounds to the FP64 sum's float32 value, within one ulp
+    assert np.max(np.abs(got - ref64) / np.maximum(np.abs(ref64), 1e-30)) <= 2.0 ** -23
     assert np.max(np.abs(got - exact)) <= 1e-6 * np.max(np.abs(exact))
 
 
@@ -76,7 +95,8 @@ def factors32(u):
 
 def collide_fp32(o, ft, F, rho_ref, beta):
     """Post-collision stored populations (f - w rho_ref) of one node, formed
-    in float32 as the FP32 path does (FP64 only for beta gamma)."""
+    in float32 as the FP32 path does (beta gamma rounded once from the
+    float32 ratio)."""
     D = o.D
     c = o.c[:, :3]
     w = o.w.astype(f32)
