@@ -735,6 +735,7 @@ extern "C" int tel_fields_noalloc(int lattice, int nx, int ny, int nz, const tel
 struct tel_batch {
     int ncases, precision;
     bool fast;
+    bool vec;                    // vector phase A: FP32, fast, every nx % 4 == 0
     int *nx, *ny;
     long long *off;              // element offset of each case's arrays in one buffer
     long long total;             // total nodes
@@ -807,7 +808,7 @@ static int batch_build(tel_batch *b, int tx, int ch)
     if (e != cudaSuccess) return bfail(b, TEL_ECUDA, "work list upload: %s", cudaGetErrorString(e));
     for (int c = 0; c < b->ncases; ++c) b->hP[c].chunk = ch;
     BCUDA(b, cudaMemcpy(b->dP, b->hP, sizeof(tel::DevParams) * (size_t)b->ncases, cudaMemcpyHostToDevice));
-    int nb = tel::batch_blocks_per_sm(b->precision, tx, b->fast);
+    int nb = tel::batch_blocks_per_sm(b->precision, tx, b->fast, b->vec);
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -845,6 +846,11 @@ extern "C" int tel_batch_create(int ncases, const int *nx, const int *ny, const 
     b->precision = prec;
     b->total = total;
     b->fast = !walls && 9LL * total < (1LL << 31);
+    // vector phase A: every case's row a whole number of aligned four-node
+    // vectors, so that each case's arrays (offsets sums of nx * ny) stay
+    // 16-byte aligned
+    b->vec = b->fast && prec == TEL_FP32_SHIFTED;
+    for (int c = 0; c < ncases; ++c) b->vec = b->vec && nx[c] % 4 == 0;
     b->nx = new (std::nothrow) int[ncases];
     b->ny = new (std::nothrow) int[ncases];
     b->off = new (std::nothrow) long long[ncases];
@@ -989,7 +995,7 @@ extern "C" int tel_batch_init(tel_batch *b, int c, const double *rho, const doub
 
 static int batch_launch(tel_batch *b, int k)
 {
-    BCUDA(b, tel::launch_d2q9_batch(b->precision, b->tx, b->fast, b->dP, b->dA[k], b->d_items, b->nitems, b->grid,
+    BCUDA(b, tel::launch_d2q9_batch(b->precision, b->tx, b->fast, b->vec, b->dP, b->dA[k], b->d_items, b->nitems, b->grid,
                                     b->stream));
     return TEL_OK;
 }

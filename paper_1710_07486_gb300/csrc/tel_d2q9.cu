@@ -10,55 +10,63 @@ cudaError_t launch_d2q9(int precision, int mode, const DevParams &P, const Launc
 }  // namespace tel
 
 namespace tel {
-template <int TX, typename ST, bool FAST>
+template <int TX, typename ST, bool FAST, bool VEC>
 static cudaError_t launch_batch_one(const DevParams *Ps, const LaunchArgs *As, const int4 *items, int nitems,
                                     int grid, cudaStream_t s)
 {
-    typedef Fused<2, TX, 1, ST, MODE_STEP, FAST> K;
+    typedef Fused<2, TX, 1, ST, MODE_STEP, FAST, VEC> K;
     static DeviceOnce once;
     cudaError_t e = once.run([] {
-        return cudaFuncSetAttribute(batch_kernel<TX, ST, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(batch_kernel<TX, ST, FAST, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)K::SMEM_BYTES);
     });
     if (e != cudaSuccess) return e;
-    batch_kernel<TX, ST, FAST><<<grid, TX, K::SMEM_BYTES, s>>>(Ps, As, items, nitems);
+    batch_kernel<TX, ST, FAST, VEC><<<grid, TX, K::SMEM_BYTES, s>>>(Ps, As, items, nitems);
     return cudaGetLastError();
 }
 
-template <int TX, typename ST, bool FAST>
+template <int TX, typename ST, bool FAST, bool VEC>
 static int blocks_one()
 {
-    typedef Fused<2, TX, 1, ST, MODE_STEP, FAST> K;
-    cudaFuncSetAttribute(batch_kernel<TX, ST, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM_BYTES);
+    typedef Fused<2, TX, 1, ST, MODE_STEP, FAST, VEC> K;
+    cudaFuncSetAttribute(batch_kernel<TX, ST, FAST, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)K::SMEM_BYTES);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<TX, ST, FAST>, TX, K::SMEM_BYTES) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<TX, ST, FAST, VEC>, TX, K::SMEM_BYTES) !=
+        cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_d2q9_batch(int precision, int tx, bool fast, const DevParams *Ps, const LaunchArgs *As,
-                              const int4 *items, int nitems, int grid, cudaStream_t s)
+cudaError_t launch_d2q9_batch(int precision, int tx, bool fast, bool vec, const DevParams *Ps,
+                              const LaunchArgs *As, const int4 *items, int nitems, int grid, cudaStream_t s)
 {
-#define TEL_BATCH_CASE(TXV, STT, FV) \
-    if (tx == TXV && fast == FV) return launch_batch_one<TXV, STT, FV>(Ps, As, items, nitems, grid, s);
+#define TEL_BATCH_CASE(TXV, STT, FV, VV) \
+    if (tx == TXV && fast == FV && vec == VV) return launch_batch_one<TXV, STT, FV, VV>(Ps, As, items, nitems, grid, s);
     if (precision == 0) {
-        TEL_BATCH_CASE(32, double, true) TEL_BATCH_CASE(32, double, false)
-        TEL_BATCH_CASE(64, double, true) TEL_BATCH_CASE(64, double, false)
+        TEL_BATCH_CASE(32, double, true, false) TEL_BATCH_CASE(32, double, false, false)
+        TEL_BATCH_CASE(64, double, true, false) TEL_BATCH_CASE(64, double, false, false)
     } else {
-        TEL_BATCH_CASE(32, float, true) TEL_BATCH_CASE(32, float, false)
-        TEL_BATCH_CASE(64, float, true) TEL_BATCH_CASE(64, float, false)
+        TEL_BATCH_CASE(32, float, true, true) TEL_BATCH_CASE(32, float, true, false)
+        TEL_BATCH_CASE(32, float, false, false)
+        TEL_BATCH_CASE(64, float, true, true) TEL_BATCH_CASE(64, float, true, false)
+        TEL_BATCH_CASE(64, float, false, false)
     }
 #undef TEL_BATCH_CASE
     return cudaErrorInvalidValue;
 }
 
-int batch_blocks_per_sm(int precision, int tx, bool fast)
+int batch_blocks_per_sm(int precision, int tx, bool fast, bool vec)
 {
     if (precision == 0) {
-        if (tx == 32) return fast ? blocks_one<32, double, true>() : blocks_one<32, double, false>();
-        return fast ? blocks_one<64, double, true>() : blocks_one<64, double, false>();
+        if (tx == 32) return fast ? blocks_one<32, double, true, false>() : blocks_one<32, double, false, false>();
+        return fast ? blocks_one<64, double, true, false>() : blocks_one<64, double, false, false>();
     }
-    if (tx == 32) return fast ? blocks_one<32, float, true>() : blocks_one<32, float, false>();
-    return fast ? blocks_one<64, float, true>() : blocks_one<64, float, false>();
+    if (tx == 32) {
+        if (fast) return vec ? blocks_one<32, float, true, true>() : blocks_one<32, float, true, false>();
+        return blocks_one<32, float, false, false>();
+    }
+    if (fast) return vec ? blocks_one<64, float, true, true>() : blocks_one<64, float, true, false>();
+    return blocks_one<64, float, false, false>();
 }
 }  // namespace tel

@@ -521,8 +521,18 @@ struct Fused {
     // (x0 - 4 .. x0 + TX + 3) in lanes 0-29; warps 0-3 sum f, warps 4-7 g,
     // over the TY + 4 rows of tile + ring 2
     static constexpr int NAV = 256;
-    static_assert(!VEC || (D == 3 && TX == 32 && TY == 8 && STEPPING && FAST &&
-                           StoreTraits<ST>::shifted), "vector phase A: D3Q27 32 x 8 FP32 periodic step");
+    // D2Q9: one row of NV2 four-node vectors (x0 - 4 .. x0 + TX + 3) per
+    // population set; with one warp, f in lanes 0 .. NV2-1 and g in lanes
+    // NV2 .. 2 NV2-1; with two warps, f in warp 0 and g in warp 1, lanes
+    // 0 .. NV2-1.  The warps' other lanes take chemical-potential items in
+    // the same round.
+    static constexpr int NV2 = TX / 4 + 2;
+    static constexpr int AV2 = (NT == 32) ? 2 * NV2 : NV2;  // vector lanes per warp
+    static constexpr int NB0 = (NT / 32) * (32 - AV2);      // chemical-potential items in round 0
+    static_assert(!VEC || (STEPPING && FAST && StoreTraits<ST>::shifted &&
+                           ((D == 3 && TX == 32 && TY == 8) ||
+                            (D == 2 && TY == 1 && (TX == 32 || TX == 64)))),
+                  "vector phase A: FP32 periodic step, D3Q27 32 x 8 or D2Q9 rows of 32 or 64");
 
     // shared memory layout (in CT units)
     // ring buffers over planes: RS slots of rho, phi (tile + ring 2), MS of
@@ -734,7 +744,7 @@ struct Fused {
             const int nA = doA ? (VEC ? NAV : NA) : 0;
             const int mm = map_coord(mA, PM, bM);
             auto item_a = [&](int w) {
-                if constexpr (VEC) {
+                if constexpr (VEC && D == 3) {
                     phase_a_vec(P, fs, gs, rp_s + slotR(mA) * NA, w, x0, y0, mm, shift);
                     return;
                 }
@@ -842,6 +852,29 @@ struct Fused {
                 __syncthreads();
                 if (doB)
                     for (int s = tid; s < NB; s += NT) item_b(s);
+            } else if constexpr (VEC) {
+                // D2Q9 vector phase A: round 0 runs the row's vectors in the
+                // first AV2 lanes of each warp and chemical-potential items in
+                // the others; the vectors' end elements are exchanged after
+                // the branches, with every lane of the warp present
+                const int lane = tid & 31, q = tid >> 5;
+                const bool a_lane = doA && lane < AV2;
+                const bool is_g = (NT == 32) ? lane >= NV2 : q == 1;
+                const int c = (NT == 32 && lane >= NV2) ? lane - NV2 : lane;
+                float2 h[3][2];
+                if (a_lane) {
+                    row_vec_sums(P, fs, gs, c, is_g, x0, mm, h);
+                } else {
+                    const int b = q * (32 - AV2) + (lane - AV2);
+                    if (doB && lane >= AV2 && b < NB) item_b(b);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) h[a][0] = h[a][1] = bc2(0.f);
+                }
+                const float hl = __shfl_up_sync(0xffffffffu, h[2][1].y, 1);
+                const float hr = __shfl_down_sync(0xffffffffu, h[0][0].x, 1);
+                if (a_lane) row_vec_store(rp_s + slotR(mA) * NA, c, is_g, h, hl, hr, shift);
+                if (doB)
+                    for (int b = NB0 + tid; b < NB; b += NT) item_b(b);
             } else {
                 const int nW = nA + (doB ? NB : 0);
                 for (int w = tid; w < nW; w += NT) {
@@ -919,6 +952,54 @@ struct Fused {
                 const int ox = 4 * c - 4 + e;
                 if (ox >= -2 && ox < TX + 2) dst[2 * idx2(ox, oy)] = is_g ? sum[e] : shift + sum[e];
             }
+        }
+    }
+
+    // D2Q9 phase A on four-node vectors along x (rows of the marching axis
+    // y): lane item c sums f or g over x0 - 4 + 4c .. x0 - 1 + 4c of row m,
+    // keeping the populations of each sign of c_ix apart (h[c_x + 1]), which
+    // row_vec_store shifts by one node with the neighbouring lanes' end
+    // elements.  Population i pulled into node x of row m is f_i(x - c_ix)
+    // of row m - c_iy.  nx % 4 == 0, so no vector straddles the periodic seam.
+    __device__ static void row_vec_sums(const DevParams &P, const ST *fs, const ST *gs, int c, bool is_g, int x0,
+                                        int m, float2 (&h)[3][2])
+    {
+        const int PX = P.nx, PM = P.ny;
+        int X = (x0 - 4 + 4 * c) % PX;
+        if (X < 0) X += PX;
+        int po[3];
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+            int mm = m - d;  // m is already in [0, PM)
+            if (mm < 0) mm += PM; else if (mm >= PM) mm -= PM;
+            po[d + 1] = mm * PX;
+        }
+        const ST *src = is_g ? gs : fs;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) h[a][0] = h[a][1] = bc2(0.f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned k = (unsigned)i * (unsigned)P.N + (unsigned)(po[L::cy(i) + 1] + X);
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(src + k));
+            const int a = L::cx(i) + 1;
+            h[a][0] = add2(h[a][0], make_float2(v.x, v.y));
+            h[a][1] = add2(h[a][1], make_float2(v.z, v.w));
+        }
+    }
+    // The four nodes' sums (c_x = +1 pulls from x - 1, c_x = -1 from x + 1;
+    // hl, hr: the previous lane's last and the next lane's first element),
+    // stored for the nodes of tile + ring 2.  The outermost node of the first
+    // and the last vector takes another item's value and is not stored.
+    __device__ static void row_vec_store(V2 *rp_plane, int c, bool is_g, const float2 (&h)[3][2], float hl, float hr,
+                                         CT shift)
+    {
+        const float sum[4] = {h[1][0].x + hl + h[0][0].y, h[1][0].y + h[2][0].x + h[0][1].x,
+                              h[1][1].x + h[2][0].y + h[0][1].y, h[1][1].y + h[2][1].x + hr};
+        float *dst = reinterpret_cast<float *>(rp_plane) + (is_g ? 1 : 0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int ox = 4 * c - 4 + e;
+            if (ox >= -2 && ox < TX + 2) dst[2 * idx2(ox, 0)] = is_g ? sum[e] : shift + sum[e];
         }
     }
 
@@ -1645,14 +1726,26 @@ struct Fused {
 #ifndef TEL_D2Q9_WARPS_PER_SM
 #define TEL_D2Q9_WARPS_PER_SM 4
 #endif
+// With the vector phase A the row's loads are in flight together and the
+// kernel asks for more registers (130 unbounded), so the request is set
+// separately: 18 warps per SM (96 registers, no spills) measured 10250 /
+// 18366 MLUPS on 512^2 / 2048^2 FP32, against 10595 / 15150 with 4 and
+// 9819 / 18096 with 24.
+#ifndef TEL_D2Q9_VEC_WARPS_PER_SM
+#define TEL_D2Q9_VEC_WARPS_PER_SM 18
+#endif
 template <typename ST> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<float> { static constexpr int value = TEL_MIN_BLOCKS_FP32; };
-// D2Q9 FP32: TEL_D2Q9_WARPS_PER_SM warps per SM requested
-template <int D, int NTH, typename ST> struct KernelMinBlocks { static constexpr int value = MinBlocks<ST>::value; };
-template <int NTH> struct KernelMinBlocks<2, NTH, float> { static constexpr int value = TEL_D2Q9_WARPS_PER_SM * 32 / NTH; };
+// D2Q9 FP32: TEL_D2Q9_(VEC_)WARPS_PER_SM warps per SM requested
+template <int D, int NTH, typename ST, bool VEC> struct KernelMinBlocks {
+    static constexpr int value = MinBlocks<ST>::value;
+};
+template <int NTH, bool VEC> struct KernelMinBlocks<2, NTH, float, VEC> {
+    static constexpr int value = (VEC ? TEL_D2Q9_VEC_WARPS_PER_SM : TEL_D2Q9_WARPS_PER_SM) * 32 / NTH;
+};
 
 template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false>
-__global__ void __launch_bounds__(TX * TY, (KernelMinBlocks<D, TX * TY, ST>::value))
+__global__ void __launch_bounds__(TX * TY, (KernelMinBlocks<D, TX * TY, ST, VEC>::value))
     fused_kernel(const DevParams P, const LaunchArgs A)
 {
     Fused<D, TX, TY, ST, MODE, FAST, VEC>::run(P, A);
@@ -1665,12 +1758,17 @@ __global__ void __launch_bounds__(TX * TY, (KernelMinBlocks<D, TX * TY, ST>::val
 // per SM (24 CTAs of width 32, 12 of width 64), which caps the registers at
 // 80-85 per thread without spills (measured with width 32 on the 256-case
 // workload: 15640 MLUPS, against 14168 with 2 CTAs requested (115 registers,
-// 17 CTAs resident) and 13553 with 32 (64 registers, small spills)).  FP64:
-// 2, its collision needs its registers.
+// 17 CTAs resident) and 13553 with 32 (64 registers, small spills)).  With
+// the vector phase A (80 registers, 16-24 bytes of spills): 18000 MLUPS at
+// 24 warps, 17690 at 20 and 17400 at 16.  FP64: 2, its collision needs its
+// registers.
+#ifndef TEL_BATCH_WARPS_PER_SM
+#define TEL_BATCH_WARPS_PER_SM 24
+#endif
 template <int TX, typename ST> struct BatchMinBlocks { static constexpr int value = 2; };
-template <int TX> struct BatchMinBlocks<TX, float> { static constexpr int value = 768 / TX; };
+template <int TX> struct BatchMinBlocks<TX, float> { static constexpr int value = TEL_BATCH_WARPS_PER_SM * 32 / TX; };
 
-template <int TX, typename ST, bool FAST>
+template <int TX, typename ST, bool FAST, bool VEC = false>
 __global__ void __launch_bounds__(TX, (BatchMinBlocks<TX, ST>::value))
     batch_kernel(const DevParams *Ps, const LaunchArgs *As, const int4 *items, int nitems)
 {
@@ -1688,15 +1786,16 @@ __global__ void __launch_bounds__(TX, (BatchMinBlocks<TX, ST>::value))
             for (int k = threadIdx.x; k < (int)(sizeof(LaunchArgs) / sizeof(int)); k += blockDim.x) da[k] = sa[k];
         }
         __syncthreads();
-        Fused<2, TX, 1, ST, MODE_STEP, FAST>::run_tile(Psh, Ash, it.y, 0, it.z);
+        Fused<2, TX, 1, ST, MODE_STEP, FAST, VEC>::run_tile(Psh, Ash, it.y, 0, it.z);
     }
 }
 
-// Batched launcher (tel_d2q9.cu): tx in {32, 64}; grid = persistent CTAs.
-cudaError_t launch_d2q9_batch(int precision, int tx, bool fast, const DevParams *Ps, const LaunchArgs *As,
-                              const int4 *items, int nitems, int grid, cudaStream_t s);
+// Batched launcher (tel_d2q9.cu): tx in {32, 64}; grid = persistent CTAs;
+// vec: vector phase A (FP32, fast, every case with nx % 4 == 0).
+cudaError_t launch_d2q9_batch(int precision, int tx, bool fast, bool vec, const DevParams *Ps,
+                              const LaunchArgs *As, const int4 *items, int nitems, int grid, cudaStream_t s);
 // Resident CTAs per SM of the batched kernel with shape tx.
-int batch_blocks_per_sm(int precision, int tx, bool fast);
+int batch_blocks_per_sm(int precision, int tx, bool fast, bool vec);
 
 // Tile shapes and launcher (defined per lattice in tel_d2q9.cu / tel_d3q27.cu).
 cudaError_t launch_d2q9(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s);

@@ -40,8 +40,9 @@ static cudaError_t launch_prec(int precision, int mode, const DevParams &P, cons
         return launch_one<D, TX, TY, double, MODE_FIELDS, FAST>(P, A, s);
     }
     if (mode == MODE_STEP || mode == MODE_STEP_EXACT || mode == MODE_STEP_G64) {
-        // aligned four-node vectors in phase A (D3Q27 32 x 8, periodic, nx % 4 == 0)
-        if constexpr (D == 3 && TX == 32 && TY == 8 && FAST)
+        // aligned four-node vectors in phase A (D3Q27 32 x 8 or D2Q9 rows of
+        // 32 or 64, periodic, nx % 4 == 0)
+        if constexpr (((D == 3 && TX == 32 && TY == 8) || (D == 2 && TY == 1 && (TX == 32 || TX == 64))) && FAST)
             if (P.nx % 4 == 0) {
                 if (mode == MODE_STEP_EXACT) return launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST, true>(P, A, s);
                 if (mode == MODE_STEP_G64) return launch_one<D, TX, TY, float, MODE_STEP_G64, FAST, true>(P, A, s);

@@ -18,6 +18,9 @@ from tests.cases import A, B, RGAS, asymmetric, base
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(48, 40), (100, 36), (64, 64), (33, 17), (130, 70), (16, 16)]
+# every row a whole number of four-node vectors: the FP32 batch reads phase A
+# as aligned vectors (one odd row, as in SHAPES, takes the scalar path)
+SHAPES_VEC = [(48, 40), (100, 36), (64, 64), (36, 17), (132, 70), (16, 16)]
 
 
 def case_params(k, precision, walls=False):
@@ -39,11 +42,11 @@ def case_fields(k, shape, p):
     return inputs.perturb(100 + k, rho, phi, u, 1e-3, 1e-3, 1e-3)
 
 
-def run_pair(precision, steps, walls=False, tune=False):
-    ps = [case_params(k, precision, walls) for k in range(len(SHAPES))]
-    b = tel.Batch(SHAPES, ps)
+def run_pair(precision, steps, walls=False, tune=False, shapes=SHAPES):
+    ps = [case_params(k, precision, walls) for k in range(len(shapes))]
+    b = tel.Batch(shapes, ps)
     singles = []
-    for k, (shape, p) in enumerate(zip(SHAPES, ps)):
+    for k, (shape, p) in enumerate(zip(shapes, ps)):
         rho, phi, u = case_fields(k, shape, p)
         b.init(k, rho, phi, u)
         s = tel.Lattice(tel.D2Q9, shape[0], shape[1], 1, p)
@@ -104,6 +107,16 @@ def test_batch_after_tuning_matches_single_lattices():
     assert info["tile_x"] in (32, 64) and info["chunk"] in (8, 16, 32, 64)
     assert info["ncases"] == len(SHAPES) and info["nodes"] == sum(x * y for x, y in SHAPES)
     assert 0 < info["ctas"] <= info["items"]
+    for k, s in enumerate(singles):
+        got, ref = b.fields(k), s.fields()
+        assert close_fp32(got, ref), (k, errs(got, ref))
+
+
+def test_batch_vector_phase_a_matches_single_lattices():
+    """FP32 batch whose rows are all whole four-node vectors: the tuner runs
+    every tile width and chunk on the vector path; each case still matches
+    its single lattice."""
+    b, singles = run_pair(tel.FP32_SHIFTED, [4, 3], tune=True, shapes=SHAPES_VEC)
     for k, s in enumerate(singles):
         got, ref = b.fields(k), s.fields()
         assert close_fp32(got, ref), (k, errs(got, ref))

@@ -145,6 +145,26 @@ def test_one_step_fp32_state_parity_d3q27(orc, T10, shape):
     assert max(ef, eg) < 2e-5, (ef, eg)
 
 
+@pytest.mark.parametrize("shape", [(36, 21), (132, 17), (64, 40), (37, 19), (38, 9)])
+def test_one_step_fp32_state_parity_d2q9(orc, T10, shape):
+    """As the D3Q27 case: nx % 4 == 0 reads phase A as aligned four-node
+    vectors along rows of 64 (36: one partial tile with the periodic seam
+    inside it; 132: two whole tiles and a partial one), nx % 4 != 0 takes the
+    scalar path.  Same bar."""
+    p = asymmetric(T10, force_form=1)
+    g, o, rho, phi, u = setup_pair(orc, 0, shape, p, precision=tel.FP32_SHIFTED)
+    g.init(rho, phi, u)
+    g.step(2)
+    f0, g0 = g.get_state()
+    g.step(1)
+    f1, g1 = g.get_state()
+    o1 = orc.Oracle(0, shape[0], shape[1], 1, dict(p, rho_ref=0.0))
+    assert o1.step(f0, g0, 1) == 0
+    ef = np.max(np.abs(f0 - f1) / np.max(np.abs(f0), axis=0))
+    eg = np.max(np.abs(g0 - g1)) / p["chi"]
+    assert max(ef, eg) < 2e-5, (ef, eg)
+
+
 def test_step_batches_and_checkpoint_are_bitwise(orc, T10):
     p = base(T10)
     g, o, rho, phi, u = setup_pair(orc, 0, (40, 24), p)
