@@ -33,7 +33,7 @@ class Params(C.Structure):
         "a", "b", "R", "T", "lambda1", "lambda2", "lambda3",
         "kappa1", "kappa2", "kappa3", "chi", "nu", "Gamma", "tau_g")] + [
         ("force_form", C.c_int), ("eos", C.c_int), ("omega", C.c_double), ("gamma_mode", C.c_int),
-        ("solid", C.c_void_p)]
+        ("solid", C.c_void_p), ("wet_rho", C.c_double), ("wet_phi", C.c_double)]
 
 
 CS, VDW, PR = 0, 1, 2  # equations of state
@@ -131,6 +131,8 @@ def lib(openmp: bool = False):
             fn.restype = None
         L.orc_gradient.argtypes = [C.c_void_p, dp, dp]
         L.orc_gradient.restype = None
+        L.orc_laplacian_wet.argtypes = [C.c_void_p, dp, C.c_double, dp]
+        L.orc_laplacian_wet.restype = None
         L.orc_chem_pot.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.orc_chem_pot.restype = None
         L.orc_force.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
@@ -238,7 +240,7 @@ class Oracle:
         self.lattice = lattice
         self.nx, self.ny, self.nz = nx, ny, nz
         self.params = dict(params)
-        ints = ("force_form", "eos", "omega", "gamma_mode", "solid")
+        ints = ("force_form", "eos", "omega", "gamma_mode", "solid", "wet_rho", "wet_phi")
         vals = {k: float(params[k]) for k, _ in Params._fields_ if k not in ints}
         solid = params.get("solid")
         self.solid = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).ravel()
@@ -247,7 +249,8 @@ class Oracle:
         p = Params(force_form=int(params.get("force_form", 1)), eos=int(params.get("eos", CS)),
                    omega=float(params.get("omega", 0.0)),
                    gamma_mode=int(params.get("gamma_mode", GAMMA_CLOSED)),
-                   solid=None if self.solid is None else self.solid.ctypes.data, **vals)
+                   solid=None if self.solid is None else self.solid.ctypes.data,
+                   wet_rho=float(params.get("wet_rho", 0.0)), wet_phi=float(params.get("wet_phi", 0.0)), **vals)
         bca = np.asarray(bc, dtype=np.int32)
         self._h = self._L.orc_create(lattice, nx, ny, nz, C.byref(p), bca)
         if not self._h:
@@ -324,9 +327,14 @@ class Oracle:
         self._L.orc_unstream(self._h, _f64(pre, self.Q * self.N), post)
         return post
 
-    def laplacian(self, psi):
+    def laplacian(self, psi, wet=None):
+        """Isotropic Laplacian; with wet, the ghost rule of a density-like
+        field with that wetting gradient (orc_laplacian_wet)."""
         out = np.zeros(self.N)
-        self._L.orc_laplacian(self._h, _f64(psi, self.N), out)
+        if wet is None:
+            self._L.orc_laplacian(self._h, _f64(psi, self.N), out)
+        else:
+            self._L.orc_laplacian_wet(self._h, _f64(psi, self.N), float(wet), out)
         return out
 
     def gradient(self, psi):

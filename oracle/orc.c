@@ -519,15 +519,30 @@ static long stencil_nb_vec(const orc_ctx *o, int x, int y, int z, const int *c, 
     return m;  /* a solid node with no fluid neighbour: its values are unused */
 }
 
-static long stencil_nb(const orc_ctx *o, int x, int y, int z, const int *c)
+/* Value of a scalar field seen by a stencil at (x,y,z) along c.  Reading
+   (wetting; not in the paper, which only says that wetting boundary
+   conditions fit the model): the ghost across a wall or a solid surface is
+   the mirrored fluid value plus wet for each axis the read was mirrored on,
+   i.e. the field is continued linearly with a prescribed change wet per
+   lattice spacing into the wall -- a gradient (Cahn-type) wetting condition.
+   wet = 0 is the neutral mirror.  It enters where the free energy is
+   differentiated: the Laplacians of density and composition in the chemical
+   potentials.  The gradients keep the plain mirror: the chemical potentials'
+   (no diffusive flux into the wall), and the density gradient of the force's
+   ideal-pressure term, which stands for the pressure the populations carry,
+   and at a bounce-back wall that pressure has no ghost. */
+static double stencil_val(const orc_ctx *o, const double *psi, double wet, int x, int y, int z, const int *c)
 {
     int sg[3];
-    return stencil_nb_vec(o, x, y, z, c, sg);
+    long m = stencil_nb_vec(o, x, y, z, c, sg);
+    if (wet == 0.0) return psi[m];
+    int k = (sg[0] < 0) + (sg[1] < 0) + (sg[2] < 0);
+    return psi[m] + wet * k;
 }
 
 /* Reading (stencils; not in the paper): the lattice-weight isotropic
    Laplacian  lap psi = (2/c_s^2) sum_i w_i (psi(x+c_i) - psi(x)). */
-void orc_laplacian(const orc_ctx *o, const double *psi, double *lap)
+void orc_laplacian_wet(const orc_ctx *o, const double *psi, double wet, double *lap)
 {
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < o->nz; z++)
@@ -536,14 +551,19 @@ void orc_laplacian(const orc_ctx *o, const double *psi, double *lap)
                 long n = x + (long)o->nx * (y + (long)o->ny * z);
                 double s = 0.0;
                 for (int i = 0; i < o->Q; i++)
-                    s += o->w[i] * (psi[stencil_nb(o, x, y, z, o->c[i])] - psi[n]);
+                    s += o->w[i] * (stencil_val(o, psi, wet, x, y, z, o->c[i]) - psi[n]);
                 lap[n] = 6.0 * s;
             }
 }
 
+void orc_laplacian(const orc_ctx *o, const double *psi, double *lap)
+{
+    orc_laplacian_wet(o, psi, 0.0, lap);
+}
+
 /* Reading (stencils): the isotropic gradient
    grad psi = (1/c_s^2) sum_i w_i c_i psi(x+c_i).  grad is [3][N]. */
-void orc_gradient(const orc_ctx *o, const double *psi, double *grad)
+static void gradient_wet(const orc_ctx *o, const double *psi, double wet, double *grad)
 {
     long N = o->N;
 #pragma omp parallel for collapse(2) schedule(static)
@@ -553,11 +573,16 @@ void orc_gradient(const orc_ctx *o, const double *psi, double *grad)
                 long n = x + (long)o->nx * (y + (long)o->ny * z);
                 double s[3] = {0.0, 0.0, 0.0};
                 for (int i = 0; i < o->Q; i++) {
-                    double v = psi[stencil_nb(o, x, y, z, o->c[i])];
+                    double v = stencil_val(o, psi, wet, x, y, z, o->c[i]);
                     for (int a = 0; a < 3; a++) s[a] += o->w[i] * o->c[i][a] * v;
                 }
                 for (int a = 0; a < 3; a++) grad[a * N + n] = 3.0 * s[a];
             }
+}
+
+void orc_gradient(const orc_ctx *o, const double *psi, double *grad)
+{
+    gradient_wet(o, psi, 0.0, grad);
 }
 
 /* mu_rho = dF/drho and mu_phi = dF/dphi of Eq. 1 written with Eq. 5:
@@ -576,8 +601,8 @@ void orc_chem_pot(const orc_ctx *o, const double *rho, const double *phi,
     long N = o->N;
     double *lr = (double *)malloc(sizeof(double) * N);
     double *lp = (double *)malloc(sizeof(double) * N);
-    orc_laplacian(o, rho, lr);
-    orc_laplacian(o, phi, lp);
+    orc_laplacian_wet(o, rho, o->p.wet_rho, lr);
+    orc_laplacian_wet(o, phi, o->p.wet_phi, lp);
     double Dl = o->rho_g - o->rho_l, chi = p->chi;
     orc_eos e = {p->eos, p->a, p->b, p->R, p->T, p->omega};
 #pragma omp parallel for schedule(static)

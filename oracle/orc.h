@@ -44,6 +44,8 @@ typedef struct {
     int gamma_mode;                    /* ORC_GAMMA_CLOSED or ORC_GAMMA_EXACT    */
     const unsigned char *solid;        /* per-node solid mask [N] (nonzero =
                                           solid), copied at create; NULL: none */
+    double wet_rho, wet_phi;           /* wetting gradients at walls and solid
+                                          nodes (0: neutral); see orc_laplacian_wet */
 } orc_params;
 
 /* Stabiliser of the KBC collision: the closed form (the root of the entropy
@@ -135,6 +137,11 @@ void orc_force(const orc_ctx *o, const double *rho, const double *phi,
 /* isotropic gradient [3*N] and Laplacian [N] of a scalar field */
 void orc_gradient(const orc_ctx *o, const double *psi, double *grad);
 void orc_laplacian(const orc_ctx *o, const double *psi, double *lap);
+/* The Laplacian of a density-like field with a wetting gradient: a ghost
+   read across a wall or a solid surface takes the mirrored fluid value plus
+   wet times the number of axes mirrored (the chemical potentials' Laplacians
+   of density and composition use it with wet_rho and wet_phi). */
+void orc_laplacian_wet(const orc_ctx *o, const double *psi, double wet, double *lap);
 
 /* rho[N], phi[N], u[D*N] (SoA) -> post-collision state f[Q*N], g[Q*N] */
 int orc_init(const orc_ctx *o, const double *rho, const double *phi,
