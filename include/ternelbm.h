@@ -95,6 +95,8 @@ typedef struct {
                                          TEL_GAMMA_CLOSED_F64SUM */
     const unsigned char *solid;       /* optional host solid mask [nz][ny][nx] (nonzero = solid),
                                          copied by tel_create; NULL = no solid nodes (see below) */
+    double wet_rho, wet_phi;          /* wetting gradients at walls and solid nodes (see below);
+                                         0, 0 = neutral wetting */
 } tel_params;
 
 /* Solid nodes (tel_params.solid; not in the paper, which names wetting
@@ -108,6 +110,20 @@ typedef struct {
  * fields of a solid node are zero; tel_init ignores its input fields there.
  * A lattice with solid nodes takes the kernel's walled path (64-bit indices,
  * per-pull tests).  Not available for batches or tel_fields_noalloc. */
+
+/* Wetting (tel_params.wet_rho, wet_phi; not in the paper, which says only
+ * that wetting boundary conditions fit the model): a gradient (Cahn-type)
+ * condition.  In the Laplacians of density and composition in the chemical
+ * potentials (Eq. 5), a ghost read across a bounce-back wall or a solid
+ * surface is the mirrored fluid value plus wet_rho (wet_phi) for each axis
+ * the read was mirrored on: the field continues linearly with that change
+ * per lattice spacing into the wall.  wet_rho > 0 draws density to the wall
+ * (the liquid wets it), wet_phi > 0 favours liquid 1 (phi > 0) there.  The
+ * gradients keep the plain mirror: the chemical potentials' (no diffusive
+ * flux into the wall) and the density gradient of the force's ideal-pressure
+ * term, which stands for the pressure the bounced-back populations carry.
+ * Both 0 gives the neutral rule above; both must be finite; they act only
+ * where walls or solid nodes exist. */
 
 /* Stabiliser gamma of the KBC collision f' = f - beta (2 Delta s + gamma
  * Delta h) (the entropic scheme named after Eq. 8):

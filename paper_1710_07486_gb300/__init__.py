@@ -45,7 +45,8 @@ class Params(C.Structure):
         "a", "b", "R", "T", "lambda1", "lambda2", "lambda3", "kappa1", "kappa2",
         "kappa3", "chi", "nu", "Gamma", "tau_g", "rho_ref")] + [
         ("precision", C.c_int), ("force_form", C.c_int), ("bc", C.c_int * 3), ("eos", C.c_int),
-        ("omega", C.c_double), ("gamma_mode", C.c_int), ("solid", C.c_void_p)]
+        ("omega", C.c_double), ("gamma_mode", C.c_int), ("solid", C.c_void_p),
+        ("wet_rho", C.c_double), ("wet_phi", C.c_double)]
 
 
 _lib = None
@@ -154,6 +155,8 @@ def _params_struct(p):
     s.eos = int(p.get("eos", EOS_CS))
     s.omega = float(p.get("omega", 0.0))
     s.gamma_mode = int(p.get("gamma_mode", GAMMA_CLOSED))
+    s.wet_rho = float(p.get("wet_rho", 0.0))
+    s.wet_phi = float(p.get("wet_phi", 0.0))
     solid = p.get("solid")
     if solid is not None:
         # kept alive on the struct until the call that copies it returns

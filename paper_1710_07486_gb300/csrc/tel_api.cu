@@ -258,6 +258,7 @@ static void fill_coef(const tel::DevParams &d, tel::Coef<T> &k)
     k.rho_switch = (T)d.rho_switch; k.rho_ref = (T)d.rho_ref;
     k.beta = (T)d.beta; k.Gamma3 = (T)(3.0 * d.Gamma); k.inv_tau_g = (T)d.inv_tau_g;
     k.aal = (T)d.aal; k.prA = (T)d.prA; k.c1 = (T)d.c1; k.c2 = (T)d.c2;
+    k.wr = (T)d.wet_rho; k.wp = (T)d.wet_phi;
 }
 
 static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
@@ -278,6 +279,8 @@ static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
     if (p->force_form != TEL_FORCE_POTENTIAL && p->force_form != TEL_FORCE_LATTICE) return fail(nullptr, TEL_EINVAL, "bad force_form");
     if (p->gamma_mode != TEL_GAMMA_CLOSED && p->gamma_mode != TEL_GAMMA_EXACT && p->gamma_mode != TEL_GAMMA_CLOSED_F64SUM)
         return fail(nullptr, TEL_EINVAL, "bad gamma_mode");
+    if (!std::isfinite(p->wet_rho) || !std::isfinite(p->wet_phi))
+        return fail(nullptr, TEL_EINVAL, "wetting gradients must be finite");
     for (int a = 0; a < 3; ++a)
         if (p->bc[a] != TEL_PERIODIC && p->bc[a] != TEL_BOUNCEBACK) return fail(nullptr, TEL_EINVAL, "bad bc[%d]", a);
     if (((long long)nx * ny * nz) >= (1LL << 31)) return fail(nullptr, TEL_EINVAL, "lattice too large (N must be < 2^31)");
@@ -354,6 +357,8 @@ static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params
     d.inv_tau_g = 1.0 / p.tau_g;
     d.rho_ref = p.precision == TEL_FP32_SHIFTED ? (p.rho_ref > 0 ? p.rho_ref : co[0]) : 0.0;
     d.gamma_mode = p.gamma_mode;
+    d.wet_rho = p.wet_rho;
+    d.wet_phi = p.wet_phi;
     d.solid = nullptr;  // the device copy is set by tel_create
     fill_coef(d, d.cf);
     fill_coef(d, d.cd);

@@ -57,6 +57,7 @@ struct Coef {
     T rho_switch, rho_ref;
     T beta, Gamma3, inv_tau_g;         // Gamma3 = 3 Gamma
     T aal, prA, c1, c2;                // PR: a alpha(T), a alpha/(2 sqrt2 b), (1 +- sqrt2) b
+    T wr, wp;                          // wetting gradients of rho and phi at walls and solid nodes
 };
 
 struct DevParams {
@@ -94,6 +95,7 @@ struct DevParams {
     double Gamma, inv_tau_g;
     double rho_ref;                   // FP32 shift (0 in FP64)
     int gamma_mode;                   // 0 closed-form stabiliser, 1 exact root
+    double wet_rho, wet_phi;          // wetting gradients (0: neutral walls)
     const unsigned char *solid;       // per-node solid mask (device), or NULL
     unsigned *err;                    // device error word
     unsigned long long *gfall;        // count of exact-stabiliser fallbacks
@@ -603,6 +605,44 @@ struct Fused {
         cX = cY = cM = 0;
     }
 
+    // Bounce-back walls seen by a stencil centred at the lattice position
+    // (gx, gy, gm) (gy unused in D2Q9; positions outside the lattice are
+    // ghost slots whose values are not used): walls_crossed counts the axes
+    // along which the read c leaves the lattice through a wall, wall_zero
+    // sets those components of c to zero (the read goes to the mirrored
+    // node, the centre's own coordinate on that axis), walls_adjacent counts
+    // the wall sides next to the position.
+    __device__ static __forceinline__ int walls_crossed(const DevParams &P, int gx, int gy, int gm, int cX, int cY,
+                                                        int cM)
+    {
+        const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
+        const int bX = P.bc[0], bY = (D == 3 ? P.bc[1] : 0), bM = (D == 3 ? P.bc[2] : P.bc[1]);
+        int k = 0;
+        if (bX && (gx + cX < 0 || gx + cX >= PX)) ++k;
+        if (D == 3 && bY && (gy + cY < 0 || gy + cY >= PY)) ++k;
+        if (bM && (gm + cM < 0 || gm + cM >= PM)) ++k;
+        return k;
+    }
+    __device__ static __forceinline__ void wall_zero(const DevParams &P, int gx, int gy, int gm, int &cX, int &cY,
+                                                     int &cM)
+    {
+        const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
+        const int bX = P.bc[0], bY = (D == 3 ? P.bc[1] : 0), bM = (D == 3 ? P.bc[2] : P.bc[1]);
+        if (bX && (gx + cX < 0 || gx + cX >= PX)) cX = 0;
+        if (D == 3 && bY && (gy + cY < 0 || gy + cY >= PY)) cY = 0;
+        if (bM && (gm + cM < 0 || gm + cM >= PM)) cM = 0;
+    }
+    __device__ static __forceinline__ int walls_adjacent(const DevParams &P, int gx, int gy, int gm)
+    {
+        const int PX = P.nx, PY = (D == 3 ? P.ny : 1), PM = (D == 3 ? P.nz : P.ny);
+        const int bX = P.bc[0], bY = (D == 3 ? P.bc[1] : 0), bM = (D == 3 ? P.bc[2] : P.bc[1]);
+        int k = 0;
+        if (bX) k += (gx == 0) + (gx == PX - 1);
+        if (D == 3 && bY) k += (gy == 0) + (gy == PY - 1);
+        if (bM) k += (gm == 0) + (gm == PM - 1);
+        return k;
+    }
+
     // Sources of the populations pulled into node (x, y, m): per axis the
     // source coordinate x - c for c = -1, 0, 1 (periodic wrap) as an offset,
     // and a bit per (axis, c) when that source lies beyond a bounce-back wall
@@ -793,6 +833,10 @@ struct Fused {
                 const V2 ncp = V::pair(-r0, -p0);
                 V2 lap = V::pair((CT)0, (CT)0);
                 CT gx = 0, gy = 0, gz = 0;
+                // wetting: sum of w_i times the axes mirrored by read i (the
+                // ghost of rho, phi in the Laplacians is the mirrored value
+                // plus wet_rho, wet_phi per mirrored axis)
+                CT wet_w = 0;
                 bool masked = false;
                 if constexpr (!FAST) masked = P.solid != nullptr;
                 if (masked) {
@@ -812,6 +856,7 @@ struct Fused {
                         resolve(sol, ox, oy, mB, cX, cY, cM, fl);
                         const V2 v = rp_s[slotR(mB + cM) * NA + idx2(ox + cX, oy + cY)];
                         const CT wi = (CT)L::w(i);
+                        wet_w += wi * (CT)(__popc(fl) + walls_crossed(P, x0 + ox, y0 + oy, mB, cX, cY, cM));
                         lap = V::fma(V::pair(wi, wi), V::add(v, ncp), lap);
                         if (L::cx(i)) gx += wi * (CT)L::cx(i) * v.x;
                         if (L::cy(i)) gy += wi * (CT)L::cy(i) * v.x;
@@ -833,9 +878,12 @@ struct Fused {
                         if (L::cy(i)) gy += wi * (CT)L::cy(i) * d;
                         if (D == 3 && L::cz(i)) gz += wi * (CT)L::cz(i) * d;
                     }
+                    // at the walls the ghost slots hold the mirrored values;
+                    // the reads across one wall side carry weight 1/6 in all
+                    if constexpr (!FAST) wet_w = (CT)walls_adjacent(P, x0 + ox, y0 + oy, mB) * (CT)(1.0 / 6.0);
                 }
-                const CT lr = (CT)6 * lap.x;
-                const CT lp = (CT)6 * lap.y;
+                const CT lr = (CT)6 * (coef<CT>(P).wr * wet_w + lap.x);
+                const CT lp = (CT)6 * (coef<CT>(P).wp * wet_w + lap.y);
                 CT mr, mp;
                 mu_wells<CT>(P, r0, p0, mr, mp);
                 if (StoreTraits<ST>::shifted && r0 < coef<CT>(P).rho_switch)  // FP64 gas side
@@ -1070,8 +1118,11 @@ struct Fused {
                 int cX = L::pX(i), cY = L::pY(i), cM = L::pM(i);
                 unsigned fl;
                 resolve(sol, ox, oy, m, cX, cY, cM, fl);
-                const V2 vm = mu_s[slotM(m + cM) * NB + idx1(ox + cX, oy + cY)];
                 const V2 vr = rp_s[slotR(m + cM) * NA + idx2(ox + cX, oy + cY)];
+                // the chemical potentials' ghost across a wall is the mirrored
+                // node's value
+                wall_zero(P, x, y, m, cX, cY, cM);
+                const V2 vm = mu_s[slotM(m + cM) * NB + idx1(ox + cX, oy + cY)];
                 const CT wi = (CT)L::w(i);
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
@@ -1087,8 +1138,16 @@ struct Fused {
 #pragma unroll
             for (int i = 0; i < L::REST; ++i) {
                 const int io = Q - 1 - i;
-                const V2 vm = V::sub(mu_s[slotM(m + L::pM(i)) * NB + idx1(ox + L::pX(i), oy + L::pY(i))],
-                                     mu_s[slotM(m + L::pM(io)) * NB + idx1(ox + L::pX(io), oy + L::pY(io))]);
+                int aX = L::pX(i), aY = L::pY(i), aM = L::pM(i);
+                int bX_ = L::pX(io), bY_ = L::pY(io), bM_ = L::pM(io);
+                if constexpr (!FAST) {
+                    // walls: the chemical potentials' ghost is the mirrored
+                    // node's value
+                    wall_zero(P, x, y, m, aX, aY, aM);
+                    wall_zero(P, x, y, m, bX_, bY_, bM_);
+                }
+                const V2 vm = V::sub(mu_s[slotM(m + aM) * NB + idx1(ox + aX, oy + aY)],
+                                     mu_s[slotM(m + bM_) * NB + idx1(ox + bX_, oy + bY_)]);
                 const CT wi = (CT)L::w(i);
 #pragma unroll
                 for (int a = 0; a < D; ++a) {

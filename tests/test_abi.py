@@ -68,6 +68,8 @@ def test_invalid_parameters_rejected_before_any_device_work():
         (0, 8, 8, 1, dict(good, precision=7)),
         (0, 8, 8, 1, dict(good, force_form=3)),
         (0, 8, 8, 1, dict(good, bc=(0, 2, 0))),
+        (0, 8, 8, 1, dict(good, bc=(0, 1, 0), wet_rho=float("nan"))),
+        (0, 8, 8, 1, dict(good, bc=(0, 1, 0), wet_phi=float("inf"))),
     ]
     for lat, nx, ny, nz, p in bad_cases:
         with pytest.raises(tel.TelError) as ei:
