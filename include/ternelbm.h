@@ -97,6 +97,8 @@ typedef struct {
                                          copied by tel_create; NULL = no solid nodes (see below) */
     double wet_rho, wet_phi;          /* wetting gradients at walls and solid nodes (see below);
                                          0, 0 = neutral wetting */
+    int moments;                      /* tel_moments: TEL_MOMENTS_CARRIED (default 0) or
+                                         TEL_MOMENTS_PULLED (see below) */
 } tel_params;
 
 /* Solid nodes (tel_params.solid; not in the paper, which names wetting
@@ -159,6 +161,28 @@ typedef enum { TEL_GAMMA_CLOSED = 0, TEL_GAMMA_EXACT = 1, TEL_GAMMA_CLOSED_F64SU
  * The common tangent (C, Psi_0) is constructed the same way for all three. */
 typedef enum { TEL_EOS_CS = 0, TEL_EOS_VDW = 1, TEL_EOS_PR = 2 } tel_eos;
 
+/* How a step obtains the moments rho, phi (Eqs. 6-8: the zeroth moments of
+ * the pulled f and g) that its stencils read on the tile + ring 2.  The
+ * update computed is the same either way; the two differ only in the
+ * rounding of those stencil inputs.
+ *   TEL_MOMENTS_CARRIED: where it applies -- D3Q27, TEL_FP32_SHIFTED, every
+ *     axis periodic, no solid node, nx % 32 == 0, ny % 8 == 0 -- each step
+ *     also adds every post-collision population into the moments of the node
+ *     that the next step's pull brings it to (FP32 atomic additions into a
+ *     device array, so their summation order, and the last bit of those
+ *     moments, varies from run to run), and the next step reads them instead
+ *     of pulling the 54 populations of every ring node again.  The node's
+ *     own collision still takes its mass from its pulled populations, so
+ *     mass stays conserved to rounding.  tel_create then allocates three
+ *     moment arrays (24 bytes per node); after tel_init, tel_init_device or
+ *     tel_set_state the next tel_step first sums them from the state (one
+ *     extra launch).  tel_step keeps a rotation over those arrays on the
+ *     host, so a graph captured from tel_step calls repeats correctly only
+ *     for a multiple of 6 steps.  Elsewhere this mode pulls (as below).
+ *   TEL_MOMENTS_PULLED: every step pulls the populations of the tile and its
+ *     ring to form their moments (deterministic). */
+typedef enum { TEL_MOMENTS_CARRIED = 0, TEL_MOMENTS_PULLED = 1 } tel_moments;
+
 typedef struct tel_ctx tel_ctx;
 
 /* Create a lattice of nx*ny*nz nodes on the current CUDA device.
@@ -196,8 +220,9 @@ int tel_init_device(tel_ctx *ctx, const double *rho, const double *phi, const do
 /* Advance nsteps time steps: per node pull-stream f and g, moments,
  * chemical potentials (Eqs. 1-5) on the isotropic stencils, force,
  * KBC collision with per-node stabiliser and exact-difference forcing for f,
- * BGK for g.  One fused kernel launch per step.  Asynchronous.
- * TEL_ESTATE before initialisation. */
+ * BGK for g.  One fused kernel launch per step (plus, with carried moments,
+ * one launch that sums them after a new state; see tel_moments).
+ * Asynchronous.  TEL_ESTATE before initialisation. */
 int tel_step(tel_ctx *ctx, int nsteps);
 
 /* Wait for the context's stream and report the device's instability flag

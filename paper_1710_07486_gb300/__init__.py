@@ -25,6 +25,7 @@ PERIODIC, BOUNCEBACK = 0, 1
 FORCE_POTENTIAL, FORCE_LATTICE = 0, 1
 GAMMA_CLOSED, GAMMA_EXACT, GAMMA_CLOSED_F64SUM = 0, 1, 2
 EOS_CS, EOS_VDW, EOS_PR = 0, 1, 2
+MOMENTS_CARRIED, MOMENTS_PULLED = 0, 1
 
 TEL_OK, TEL_EINVAL, TEL_ENOMEM, TEL_ECUDA, TEL_EUNSTABLE, TEL_ESTATE = 0, -1, -2, -3, -4, -5
 _NAMES = {-1: "TEL_EINVAL", -2: "TEL_ENOMEM", -3: "TEL_ECUDA", -4: "TEL_EUNSTABLE", -5: "TEL_ESTATE"}
@@ -46,7 +47,7 @@ class Params(C.Structure):
         "kappa3", "chi", "nu", "Gamma", "tau_g", "rho_ref")] + [
         ("precision", C.c_int), ("force_form", C.c_int), ("bc", C.c_int * 3), ("eos", C.c_int),
         ("omega", C.c_double), ("gamma_mode", C.c_int), ("solid", C.c_void_p),
-        ("wet_rho", C.c_double), ("wet_phi", C.c_double)]
+        ("wet_rho", C.c_double), ("wet_phi", C.c_double), ("moments", C.c_int)]
 
 
 _lib = None
@@ -157,6 +158,7 @@ def _params_struct(p):
     s.gamma_mode = int(p.get("gamma_mode", GAMMA_CLOSED))
     s.wet_rho = float(p.get("wet_rho", 0.0))
     s.wet_phi = float(p.get("wet_phi", 0.0))
+    s.moments = int(p.get("moments", MOMENTS_CARRIED))
     solid = p.get("solid")
     if solid is not None:
         # kept alive on the struct until the call that copies it returns

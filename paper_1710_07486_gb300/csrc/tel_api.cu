@@ -27,6 +27,10 @@ struct tel_ctx {
     unsigned char *d_solid;       // device copy of the solid mask, or NULL
     double *scratch;  // FP64 fields / state staging, lazily allocated
     size_t scratch_elems;
+    // carried moments (tel_moments): three arrays of 2N floats; mom[mom_r]
+    // holds the moments of the current state when mom_valid
+    float *mom[3];
+    int mom_r, mom_valid;
     cudaStream_t own_stream, stream;
     int initialized;
     char msg[512];
@@ -279,6 +283,8 @@ static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
     if (p->force_form != TEL_FORCE_POTENTIAL && p->force_form != TEL_FORCE_LATTICE) return fail(nullptr, TEL_EINVAL, "bad force_form");
     if (p->gamma_mode != TEL_GAMMA_CLOSED && p->gamma_mode != TEL_GAMMA_EXACT && p->gamma_mode != TEL_GAMMA_CLOSED_F64SUM)
         return fail(nullptr, TEL_EINVAL, "bad gamma_mode");
+    if (p->moments != TEL_MOMENTS_CARRIED && p->moments != TEL_MOMENTS_PULLED)
+        return fail(nullptr, TEL_EINVAL, "bad moments mode");
     if (!std::isfinite(p->wet_rho) || !std::isfinite(p->wet_phi))
         return fail(nullptr, TEL_EINVAL, "wetting gradients must be finite");
     for (int a = 0; a < 3; ++a)
@@ -409,6 +415,12 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
         }
         delete[] h;
     }
+    // carried moments: D3Q27 FP32, periodic, no solid node, full 32 x 8
+    // tiles, 32-bit population indices (the step kernel's vector path)
+    const bool carried = p.moments == TEL_MOMENTS_CARRIED && lattice == TEL_D3Q27 && p.precision == TEL_FP32_SHIFTED &&
+                         !p.bc[0] && !p.bc[1] && !p.bc[2] && !params->solid && nx % 32 == 0 && ny % 8 == 0 &&
+                         27LL * c->N < (1LL << 31);
+    for (int k = 0; k < 3 && carried && e == cudaSuccess; ++k) e = cudaMalloc(&c->mom[k], 2 * sizeof(float) * (size_t)c->N);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->own_stream);
@@ -440,6 +452,8 @@ extern "C" void tel_destroy(tel_ctx *c)
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_gfall) cudaFree(c->d_gfall);
     if (c->d_solid) cudaFree(c->d_solid);
+    for (int k = 0; k < 3; ++k)
+        if (c->mom[k]) cudaFree(c->mom[k]);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->scratch) cudaFree(c->scratch);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -510,6 +524,7 @@ extern "C" int tel_init_device(tel_ctx *c, const double *rho, const double *phi,
     tel::LaunchArgs A{};
     A.in_rho = rho; A.in_phi = phi; A.in_u = u;
     A.fdst = c->f[c->cur]; A.gdst = c->g[c->cur];
+    c->mom_valid = 0;
     CUDA_OR_FAIL(c, launch(c, tel::MODE_INIT, A));
     c->initialized = 1;
     return TEL_OK;
@@ -536,14 +551,33 @@ extern "C" int tel_step(tel_ctx *c, int nsteps)
     if (!c) return TEL_EINVAL;
     if (nsteps < 0) return fail(c, TEL_EINVAL, "nsteps must be >= 0");
     if (!c->initialized) return fail(c, TEL_ESTATE, "tel_step before tel_init/tel_set_state");
+    const bool carried = c->mom[0] != nullptr;
+    if (carried && !c->mom_valid && nsteps > 0) {
+        // moments of the new state into mom[r]; mom[r + 1] (the first step's
+        // accumulator) cleared
+        c->mom_r = 0;
+        CUDA_OR_FAIL(c, tel::launch_d3q27_moments(c->dp, (const float *)c->f[c->cur], (const float *)c->g[c->cur],
+                                                  c->mom[0], c->mom[1], c->stream));
+        c->mom_valid = 1;
+    }
     for (int s = 0; s < nsteps; ++s) {
         tel::LaunchArgs A{};
         A.fsrc = c->f[c->cur]; A.gsrc = c->g[c->cur];
         A.fdst = c->f[1 - c->cur]; A.gdst = c->g[1 - c->cur];
+        if (carried) {
+            A.m_read = c->mom[c->mom_r];
+            A.m_acc = c->mom[(c->mom_r + 1) % 3];
+            A.m_zero = c->mom[(c->mom_r + 2) % 3];
+        }
         const int mode = c->p.gamma_mode == TEL_GAMMA_EXACT ? tel::MODE_STEP_EXACT
                          : (c->p.gamma_mode == TEL_GAMMA_CLOSED_F64SUM ? tel::MODE_STEP_G64 : tel::MODE_STEP);
-        CUDA_OR_FAIL(c, launch(c, mode, A));
+        const cudaError_t e = launch(c, mode, A);
+        if (e != cudaSuccess) {
+            c->mom_valid = 0;
+            return fail(c, TEL_ECUDA, "step launch: %s", cudaGetErrorString(e));
+        }
         c->cur = 1 - c->cur;
+        if (carried) c->mom_r = (c->mom_r + 1) % 3;
     }
     return TEL_OK;
 }
@@ -627,6 +661,7 @@ extern "C" int tel_set_state(tel_ctx *c, const double *f, const double *g)
         CUDA_OR_FAIL(c, cudaMemcpyAsync(c->scratch, g, QN * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CUDA_OR_FAIL(c, tel::launch_state_from_f64(c->lattice, c->scratch, (float *)c->g[c->cur], c->N, 0.0, c->stream));
     }
+    c->mom_valid = 0;
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     c->initialized = 1;
     return TEL_OK;

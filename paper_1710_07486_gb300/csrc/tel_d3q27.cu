@@ -15,6 +15,42 @@ cudaError_t launch_d3q27(int precision, int mode, const DevParams &P, const Laun
     return launch_lattice<3, TEL_D3_TX, TEL_D3_TY>(precision, mode, P, A, s);
 }
 
+// Carried moments of a state: node n pulls f_i from n - c_i (periodic), so
+// its rho - rho_ref and phi for the next step are the sums of the stored
+// (shifted) f and of g over those sources; the buffer that the first step
+// accumulates into is cleared.
+__global__ void moments_kernel(const float *f, const float *g, float *m_out, float *m_zero, int nx, int ny, int nz)
+{
+    typedef Lat<3> L;
+    const int N = nx * ny * nz;  // Q N < 2^31 on the periodic fast path
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+        float sf = 0.f, sg = 0.f;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            int sx = x - L::cx(i), sy = y - L::cy(i), sz = z - L::cz(i);
+            if (sx < 0) sx += nx; else if (sx >= nx) sx -= nx;
+            if (sy < 0) sy += ny; else if (sy >= ny) sy -= ny;
+            if (sz < 0) sz += nz; else if (sz >= nz) sz -= nz;
+            const int k = i * N + sx + nx * (sy + ny * sz);
+            sf += __ldg(f + k);
+            sg += __ldg(g + k);
+        }
+        m_out[n] = sf;
+        m_out[N + n] = sg;
+        m_zero[n] = 0.f;
+        m_zero[N + n] = 0.f;
+    }
+}
+
+cudaError_t launch_d3q27_moments(const DevParams &P, const float *f, const float *g, float *m_out, float *m_zero,
+                                 cudaStream_t s)
+{
+    if ((long long)Lat<3>::Q * P.N >= (1LL << 31)) return cudaErrorInvalidValue;
+    moments_kernel<<<152 * 8, 256, 0, s>>>(f, g, m_out, m_zero, P.nx, P.ny, P.nz);
+    return cudaGetLastError();
+}
+
 // f_i = fbar_i + w_i shift (shift = 0 for g)
 template <int D>
 __global__ void to_f64_kernel(const float *src, double *dst, long long N, double shift)

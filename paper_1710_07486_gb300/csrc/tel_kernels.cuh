@@ -112,6 +112,12 @@ struct LaunchArgs {
     void *fdst, *gdst;                        // populations (step, init)
     const double *in_rho, *in_phi, *in_u;     // init
     double *out_rho, *out_phi, *out_u, *out_p;// fields (nullable)
+    // carried moments (step, D3Q27 FP32 periodic): m_read holds the moments
+    // of this step's pull (rho - rho_ref for nodes 0..N-1, then phi), m_acc
+    // (zero on entry) receives the next step's, m_zero is cleared for the
+    // step after that
+    const float *m_read;
+    float *m_acc, *m_zero;
 };
 
 // ---------------------------------------------------------------------------
@@ -505,7 +511,12 @@ template <> struct StoreTraits<float> { typedef float CT; static constexpr bool 
 // their indices fit 32 bits.
 // VEC: phase A reads the populations as aligned four-node vectors along x
 // (D3Q27, FP32 storage, periodic, nx a multiple of 4, 32 x 8 tiles).
-template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false>
+// MOM (carried moments; D3Q27 VEC with nx % 32 == 0 and ny % 8 == 0): the
+// step scatters each post-collision population to the node that the next
+// step's pull brings it to, so that the next step's phase A reads rho and phi
+// (Eqs. 6-8, the zeroth moments of the pulled f and g) instead of pulling the
+// 54 populations of every node of the tile + ring 2 again.
+template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false, bool MOM = false>
 struct Fused {
     typedef Lat<D> L;
     typedef typename StoreTraits<ST>::CT CT;
@@ -535,6 +546,7 @@ struct Fused {
                            ((D == 3 && TX == 32 && TY == 8) ||
                             (D == 2 && TY == 1 && (TX == 32 || TX == 64)))),
                   "vector phase A: FP32 periodic step, D3Q27 32 x 8 or D2Q9 rows of 32 or 64");
+    static_assert(!MOM || (VEC && D == 3), "carried moments: the D3Q27 vector step only");
 
     // shared memory layout (in CT units)
     // ring buffers over planes: RS slots of rho, phi (tile + ring 2), MS of
@@ -781,9 +793,13 @@ struct Fused {
             const int mC = mA - dir * (SPLIT ? 2 : 3);
             const bool doA = dir > 0 ? mA <= m1 + 1 : mA >= m0 - 2;
             const bool doB = mB >= m0 - 1 && mB <= m1;
-            const int nA = doA ? (VEC ? NAV : NA) : 0;
+            const int nA = doA ? ((VEC && !MOM) ? NAV : NA) : 0;
             const int mm = map_coord(mA, PM, bM);
             auto item_a = [&](int w) {
+                if constexpr (MOM) {
+                    phase_a_mom(P, A.m_read, rp_s + slotR(mA) * NA, w, x0, y0, mm, shift);
+                    return;
+                }
                 if constexpr (VEC && D == 3) {
                     phase_a_vec(P, fs, gs, rp_s + slotR(mA) * NA, w, x0, y0, mm, shift);
                     return;
@@ -941,6 +957,40 @@ struct Fused {
                 if (need_grp) __syncthreads();
             }
         }
+    }
+
+    // Phase A with carried moments: item w is node (w % R2X - 2, w / R2X - 2)
+    // of the tile + ring 2 (periodic wrap), whose rho - rho_ref and phi the
+    // previous step (or the moments kernel after a new state) has summed.
+    __device__ static __forceinline__ void phase_a_mom(const DevParams &P, const float *mr, V2 *rp_plane, int w,
+                                                       int x0, int y0, int m, CT shift)
+    {
+        const int ox = w % R2X - 2, oy = w / R2X - 2;
+        int xx = x0 + ox, yy = y0 + oy;
+        if (xx < 0) xx += P.nx; else if (xx >= P.nx) xx -= P.nx;
+        if (yy < 0) yy += P.ny; else if (yy >= P.ny) yy -= P.ny;
+        const unsigned n = (unsigned)xx + (unsigned)P.nx * ((unsigned)yy + (unsigned)P.ny * (unsigned)m);
+        rp_plane[w] = V::pair(shift + __ldg(mr + n), __ldg(mr + (unsigned)P.N + n));
+    }
+
+    // Carried moments: the post-collision populations c = (c_x, cy, cz),
+    // c_x = -1, 0, 1, of the warp's row (lane = x - x0) reach the nodes
+    // x + c of row y + cy of plane z + cz in the next step's pull.  The three
+    // that reach node x are summed across lanes first (one atomic add per
+    // node of the row), the two that leave the warp's 32 nodes (x0 - 1 from
+    // lane 0, x0 + 32 from lane 31) are added by one more instruction.  Every
+    // lane of the warp is present (full tiles).
+    __device__ static __forceinline__ void scatter_row(float *M, const Nbr &nb, int cy, int cz, float vm, float v0,
+                                                       float vp)
+    {
+        const int lane = threadIdx.x & 31;
+        const float up = __shfl_up_sync(0xffffffffu, vp, 1);    // c_x = +1 of node x - 1
+        const float dn = __shfl_down_sync(0xffffffffu, vm, 1);  // c_x = -1 of node x + 1
+        const float sum = v0 + (lane > 0 ? up : 0.f) + (lane < 31 ? dn : 0.f);
+        const unsigned row = (unsigned)(nb.off[1][1 - cy] + nb.off[2][1 - cz]);
+        atomicAdd(M + row + (unsigned)nb.off[0][1], sum);
+        if (lane == 0 || lane == 31)
+            atomicAdd(M + row + (unsigned)(lane == 0 ? nb.off[0][2] : nb.off[0][0]), lane == 0 ? vm : vp);
     }
 
     // Phase A on four-node vectors along x.  Item w (all 32 lanes of warp
@@ -1225,6 +1275,11 @@ struct Fused {
             return;
         }
         if constexpr (StoreTraits<ST>::shifted && STEPPING) {
+            if constexpr (MOM) {
+                // the buffer that the step after the next one accumulates into
+                A.m_zero[n] = 0.f;
+                A.m_zero[P.N + n] = 0.f;
+            }
             collide_pairs(P, A, gs, nbc, f_rest, reinterpret_cast<float2 *>(stash) + (tx + TX * ty), n, rho, phi,
                           mu_phi, F);
             return;
@@ -1452,6 +1507,7 @@ struct Fused {
             for (int a = 0; a < 3; ++a) U2[a] = make_float2(up[a], -up[a]);
             float2 goth = bc2(0.f);
             float *gd = reinterpret_cast<float *>(A.gdst);
+            float sG[3], sN[3];  // carried moments: row groups of k and of Q-1-k
             // pair (kp, k), kp = Q-1-k: the member kp has a positive last
             // non-zero component of c, so c.u is U2 of that axis plus or minus
             // the others
@@ -1473,8 +1529,21 @@ struct Fused {
                 goth = add2(goth, go);
                 gd[didx(kp)] = go.x;
                 gd[didx(k)] = go.y;
+                if constexpr (MOM) {
+                    // k = c_x + 1 + 3 (cy + 1) + 9 (cz + 1): the pairs k of one
+                    // row group complete it and the opposite group
+                    const int jx = k % 3;
+                    sG[jx] = go.y;
+                    sN[2 - jx] = go.x;
+                    if (jx == 2) {
+                        scatter_row(A.m_acc + P.N, nb, L::cy(k), L::cz(k), sG[0], sG[1], sG[2]);
+                        scatter_row(A.m_acc + P.N, nb, L::cy(kp), L::cz(kp), sN[0], sN[1], sN[2]);
+                    }
+                }
             }
-            gd[didx(L::REST)] = phi - (goth.x + goth.y);
+            const float grest = phi - (goth.x + goth.y);
+            gd[didx(L::REST)] = grest;
+            if constexpr (MOM) scatter_row(A.m_acc + P.N, nb, 0, 0, sG[0], grest, sN[2]);
         }
 
         // ---- equilibrium factors at u; second moments of f^eq
@@ -1647,6 +1716,7 @@ struct Fused {
         const float2 OMG = bc2(1.f - gb), PG = bc2(gb - 2.f * K.beta), NG = bc2(2.f * K.beta - gb);
         float *fd = reinterpret_cast<float *>(A.fdst);
         float2 oth = bc2(0.f);
+        float sG[3], sN[3];  // carried moments: row groups of k and of Q-1-k
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
             float2 out = fma2(OMG, stash2[k * NT], sub2(feq2(k, XF, YF, ZF), bc2((float)L::w(k) * shift)));
@@ -1661,8 +1731,19 @@ struct Fused {
             oth = add2(oth, out);
             fd[didx(k)] = out.x;
             fd[didx(Q - 1 - k)] = out.y;
+            if constexpr (MOM) {
+                const int jx = k % 3;
+                sG[jx] = out.x;
+                sN[2 - jx] = out.y;
+                if (jx == 2) {
+                    scatter_row(A.m_acc, nb, L::cy(k), L::cz(k), sG[0], sG[1], sG[2]);
+                    scatter_row(A.m_acc, nb, L::cy(Q - 1 - k), L::cz(Q - 1 - k), sN[0], sN[1], sN[2]);
+                }
+            }
         }
-        fd[didx(L::REST)] = fsum - (oth.x + oth.y);
+        const float frest = fsum - (oth.x + oth.y);
+        fd[didx(L::REST)] = frest;
+        if constexpr (MOM) scatter_row(A.m_acc, nb, 0, 0, sG[0], frest, sN[2]);
 
         if (bad) raise_err(P.err, bad);
     }
@@ -1803,11 +1884,11 @@ template <int NTH, bool VEC> struct KernelMinBlocks<2, NTH, float, VEC> {
     static constexpr int value = (VEC ? TEL_D2Q9_VEC_WARPS_PER_SM : TEL_D2Q9_WARPS_PER_SM) * 32 / NTH;
 };
 
-template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false>
+template <int D, int TX, int TY, typename ST, int MODE, bool FAST, bool VEC = false, bool MOM = false>
 __global__ void __launch_bounds__(TX * TY, (KernelMinBlocks<D, TX * TY, ST, VEC>::value))
     fused_kernel(const DevParams P, const LaunchArgs A)
 {
-    Fused<D, TX, TY, ST, MODE, FAST, VEC>::run(P, A);
+    Fused<D, TX, TY, ST, MODE, FAST, VEC, MOM>::run(P, A);
 }
 
 // Batched persistent D2Q9 step: each CTA walks a work list of (case, tile,
@@ -1859,6 +1940,12 @@ int batch_blocks_per_sm(int precision, int tx, bool fast, bool vec);
 // Tile shapes and launcher (defined per lattice in tel_d2q9.cu / tel_d3q27.cu).
 cudaError_t launch_d2q9(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s);
 cudaError_t launch_d3q27(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s);
+
+// Carried moments of a new state (D3Q27 FP32, periodic): m_out gets the
+// sums of the populations each node pulls in the next step (rho - rho_ref,
+// then phi), m_zero (2N floats) is cleared.
+cudaError_t launch_d3q27_moments(const DevParams &P, const float *f, const float *g, float *m_out, float *m_zero,
+                                 cudaStream_t s);
 
 // Shift conversion of whole population arrays (FP32 mode state get/set).
 cudaError_t launch_state_to_f64(int lattice, const float *src, double *dst, long long N, double shift,

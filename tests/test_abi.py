@@ -70,6 +70,7 @@ def test_invalid_parameters_rejected_before_any_device_work():
         (0, 8, 8, 1, dict(good, bc=(0, 2, 0))),
         (0, 8, 8, 1, dict(good, bc=(0, 1, 0), wet_rho=float("nan"))),
         (0, 8, 8, 1, dict(good, bc=(0, 1, 0), wet_phi=float("inf"))),
+        (1, 32, 8, 8, dict(good, moments=2)),   # bad moments mode
     ]
     for lat, nx, ny, nz, p in bad_cases:
         with pytest.raises(tel.TelError) as ei:
