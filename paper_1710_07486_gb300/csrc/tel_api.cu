@@ -415,11 +415,11 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
         }
         delete[] h;
     }
-    // carried moments: D3Q27 FP32, periodic, no solid node, full 32 x 8
-    // tiles, 32-bit population indices (the step kernel's vector path)
+    // carried moments: D3Q27 FP32, periodic, no solid node, full tiles of
+    // rows of 32, 32-bit population indices (the step kernel's fast path)
     const bool carried = p.moments == TEL_MOMENTS_CARRIED && lattice == TEL_D3Q27 && p.precision == TEL_FP32_SHIFTED &&
-                         !p.bc[0] && !p.bc[1] && !p.bc[2] && !params->solid && nx % 32 == 0 && ny % 8 == 0 &&
-                         27LL * c->N < (1LL << 31);
+                         !p.bc[0] && !p.bc[1] && !p.bc[2] && !params->solid && nx % 32 == 0 &&
+                         ny % tel::d3q27_carried_tile_y() == 0 && 27LL * c->N < (1LL << 31);
     for (int k = 0; k < 3 && carried && e == cudaSuccess; ++k) e = cudaMalloc(&c->mom[k], 2 * sizeof(float) * (size_t)c->N);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);

@@ -1,5 +1,6 @@
 // D3Q27 instantiation of the fused kernel: 32 x 8 tiles in the xy plane
-// marching along z; also the FP32-shift conversions of whole state arrays.
+// marching along z (32 x 4 for the step with carried moments); also the
+// moments of a new state and the FP32-shift conversions of whole state arrays.
 #include "tel_launch.cuh"
 
 #ifndef TEL_D3_TX
@@ -8,12 +9,32 @@
 #ifndef TEL_D3_TY
 #define TEL_D3_TY 8
 #endif
+// carried moments: rows of 32 (one warp per row), 4 rows, 4 CTAs per SM
+#ifndef TEL_D3_MOM_TY
+#define TEL_D3_MOM_TY 4
+#endif
 
 namespace tel {
+// The FP32 step with carried moments (A.m_read set): periodic fast path,
+// full tiles only (every lane of a warp takes part in the row scatter).
+static cudaError_t launch_carried(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s)
+{
+    constexpr int TY = TEL_D3_MOM_TY;
+    const bool fast = !P.bc[0] && !P.bc[1] && !P.bc[2] && P.solid == nullptr && 27LL * P.N < (1LL << 31);
+    if (precision != 1 || !fast || P.nx % 32 != 0 || P.ny % TY != 0 || !A.m_acc || !A.m_zero)
+        return cudaErrorInvalidValue;
+    if (mode == MODE_STEP_EXACT) return launch_one<3, 32, TY, float, MODE_STEP_EXACT, true, false, true>(P, A, s);
+    if (mode == MODE_STEP_G64) return launch_one<3, 32, TY, float, MODE_STEP_G64, true, false, true>(P, A, s);
+    if (mode == MODE_STEP) return launch_one<3, 32, TY, float, MODE_STEP, true, false, true>(P, A, s);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_d3q27(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s)
 {
+    if (A.m_read) return launch_carried(precision, mode, P, A, s);
     return launch_lattice<3, TEL_D3_TX, TEL_D3_TY>(precision, mode, P, A, s);
 }
+int d3q27_carried_tile_y() { return TEL_D3_MOM_TY; }
 
 // Carried moments of a state: node n pulls f_i from n - c_i (periodic), so
 // its rho - rho_ref and phi for the next step are the sums of the stored

@@ -511,7 +511,8 @@ template <> struct StoreTraits<float> { typedef float CT; static constexpr bool 
 // their indices fit 32 bits.
 // VEC: phase A reads the populations as aligned four-node vectors along x
 // (D3Q27, FP32 storage, periodic, nx a multiple of 4, 32 x 8 tiles).
-// MOM (carried moments; D3Q27 VEC with nx % 32 == 0 and ny % 8 == 0): the
+// MOM (carried moments; D3Q27 FP32 periodic step, rows of 32, nx % 32 == 0
+// and ny % TY == 0): the
 // step scatters each post-collision population to the node that the next
 // step's pull brings it to, so that the next step's phase A reads rho and phi
 // (Eqs. 6-8, the zeroth moments of the pulled f and g) instead of pulling the
@@ -546,7 +547,8 @@ struct Fused {
                            ((D == 3 && TX == 32 && TY == 8) ||
                             (D == 2 && TY == 1 && (TX == 32 || TX == 64)))),
                   "vector phase A: FP32 periodic step, D3Q27 32 x 8 or D2Q9 rows of 32 or 64");
-    static_assert(!MOM || (VEC && D == 3), "carried moments: the D3Q27 vector step only");
+    static_assert(!MOM || (D == 3 && TX == 32 && !VEC && STEPPING && FAST && StoreTraits<ST>::shifted),
+                  "carried moments: the D3Q27 FP32 periodic step with rows of 32 (one warp per row)");
 
     // shared memory layout (in CT units)
     // ring buffers over planes: RS slots of rho, phi (tile + ring 2), MS of
@@ -793,7 +795,7 @@ struct Fused {
             const int mC = mA - dir * (SPLIT ? 2 : 3);
             const bool doA = dir > 0 ? mA <= m1 + 1 : mA >= m0 - 2;
             const bool doB = mB >= m0 - 1 && mB <= m1;
-            const int nA = doA ? ((VEC && !MOM) ? NAV : NA) : 0;
+            const int nA = doA ? (VEC ? NAV : NA) : 0;
             const int mm = map_coord(mA, PM, bM);
             auto item_a = [&](int w) {
                 if constexpr (MOM) {
@@ -1857,8 +1859,12 @@ struct Fused {
 };
 
 // Minimum resident CTAs per SM requested from the register allocator.
-#ifndef TEL_MIN_BLOCKS_FP32
-#define TEL_MIN_BLOCKS_FP32 2
+// D3Q27 FP32: 16 warps per SM (2 CTAs of 32 x 8, 4 of 32 x 4; up to 128
+// registers).  Measured on the carried-moment step at 256^3: 32 x 4 tiles at
+// 4 CTAs per SM 8300 MLUPS, at 5 (96 registers) 8267, 32 x 8 at 2 7735 and
+// at 3 (80 registers, spills) 7360, 32 x 16 at 1 6706, 32 x 2 at 8 7140.
+#ifndef TEL_D3_FP32_WARPS_PER_SM
+#define TEL_D3_FP32_WARPS_PER_SM 16
 #endif
 // D2Q9 single lattices: measured with 4 (2 CTAs of rows of 64 requested,
 // 98 registers) and 24 warps per SM (80 registers): 7961 / 14620 MLUPS and
@@ -1874,11 +1880,13 @@ struct Fused {
 #ifndef TEL_D2Q9_VEC_WARPS_PER_SM
 #define TEL_D2Q9_VEC_WARPS_PER_SM 18
 #endif
-template <typename ST> struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<float> { static constexpr int value = TEL_MIN_BLOCKS_FP32; };
-// D2Q9 FP32: TEL_D2Q9_(VEC_)WARPS_PER_SM warps per SM requested
+// FP64: one CTA; FP32: TEL_D3_FP32_WARPS_PER_SM or TEL_D2Q9_(VEC_)WARPS_PER_SM
+// warps per SM requested
 template <int D, int NTH, typename ST, bool VEC> struct KernelMinBlocks {
-    static constexpr int value = MinBlocks<ST>::value;
+    static constexpr int value = 1;
+};
+template <int NTH, bool VEC> struct KernelMinBlocks<3, NTH, float, VEC> {
+    static constexpr int value = TEL_D3_FP32_WARPS_PER_SM * 32 / NTH;
 };
 template <int NTH, bool VEC> struct KernelMinBlocks<2, NTH, float, VEC> {
     static constexpr int value = (VEC ? TEL_D2Q9_VEC_WARPS_PER_SM : TEL_D2Q9_WARPS_PER_SM) * 32 / NTH;
@@ -1940,6 +1948,9 @@ int batch_blocks_per_sm(int precision, int tx, bool fast, bool vec);
 // Tile shapes and launcher (defined per lattice in tel_d2q9.cu / tel_d3q27.cu).
 cudaError_t launch_d2q9(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s);
 cudaError_t launch_d3q27(int precision, int mode, const DevParams &P, const LaunchArgs &A, cudaStream_t s);
+// Tile of the D3Q27 step with carried moments (TX = 32 x TY nodes of the
+// xy plane): a lattice takes that path only if nx % 32 == 0 and ny % TY == 0.
+int d3q27_carried_tile_y();
 
 // Carried moments of a new state (D3Q27 FP32, periodic): m_out gets the
 // sums of the populations each node pulls in the next step (rho - rho_ref,

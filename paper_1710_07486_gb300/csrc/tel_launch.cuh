@@ -42,17 +42,6 @@ static cudaError_t launch_prec(int precision, int mode, const DevParams &P, cons
     if (mode == MODE_STEP || mode == MODE_STEP_EXACT || mode == MODE_STEP_G64) {
         // aligned four-node vectors in phase A (D3Q27 32 x 8 or D2Q9 rows of
         // 32 or 64, periodic, nx % 4 == 0)
-        if constexpr (D == 3 && TX == 32 && TY == 8 && FAST) {
-            // carried moments: full tiles only (every lane of a warp takes
-            // part in the row scatter)
-            if (A.m_read) {
-                if (P.nx % 32 != 0 || P.ny % 8 != 0 || !A.m_acc || !A.m_zero) return cudaErrorInvalidValue;
-                if (mode == MODE_STEP_EXACT)
-                    return launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST, true, true>(P, A, s);
-                if (mode == MODE_STEP_G64) return launch_one<D, TX, TY, float, MODE_STEP_G64, FAST, true, true>(P, A, s);
-                return launch_one<D, TX, TY, float, MODE_STEP, FAST, true, true>(P, A, s);
-            }
-        }
         if constexpr (((D == 3 && TX == 32 && TY == 8) || (D == 2 && TY == 1 && (TX == 32 || TX == 64))) && FAST)
             if (P.nx % 4 == 0) {
                 if (mode == MODE_STEP_EXACT) return launch_one<D, TX, TY, float, MODE_STEP_EXACT, FAST, true>(P, A, s);
@@ -73,7 +62,6 @@ static cudaError_t launch_lattice(int precision, int mode, const DevParams &P, c
     // fast pulls: no bounce-back axis, no solid node and 32-bit population indices
     const bool walls = P.bc[0] || P.bc[1] || (D == 3 && P.bc[2]) || P.solid != nullptr;
     const bool fast = !walls && (long long)Lat<D>::Q * P.N < (1LL << 31);
-    if (A.m_read && !fast) return cudaErrorInvalidValue;  // carried moments: periodic fast path only
     if (fast) return launch_prec<D, TX, TY, true>(precision, mode, P, A, s);
     return launch_prec<D, TX, TY, false>(precision, mode, P, A, s);
 }
