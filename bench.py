@@ -689,6 +689,41 @@ def cpu_baseline(args):
         out["full_size"] = {"value": round(v_f, 4), "unit": "MLUPS", "cores": omp_threads(),
                             "sample": f"D3Q27 {args.n}^3, the bench's own collision, {d_f} step(s), FP64, "
                                       f"OpenMP, {t_f:.1f} s"}
+    if args.cpu_2d:
+        out["d2q9"] = oracle_2d_runs(args.seed)
+    return out
+
+
+def oracle_2d_runs(seed):
+    """The FP64 oracle on every host core on the two D2Q9 workloads: the
+    touching drops (64^2, density ratio 10, equal tensions) for all of their
+    2000 steps, and the 512^2 head-on collision at density ratio 1000 for a
+    20-step window."""
+    from oracle import oracle as orc
+    from paper_1710_07486_gb300 import inputs
+    out = {}
+    T = orc.temperature_for_ratio(A_, B_, R_, 10.0)
+    rg, rl = orc.coexistence(A_, B_, R_, T)[:2]
+    p = dict(a=A_, b=B_, R=R_, T=T, lambda1=0.6, lambda2=0.25, lambda3=0.25, kappa1=0.0216, kappa2=0.5,
+             kappa3=0.5, chi=5.0, nu=1.0 / 6.0, Gamma=1.0, tau_g=1.0, force_form=1)
+    rho, phi, u = inputs.touching_drops_2d(64, 64, rg, rl, p["chi"], R=12.0, offset=20.0, width=5.0)
+    runs = [("touching_drops_64", 64, p, (rho, phi, u), 2000)]
+    T = orc.temperature_for_ratio(A_, B_, R_, 1000.0)
+    rg, rl = orc.coexistence(A_, B_, R_, T)[:2]
+    p = dict(a=A_, b=B_, R=R_, T=T, lambda1=0.02, lambda2=0.4, lambda3=0.4, kappa1=0.001, kappa2=4.0,
+             kappa3=4.0, chi=5.0, nu=0.2, Gamma=1.0, tau_g=1.0, force_form=1)
+    rho, phi, u = inputs.head_on_2d(seed, 512, rg, rl, p["chi"], 0.05, width=10.0)
+    runs.append(("head_on_512_ratio_1000", 512, p, (rho, phi, u), 20))
+    for name, n, p, fields, steps in runs:
+        o = orc.Oracle(orc.D2Q9, n, n, 1, p, openmp=True)
+        f, g = o.init(*fields)
+        t0 = time.perf_counter()
+        rc = o.step(f, g, steps)
+        dt = time.perf_counter() - t0
+        out[name] = {"value": round(n * n * steps / dt / 1e6, 4), "unit": "MLUPS", "cores": omp_threads(),
+                     "sample": f"D2Q9 {n}^2, {steps} steps, FP64, OpenMP, {dt:.1f} s" + ("" if rc == 0 else
+                                                                                       ", flagged unstable")}
+        del o, f, g
     return out
 
 
@@ -751,6 +786,9 @@ def main():
     ap.add_argument("--cpu-full-steps", type=int, default=1,
                     help="oracle steps timed at the full size (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-2d", type=int, default=1,
+                    help="also time the oracle on the D2Q9 touching drops (2000 steps) and head-on collision "
+                         "(20 steps) on every core")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the batched (C4) and surrogate (C5) measurements nested in the main line")
     ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5"],
