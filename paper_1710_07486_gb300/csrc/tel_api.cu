@@ -295,6 +295,11 @@ static int validate(int lattice, int nx, int ny, int nz, const tel_params *p)
 
 // Device-side parameter block of a validated lattice and its coexistence
 // point co = {rho_g, rho_l, mu_coex, p_coex}.
+namespace tel {
+// Resident CTAs per SM of the D2Q9 single-lattice step kernel (tel_d2q9.cu).
+cudaError_t d2q9_step_ctas_per_sm(int precision, bool fast, bool vec, int *out);
+}  // namespace tel
+
 static void fill_devparams(int lattice, int nx, int ny, int nz, const tel_params &p, const double co[4],
                            tel::DevParams &d)
 {
@@ -395,6 +400,26 @@ extern "C" int tel_create(int lattice, int nx, int ny, int nz, const tel_params 
     const tel_params &p = c->p;
     fill_devparams(lattice, nx, ny, nz, p, co, d);
     c->p.rho_ref = d.rho_ref;
+    if (lattice == TEL_D2Q9 && !std::getenv("TEL_CHUNK")) {
+        // rows per CTA: the fewest (at least 2, at most 16) with which one
+        // wave of the step kernel's resident CTAs covers the lattice.  Rows
+        // of 64 march along y, so a small lattice has few CTAs unless their
+        // columns are short: 512^2 FP32 measured 9827 MLUPS with 8 rows
+        // (a third of the resident slots), 11605 with 4 and 12750 with 3;
+        // 2048^2 18520 with 32, 19385 with 16 and 18725 with 8.
+        const bool fast = !p.bc[0] && !p.bc[1] && !params->solid && 9LL * c->N < (1LL << 31);
+        const bool vec = fast && p.precision == TEL_FP32_SHIFTED && nx % 4 == 0;
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            tel::d2q9_step_ctas_per_sm(p.precision, fast, vec, &per_sm) == cudaSuccess && sms > 0 && per_sm > 0) {
+            const long long slots = (long long)sms * per_sm, tiles = (nx + 63) / 64;
+            long long ch = ((long long)ny * tiles + slots - 1) / slots;
+            d.chunk = (int)(ch < 2 ? 2 : (ch > 16 ? 16 : ch));
+        } else {
+            cudaGetLastError();  // keep the default chunk
+        }
+    }
 
     const size_t es = p.precision == TEL_FP64 ? sizeof(double) : sizeof(float);
     const size_t bytes = es * (size_t)c->Q * (size_t)c->N;

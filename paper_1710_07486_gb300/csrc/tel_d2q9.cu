@@ -7,6 +7,26 @@ cudaError_t launch_d2q9(int precision, int mode, const DevParams &P, const Launc
 {
     return launch_lattice<2, 64, 1>(precision, mode, P, A, s);
 }
+
+// Resident CTAs per SM of the single-lattice step kernel that launch_d2q9
+// picks for this storage and path (MODE_STEP).
+template <typename ST, bool FAST, bool VEC>
+static cudaError_t step_occupancy(int *out)
+{
+    typedef Fused<2, 64, 1, ST, MODE_STEP, FAST, VEC> K;
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<2, 64, 1, ST, MODE_STEP, FAST, VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fused_kernel<2, 64, 1, ST, MODE_STEP, FAST, VEC>,
+                                                         K::NT, K::SMEM_BYTES);
+}
+
+cudaError_t d2q9_step_ctas_per_sm(int precision, bool fast, bool vec, int *out)
+{
+    if (precision == 0) return fast ? step_occupancy<double, true, false>(out) : step_occupancy<double, false, false>(out);
+    if (!fast) return step_occupancy<float, false, false>(out);
+    return vec ? step_occupancy<float, true, true>(out) : step_occupancy<float, true, false>(out);
+}
 }  // namespace tel
 
 namespace tel {
