@@ -200,6 +200,17 @@ def next_summary(line):
     return {k: v for k, v in line.items() if k not in ("loss", "n_gpus", "scaling", "vs_baseline")}
 
 
+def nested_run(fn, args):
+    """A batched or surrogate measurement for the main line; a failure there
+    is reported in its place instead of losing the main line."""
+    try:
+        return next_summary(fn(args))
+    except Exception as ex:  # the headline measurement is already complete
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(ex).__name__}: {ex}"[:500]}
+
+
 def c5_setup(seed, n, H, rmin=100.0, rmax=1000.0):
     """n 2D collisions in H x H periodic boxes (the batched-case recipe at
     one size): parameters and initial fields."""
@@ -627,8 +638,8 @@ def run_gpu(args):
             line["cpu_baseline"] = cpu
         lat.close()
         if world == 1 and not args.no_next:
-            line["batched"] = next_summary(run_c4(args))
-            line["surrogate"] = next_summary(run_c5(args))
+            line["batched"] = nested_run(run_c4, args)
+            line["surrogate"] = nested_run(run_c5, args)
         print(json.dumps(line), flush=True)
     else:
         lat.close()

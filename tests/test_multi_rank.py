@@ -78,3 +78,16 @@ def test_reference_arm_prints_on_rank_zero_only(orc):
     outs = run_ranks(REF)
     assert '"impl": "reference"' in outs[0]
     assert outs[1].strip() == ""
+
+
+def test_nested_measurement_failure_keeps_the_main_line():
+    """A batched or surrogate measurement that raises is reported in its
+    place in the bench line; the training log is dropped from one that runs."""
+    import bench
+
+    def fails(args):
+        raise RuntimeError("no batched cases")
+
+    assert bench.nested_run(fails, None) == {"error": "RuntimeError: no batched cases"}
+    ok = bench.nested_run(lambda a: {"metric": "m", "value": 1.0, "loss": [0.5], "n_gpus": 1}, None)
+    assert ok == {"metric": "m", "value": 1.0}
