@@ -590,6 +590,20 @@ def run_gpu(args):
     o_u = torch.empty(3 * N, dtype=torch.float64).pin_memory()
     import ctypes as C
     L = tel.lib()
+
+    def e2e_round(steps):
+        rc = L.tel_init(lat._h, C.c_void_p(h_rho.data_ptr()), C.c_void_p(h_phi.data_ptr()),
+                        C.c_void_p(h_u.data_ptr()))
+        for _ in range(steps):
+            rc |= L.tel_step(lat._h, 1)
+            rc |= (L.tel_sync(lat._h) if rc == 0 else rc)
+        rc |= L.tel_fields(lat._h, C.c_void_p(o_rho.data_ptr()), C.c_void_p(o_phi.data_ptr()),
+                           C.c_void_p(o_u.data_ptr()), None)
+        return rc
+
+    # untimed warm-up of the same calls: the library's host-field staging
+    # buffer is allocated by the first tel_init / tel_fields of a context
+    e2e_round(min(args.warmup, 3))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
