@@ -166,7 +166,7 @@ typedef enum { TEL_EOS_CS = 0, TEL_EOS_VDW = 1, TEL_EOS_PR = 2 } tel_eos;
  * update computed is the same either way; the two differ only in the
  * rounding of those stencil inputs.
  *   TEL_MOMENTS_CARRIED: where it applies -- D3Q27, TEL_FP32_SHIFTED, every
- *     axis periodic, no solid node, nx % 32 == 0, ny % 8 == 0 -- each step
+ *     axis periodic, no solid node, nx % 32 == 0, ny % 4 == 0 -- each step
  *     also adds every post-collision population into the moments of the node
  *     that the next step's pull brings it to (FP32 atomic additions into a
  *     device array, so their summation order, and the last bit of those

@@ -1,5 +1,5 @@
 """Carried moments (tel_params.moments = TEL_MOMENTS_CARRIED, the default
-where it applies: D3Q27, FP32-shifted, periodic, nx % 32 == 0, ny % 8 == 0).
+where it applies: D3Q27, FP32-shifted, periodic, nx % 32 == 0, ny % 4 == 0).
 Each step adds its post-collision populations into the moments rho, phi
 (Eqs. 6-8) of the nodes that the next step's pull brings them to, and the
 next step's stencils read those instead of pulling the ring's populations
