@@ -38,7 +38,7 @@ def one_step_err(orc, p, shape, f0, g0, f1, g1):
     return max(ef, eg)
 
 
-@pytest.mark.parametrize("shape", [(64, 16, 12), (32, 24, 9)])
+@pytest.mark.parametrize("shape", [(64, 16, 12), (32, 24, 9), (64, 12, 10)])
 @pytest.mark.parametrize("mode", [tel.GAMMA_CLOSED, tel.GAMMA_EXACT, tel.GAMMA_CLOSED_F64SUM])
 def test_carried_one_step_against_oracle(orc, T10, shape, mode):
     """Steps 1-3 read moments from the scatter of the step before (after
