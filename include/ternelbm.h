@@ -189,7 +189,8 @@ typedef struct tel_ctx tel_ctx;
  * Validates the parameters (tau > 1/2, tau_g > 1/2, chi > 0, kappa >= 0,
  * lambda >= 0, T below the critical temperature, every extent >= 4, nz == 1
  * for D2Q9), solves the common-tangent construction for rho_g, rho_l
- * (text after Eq. 4), allocates the double-buffered populations and returns
+ * (text after Eq. 4), allocates the double-buffered populations (and, where
+ * TEL_MOMENTS_CARRIED applies, three moment arrays of 2 N floats) and returns
  * the context in *out.  Errors: TEL_EINVAL, TEL_ENOMEM, TEL_ECUDA. */
 int tel_create(int lattice, int nx, int ny, int nz, const tel_params *params,
                tel_ctx **out);
